@@ -1,0 +1,162 @@
+/*
+ * dls.h -- C ABI of the GB300 (sm_103a) Discontinuous DLS block compressor.
+ *
+ * Method: arXiv 2601.20113, "A Data-Informed Local Subspaces Method for
+ * Error-Bounded Lossy Compression of Large-Scale Scientific Datasets".
+ * The field is partitioned into independent space-time blocks (patches,
+ * Algorithm 1 step 2); each block gets its own basis from the right singular
+ * vectors of its data matrix, computed the cross-product way (Gram matrix +
+ * symmetric eigensolve; Sec. 2.3 Eq. 2-3, Sec. 2.7.1); its coefficients are
+ * the projection S = C^T P (Sec. 2.5, Eq. 5); the retained prefix is the
+ * smallest one meeting the local L2 tolerance (Sec. 2.4 Eq. 4, Sec. 2.5
+ * Eq. 6), found by bisection; coefficients are quantized (in place of
+ * bit-grooming) and, for pointwise bounds, a correction pass makes every
+ * point meet the bound.  Streams follow Sec. 2.7.2: an addressable header,
+ * an offset table from an exclusive scan of record sizes, packed records.
+ *
+ * Conventions for every call:
+ *   - Pointers named d_* are device pointers, h_* are host pointers.  The
+ *     caller owns every buffer; the library keeps only small cached state
+ *     (pinned status words, the rank model, graph and tuning caches).
+ *   - Calls are ordered on `stream` and asynchronous, except that values the
+ *     call returns through host pointers (out_bytes, reports) are written
+ *     before it returns: such calls synchronize `stream` once.
+ *   - Return value: DLS_OK (0) or a negative DLS_ERR_* status.  On error, the
+ *     contents of output buffers are unspecified.
+ *   - Fields hold nvars variables back to back, each laid out
+ *     [nt][nz][ny][nx] (x fastest), in float32 or float64.
+ */
+#ifndef DLS_H
+#define DLS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st* dls_stream_t;
+
+enum { DLS_F32 = 0, DLS_F64 = 1 };
+/* Bound types.  ABS: absolute pointwise bound.  REL_RANGE: bound = value x
+ * (max - min) of each variable (one extra read of the field).  NRMSE: the
+ * paper's global L2 target in percent, eps = eps_t ||u|| / 100 (Sec. 2.4);
+ * no pointwise correction in that mode. */
+enum { DLS_EB_ABS = 0, DLS_EB_REL_RANGE = 1, DLS_EB_NRMSE = 2 };
+/* Arithmetic of the Gram and projection products.  FP64: plain double
+ * precision everywhere.  TF32X3 / BF16X3: split-precision products on the
+ * tensor cores with FP32 accumulation (3 terms), eigensolve, residual and
+ * bound checks keep FP64 semantics. */
+enum { DLS_PREC_FP64 = 0, DLS_PREC_TF32X3 = 1, DLS_PREC_BF16X3 = 2 };
+/* Rank selection.  SEARCH: bisection of Algorithm 1.  LEARNED: a small MLP
+ * predicts the rank, which is accepted only if it is the smallest passing
+ * rank around the prediction; otherwise the bisection decides. */
+enum { DLS_RANK_SEARCH = 0, DLS_RANK_LEARNED = 1 };
+
+enum {
+  DLS_OK = 0,
+  DLS_ERR_INVALID_ARG = -1,   /* bad parameter, null pointer, bad size */
+  DLS_ERR_CAPACITY = -2,      /* output too small; *out_bytes holds the size needed */
+  DLS_ERR_NONFINITE = -3,     /* NaN or Inf in the input field */
+  DLS_ERR_CORRUPT = -4,       /* stream fails structural validation */
+  DLS_ERR_CUDA = -5,          /* a CUDA runtime call failed */
+  DLS_ERR_TIMEOUT = -6,       /* a bounded device wait gave up */
+  DLS_ERR_BOUND_VIOLATED = -7,/* dls_verify: some point exceeds its bound */
+  DLS_ERR_WORKSPACE = -8,     /* workspace missing or smaller than dls_workspace_size */
+  DLS_ERR_NO_MODEL = -9       /* LEARNED rank mode without a loaded model */
+};
+
+typedef struct {
+  int32_t nvars;          /* >= 1, <= 64 */
+  int64_t dims[4];        /* nx, ny, nz, nt (nz = 1 for 2-D fields) */
+  int32_t block[4];       /* bx, by, bz, bt; 1 <= block[i] <= dims[i];
+                             min(bx*by*bz, bt) <= 32; bx*by*bz*bt <= 2^26 */
+  int32_t dtype;          /* DLS_F32 / DLS_F64 */
+  int32_t eb_type;        /* DLS_EB_* */
+  const double* eb;       /* host array of nvars values, each > 0 */
+  int32_t rank_cap;       /* >= 0; per block min(rank_cap, Gram order) */
+  int32_t precision;      /* DLS_PREC_* */
+  int32_t rank_mode;      /* DLS_RANK_* */
+  int64_t block_begin;    /* compress blocks [block_begin, block_end) only; */
+  int64_t block_end;      /* block_end < 0 means through the last block      */
+} dls_params;
+
+/* Worst-case stream size for these parameters (each record is at most the
+ * raw block plus 16 bytes).  0 if the parameters are invalid. */
+size_t dls_compress_bound(const dls_params* p);
+
+/* Device workspace dls_compress needs, in bytes (caller allocates, 256-byte
+ * aligned).  0 if the parameters are invalid. */
+size_t dls_workspace_size(const dls_params* p);
+
+/* Compress a device field (Algorithm 1, step 2-3; Sec. 2.7.2 stream).
+ * d_in: nvars * nx*ny*nz*nt values of p->dtype.  d_out: out_cap bytes.
+ * d_workspace: ws_bytes >= dls_workspace_size(p).  On success *out_bytes is
+ * the stream size.  On DLS_ERR_CAPACITY *out_bytes is the size needed.
+ * Synchronizes `stream` once to read the stream size. */
+int dls_compress(const dls_params* p, const void* d_in, void* d_out, size_t out_cap,
+                 size_t* out_bytes, void* d_workspace, size_t ws_bytes, dls_stream_t stream);
+
+/* Device staging bytes dls_compress_host needs: the input field, the stream
+ * bound and the workspace, each 256-byte aligned.  0 if parameters are invalid. */
+size_t dls_host_staging_size(const dls_params* p);
+
+/* End-to-end compression of a HOST field (host in, host stream out): copies
+ * h_in to the device, runs dls_compress, copies the stream back to h_out.
+ * Pinned host memory (cudaHostAlloc) gives full copy bandwidth; pageable
+ * memory works but is slower.  d_staging: staging_bytes >= dls_host_staging_size(p),
+ * 256-byte aligned, owned by the caller.  out_cap bounds the host output.
+ * Synchronizes `stream`; *out_bytes as in dls_compress. */
+int dls_compress_host(const dls_params* p, const void* h_in, void* h_out, size_t out_cap, size_t* out_bytes,
+                      void* d_staging, size_t staging_bytes, dls_stream_t stream);
+
+/* Decompress a device stream into a device field (Sec. 2.6, Algorithm 2).
+ * d_out must hold nvars * nx*ny*nz*nt values of the stream's dtype; blocks
+ * outside the stream's block range are left untouched.  Reads the header
+ * with one synchronous copy and synchronizes `stream` at the end to report
+ * DLS_ERR_CORRUPT. */
+int dls_decompress(const void* d_comp, size_t comp_bytes, void* d_out, size_t out_cap,
+                   dls_stream_t stream);
+
+typedef struct {
+  double max_abs_err;        /* max |orig - recon| over all points */
+  int64_t n_over_bound;      /* points whose error exceeds their variable's pointwise bound */
+  double nrmse;              /* 100 ||orig - recon||_2 / ||orig||_2 (Sec. 2.4), all variables */
+  double ratio;              /* raw field bytes / stream bytes */
+  double sum_sq_err, sum_sq; /* FP64 sums behind nrmse */
+  int64_t n_points;
+  int64_t n_blocks, n_raw_blocks, n_corr, n_esc;
+  double mean_rank;          /* over non-raw blocks */
+  int64_t bytes_header, bytes_basis, bytes_coeff, bytes_corr, bytes_esc, bytes_raw;
+  double var_max_abs_err[8]; /* first 8 variables */
+  double var_nrmse[8];
+  int64_t var_over[8];
+  double var_eb[8];          /* resolved bound per variable */
+} dls_report;
+
+/* Verify a reconstruction against the original (Sec. 2.4 metrics) and
+ * describe the stream.  The bound per variable is read from the stream.
+ * Returns DLS_ERR_BOUND_VIOLATED if a pointwise-mode stream has a point over
+ * its bound; *h_out is filled in either case. */
+int dls_verify(const void* d_orig, const void* d_recon, const void* d_comp, size_t comp_bytes,
+               dls_report* h_out, dls_stream_t stream);
+
+/* Stream header as a host struct (reads the header with one synchronous copy). */
+typedef struct {
+  int32_t version, nvars, dtype, eb_type, precision, rank_mode, rank_cap;
+  int64_t dims[4];
+  int32_t block[4];
+  int64_t block_begin, block_end, total_blocks;
+  uint64_t total_bytes;
+  double eb[64], delta[64], step[64];
+} dls_stream_info;
+int dls_stream_info_get(const void* d_comp, size_t comp_bytes, dls_stream_info* h_info);
+
+const char* dls_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,211 @@
+// Internal definitions shared by the CUDA translation units of libdls.
+// Nothing here is visible through the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "../../include/dls.h"
+
+namespace dls {
+
+// ---------------------------------------------------------------- stream format
+// Global header (128 bytes), per-variable table (32 bytes each), u64 offset
+// table (nb + 1 entries, relative to the payload), then 16-byte aligned
+// records.  Layout of a record: see the packer in k_pack.cu.
+constexpr uint32_t kMagic = 0x31534C44u;  // "DLS1"
+constexpr uint32_t kVersion = 1u;
+constexpr int kHdr = 128;
+constexpr int kVarRec = 32;
+constexpr uint32_t kFlagRaw = 1u, kFlagSpatial = 2u, kFlagDense = 4u;
+constexpr double kQmaxF32 = 16777216.0;    // |c/delta| must stay below 2^24 (f32 fields)
+constexpr double kQmaxF64 = 1073741824.0;  // 2^30 (f64 fields)
+constexpr double kKmax = 1048576.0;        // corrections beyond 2^20 steps become escapes
+constexpr int32_t kEscape = INT32_MIN;     // escape marker in the correction workspace
+constexpr int kMaxVars = 64;
+constexpr int kMaxN = 32;                  // largest Gram order
+
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ inline int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+// ---------------------------------------------------------------- plan
+struct Plan {
+  int32_t nvars, dtype, eb_type, rank_cap, precision, rank_mode;
+  int64_t dims[4];
+  int32_t block[4];
+  int64_t nbk[4];          // blocks per axis
+  int64_t nb_total;        // blocks in the field
+  int64_t b0, nb;          // block range processed: [b0, b0 + nb)
+  int64_t K;               // points per variable
+  int64_t P;               // points per timestep (nx*ny*nz)
+  int32_t nmax, lmax;      // largest Gram order / long side over blocks
+  int64_t nmax_full;       // Gram order of a full block
+  int64_t offsets_pos, payload_pos;   // byte positions in the stream
+  int64_t pt_base, pt_count;          // point range of the processed blocks (workspace indexing)
+  double eb_user[kMaxVars];
+};
+
+struct Geom {
+  int32_t v, sx, sy, sz, st, n, side;
+  int64_t x0, y0, z0, t0;
+  int64_t M, T, N, L;
+  int64_t pt_off;          // offset of the block's points in point-ordered workspaces
+};
+
+__host__ __device__ inline Geom block_geom(const Plan& p, int64_t b) {
+  Geom g;
+  int64_t ix = b % p.nbk[0]; b /= p.nbk[0];
+  int64_t iy = b % p.nbk[1]; b /= p.nbk[1];
+  int64_t iz = b % p.nbk[2]; b /= p.nbk[2];
+  int64_t it = b % p.nbk[3]; b /= p.nbk[3];
+  g.v = (int32_t)b;
+  g.x0 = ix * p.block[0]; g.y0 = iy * p.block[1]; g.z0 = iz * p.block[2]; g.t0 = it * p.block[3];
+  int64_t rx = p.dims[0] - g.x0, ry = p.dims[1] - g.y0, rz = p.dims[2] - g.z0, rt = p.dims[3] - g.t0;
+  g.sx = (int32_t)(rx < p.block[0] ? rx : p.block[0]);
+  g.sy = (int32_t)(ry < p.block[1] ? ry : p.block[1]);
+  g.sz = (int32_t)(rz < p.block[2] ? rz : p.block[2]);
+  g.st = (int32_t)(rt < p.block[3] ? rt : p.block[3]);
+  g.M = (int64_t)g.sx * g.sy * g.sz;
+  g.T = g.st;
+  g.N = g.M * g.T;
+  if (g.T <= g.M) { g.side = 0; g.n = (int32_t)g.T; g.L = g.M; }
+  else { g.side = 1; g.n = (int32_t)g.M; g.L = g.T; }
+  // Blocks are ordered (v, t, z, y, x); the points of all earlier blocks are
+  // v*K + t0*P + st*(z0*nx*ny + sz*(y0*nx + sy*x0)).
+  g.pt_off = (int64_t)g.v * p.K + g.t0 * p.P +
+             (int64_t)g.st * (g.z0 * p.dims[0] * p.dims[1] + (int64_t)g.sz * (g.y0 * p.dims[0] + (int64_t)g.sy * g.x0));
+  return g;
+}
+
+// Global index of block element (spatial ls, time lt).
+__host__ __device__ inline int64_t elem_index(const Plan& p, const Geom& g, int64_t ls, int64_t lt) {
+  int64_t lx = ls % g.sx, r = ls / g.sx;
+  int64_t ly = r % g.sy, lz = r / g.sy;
+  return (int64_t)g.v * p.K + (g.t0 + lt) * p.P + (g.z0 + lz) * p.dims[0] * p.dims[1] +
+         (g.y0 + ly) * p.dims[0] + (g.x0 + lx);
+}
+
+// Global index of block-matrix entry A[l][j].
+__host__ __device__ inline int64_t a_index(const Plan& p, const Geom& g, int64_t l, int j) {
+  return g.side == 0 ? elem_index(p, g, l, j) : elem_index(p, g, j, l);
+}
+// Element order inside a block: e = t_local * M + s_local.
+__host__ __device__ inline int64_t a_elem(const Geom& g, int64_t l, int j) {
+  return g.side == 0 ? (int64_t)j * g.M + l : l * g.M + j;
+}
+
+// ---------------------------------------------------------------- per-variable state (device)
+struct VarInfo {
+  double eb_user, eb, delta, step;  // resolved bound, quantization step, correction step
+  double sumsq;                     // sum of squares (NRMSE mode)
+  unsigned long long minkey, maxkey;// ordered keys for min / max (REL_RANGE mode)
+};
+
+// ---------------------------------------------------------------- per-block result
+struct BlockMeta {
+  int32_t r, flags, wk, ib;
+  int32_t ncorr, nesc;
+  int32_t nprobes, rcap;
+  int64_t nbytes;
+  uint8_t wq[kMaxN];
+};
+
+// Status words written by kernels and read by the host after one sync.
+struct Status {
+  unsigned int nonfinite;
+  unsigned int capacity;
+  unsigned int corrupt;
+  unsigned int timeout;
+  unsigned long long total_bytes;
+  unsigned long long pad[5];
+};
+
+// ---------------------------------------------------------------- workspace
+struct Work {
+  BlockMeta* meta;      // nb
+  double* vst;          // nb * nmax * nmax (stored basis, dtype-rounded, n x rcap row-major)
+  int32_t* q;           // point-ordered: block b at pt_off, L x rcap column-major (k*L + l)
+  int32_t* kc;          // point-ordered: block b at pt_off, element order e
+  unsigned long long* offsets;  // nb + 1
+  VarInfo* vars;        // nvars
+  Status* status;
+};
+
+// ordered key for doubles (monotone map to unsigned)
+__host__ __device__ inline unsigned long long dbits(double x) {
+#ifdef __CUDA_ARCH__
+  return (unsigned long long)__double_as_longlong(x);
+#else
+  unsigned long long u;
+  memcpy(&u, &x, 8);
+  return u;
+#endif
+}
+__host__ __device__ inline double bitsd(unsigned long long u) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)u);
+#else
+  double x;
+  memcpy(&x, &u, 8);
+  return x;
+#endif
+}
+__host__ __device__ inline unsigned long long dkey(double x) {
+  unsigned long long u = dbits(x);
+  return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+__host__ __device__ inline double dunkey(unsigned long long k) {
+  return bitsd((k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k);
+}
+
+__device__ __forceinline__ uint32_t zigzag(int32_t v) { return ((uint32_t)v << 1) ^ (uint32_t)(v >> 31); }
+__device__ __forceinline__ int32_t unzigzag(uint32_t z) { return (int32_t)((z >> 1) ^ (0u - (z & 1u))); }
+__host__ __device__ inline int bit_width(uint32_t v) {
+#ifdef __CUDA_ARCH__
+  return 32 - __clz(v);
+#else
+  int b = 0;
+  while (v) { ++b; v >>= 1; }
+  return b;
+#endif
+}
+
+// Record layout arithmetic shared by the size computation and the packer.
+struct RecLayout {
+  int64_t off_wq, off_v, off_q, off_c, off_ei, off_ev, size;
+  int64_t corr_words;
+  int dense;
+};
+__host__ __device__ inline RecLayout rec_layout(int r, int n, int64_t L, int64_t N, int es,
+                                                const uint8_t* wq, int wk, int ib, int64_t ncorr,
+                                                int64_t nesc) {
+  RecLayout o;
+  o.off_wq = 16;
+  o.off_v = o.off_wq + align_up(r, 8);
+  o.off_q = o.off_v + align_up((int64_t)n * r * es, 8);
+  int64_t qwords = 0;
+  for (int c = 0; c < r; ++c) qwords += (L * wq[c] + 31) / 32;
+  int64_t dense_w = (N * wk + 31) / 32, sparse_w = (ncorr * (ib + wk) + 31) / 32;
+  o.dense = (wk > 0) && (dense_w < sparse_w);
+  o.corr_words = wk == 0 ? 0 : (o.dense ? dense_w : sparse_w);
+  o.off_c = o.off_q + align_up(qwords * 4, 8);
+  o.off_ei = o.off_c + align_up(o.corr_words * 4, 8);
+  o.off_ev = o.off_ei + align_up(nesc * 4, 8);
+  o.size = align_up(o.off_ev + align_up(nesc * es, 8), 16);
+  return o;
+}
+__host__ __device__ inline int64_t raw_record_bytes(int64_t N, int es) { return align_up(16 + N * es, 16); }
+
+// ---------------------------------------------------------------- launchers (defined in .cu files)
+int launch_plain_compress(const Plan& p, const void* d_in, const Work& w, cudaStream_t s);
+int launch_scan(const Plan& p, const Work& w, size_t out_cap, void* d_out, cudaStream_t s);
+int launch_pack(const Plan& p, const void* d_in, const Work& w, void* d_out, size_t out_cap, cudaStream_t s);
+int launch_stats_resolve(const Plan& p, const void* d_in, const Work& w, double* partial, cudaStream_t s);
+int stats_partial_doubles(const Plan& p);
+int launch_decode(const Plan& p, const void* d_comp, unsigned long long comp_bytes, void* d_out, Status* st,
+                  cudaStream_t s);
+int launch_verify(const Plan& p, const void* d_orig, const void* d_recon, const void* d_comp,
+                  unsigned long long comp_bytes, double* acc, cudaStream_t s);
+
+}  // namespace dls

@@ -1,0 +1,259 @@
+// Decompression (Sec. 2.6 and Algorithm 2 of arXiv 2601.20113) and
+// verification (Sec. 2.4 metrics).
+//
+// Decode contract: for every point, acc = 0; for k = 0..r-1,
+// acc = fma(chat[l][k], Vst[j][k], acc) in the field dtype, with
+// chat = dtype(q) * dtype(delta).  Then xtilde = fma(dtype(k), dtype(2eb), acc)
+// where the correction k is nonzero, and escaped points take their raw value.
+// One CTA per block; every structural field of a record is validated against
+// the geometry before use.
+#include "dls_internal.cuh"
+
+namespace dls {
+namespace {
+
+constexpr int kDecThreads = 256;
+
+template <typename T> __device__ __forceinline__ T dq(int32_t q, T d);
+template <> __device__ __forceinline__ float dq<float>(int32_t q, float d) { return __fmul_rn(__int2float_rn(q), d); }
+template <> __device__ __forceinline__ double dq<double>(int32_t q, double d) { return __dmul_rn((double)q, d); }
+template <typename T> __device__ __forceinline__ T tf(T a, T b, T c);
+template <> __device__ __forceinline__ float tf<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <> __device__ __forceinline__ double tf<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+template <typename T> __device__ __forceinline__ T from_d(double x);
+template <> __device__ __forceinline__ float from_d<float>(double x) { return __double2float_rn(x); }
+template <> __device__ __forceinline__ double from_d<double>(double x) { return x; }
+
+__device__ __forceinline__ uint32_t get_bits(const uint32_t* w, uint64_t pos, int width) {
+  if (width == 0) return 0;
+  const uint64_t wi = pos >> 5;
+  const int sh = (int)(pos & 31);
+  uint64_t v = w[wi] >> sh;
+  if (sh + width > 32) v |= (uint64_t)w[wi + 1] << (32 - sh);
+  return (uint32_t)(v & (width == 32 ? 0xffffffffull : ((1ull << width) - 1)));
+}
+
+template <typename T, int NM>
+__global__ void __launch_bounds__(kDecThreads) k_decode(Plan P, const uint8_t* __restrict__ comp,
+                                                        unsigned long long comp_bytes, T* __restrict__ out,
+                                                        Status* st) {
+  __shared__ T vst[NM * NM];
+  __shared__ int64_t wbase[NM + 1];
+  __shared__ int bad;
+  const int64_t bi = blockIdx.x;
+  const int tid = threadIdx.x;
+  const Geom g = block_geom(P, P.b0 + bi);
+  const int64_t N = g.N, L = g.L, M = g.M;
+  const int n = g.n;
+  const int es = (int)sizeof(T);
+  const uint64_t* offs = reinterpret_cast<const uint64_t*>(comp + P.offsets_pos);
+  const uint64_t o0 = offs[bi], o1 = offs[bi + 1];
+  if (o1 < o0 + 16 || (uint64_t)P.payload_pos + o1 > comp_bytes || (o0 & 15) != 0) {
+    if (tid == 0) atomicOr(&st->corrupt, 1u);
+    return;
+  }
+  const uint8_t* rec = comp + P.payload_pos + o0;
+  const uint32_t* rec32 = reinterpret_cast<const uint32_t*>(rec);
+  const int r = rec[0], flags = rec[1], wk = rec[2], ib = rec[3];
+  const int64_t ncorr = rec32[1], nesc = rec32[2], nbytes = rec32[3];
+  if (nbytes != (int64_t)(o1 - o0) || nbytes < 16) {
+    if (tid == 0) atomicOr(&st->corrupt, 1u);
+    return;
+  }
+  if (flags & kFlagRaw) {
+    if (16 + N * es > nbytes) {
+      if (tid == 0) atomicOr(&st->corrupt, 1u);
+      return;
+    }
+    const T* vals = reinterpret_cast<const T*>(rec + 16);
+    for (int64_t e = tid; e < N; e += kDecThreads) {
+      const int64_t lt = e / M, ls = e - lt * M;
+      out[elem_index(P, g, ls, lt)] = vals[e];
+    }
+    return;
+  }
+  const int rcap = P.rank_cap < n ? P.rank_cap : n;
+  const uint8_t* wq = rec + 16;
+  if (tid == 0) {
+    bad = 0;
+    if (16 + align_up(r, 8) > nbytes || r > rcap || wk > 32 || ib != bit_width((uint32_t)(N - 1)) || ncorr > N || nesc > N ||
+        (((flags & kFlagSpatial) ? 1 : 0) != g.side))
+      bad = 1;
+    int64_t acc = 0;
+    for (int c = 0; c < r && !bad; ++c) {
+      if (wq[c] > 32) bad = 1;
+      wbase[c] = acc;
+      acc += (L * wq[c] + 31) / 32;
+    }
+    wbase[r] = acc;
+    if (!bad) {
+      const RecLayout lay = rec_layout(r, n, L, N, es, wq, wk, ib, ncorr, nesc);
+      if (lay.size != nbytes || (lay.dense ? 1 : 0) != ((flags & kFlagDense) ? 1 : 0)) bad = 1;
+    }
+  }
+  __syncthreads();
+  if (bad) {
+    if (tid == 0) atomicOr(&st->corrupt, 1u);
+    return;
+  }
+  const RecLayout lay = rec_layout(r, n, L, N, es, wq, wk, ib, ncorr, nesc);
+  const int v = g.v;
+  const double delta = reinterpret_cast<const double*>(comp + kHdr + kVarRec * v)[2];
+  const double step = reinterpret_cast<const double*>(comp + kHdr + kVarRec * v)[3];
+  const T delta_t = from_d<T>(delta), step_t = from_d<T>(step);
+  const T* vin = reinterpret_cast<const T*>(rec + lay.off_v);
+  for (int i = tid; i < n * r; i += kDecThreads) {
+    const int c = i / n, j = i - c * n;
+    vst[j * NM + c] = vin[i];
+  }
+  __syncthreads();
+  const uint32_t* qw = reinterpret_cast<const uint32_t*>(rec + lay.off_q);
+  const uint32_t* cw = reinterpret_cast<const uint32_t*>(rec + lay.off_c);
+  const bool dense = lay.dense && wk > 0;
+  for (int64_t l = tid; l < L; l += kDecThreads) {
+    T ch[NM];
+#pragma unroll
+    for (int c = 0; c < NM; ++c) {
+      if (c < r) {
+        const uint32_t z = get_bits(qw + wbase[c], (uint64_t)l * wq[c], wq[c]);
+        ch[c] = dq<T>(unzigzag(z), delta_t);
+      } else {
+        ch[c] = T(0);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NM; ++j) {
+      if (j < n) {
+        T acc = T(0);
+#pragma unroll
+        for (int c = 0; c < NM; ++c)
+          if (c < r) acc = tf<T>(ch[c], vst[j * NM + c], acc);
+        const int64_t e = a_elem(g, l, j);
+        if (dense) {
+          const int32_t kv = unzigzag(get_bits(cw, (uint64_t)e * wk, wk));
+          if (kv != 0) acc = tf<T>((T)kv, step_t, acc);
+        }
+        out[a_index(P, g, l, j)] = acc;
+      }
+    }
+  }
+  __syncthreads();
+  if (!dense && wk > 0) {
+    for (int64_t i = tid; i < ncorr; i += kDecThreads) {
+      const uint64_t pos = (uint64_t)i * (uint64_t)(ib + wk);
+      const int64_t e = get_bits(cw, pos, ib);
+      const int32_t kv = unzigzag(get_bits(cw, pos + ib, wk));
+      if (e >= N) { atomicOr(&st->corrupt, 1u); continue; }
+      const int64_t lt = e / M, ls = e - lt * M;
+      const int64_t gi = elem_index(P, g, ls, lt);
+      out[gi] = tf<T>((T)kv, step_t, out[gi]);
+    }
+  }
+  __syncthreads();
+  if (nesc > 0) {
+    const uint32_t* ei = reinterpret_cast<const uint32_t*>(rec + lay.off_ei);
+    const T* ev = reinterpret_cast<const T*>(rec + lay.off_ev);
+    for (int64_t i = tid; i < nesc; i += kDecThreads) {
+      const int64_t e = ei[i];
+      if (e >= N) { atomicOr(&st->corrupt, 1u); continue; }
+      const int64_t lt = e / M, ls = e - lt * M;
+      out[elem_index(P, g, ls, lt)] = ev[i];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- verification
+// acc layout (doubles): per variable v (16 doubles): [0] max_abs_err key (as
+// u64), [1] n_over (u64), [2] sum_sq_err, [3] sum_sq; then stream totals at
+// 16*nvars: [0] n_raw, [1] sum rank, [2] n_corr, [3] n_esc, [4] basis bytes,
+// [5] coeff bytes, [6] corr bytes, [7] esc bytes, [8] raw bytes, [9] header bytes.
+template <typename T>
+__global__ void __launch_bounds__(256) k_verify_points(Plan P, const T* __restrict__ a, const T* __restrict__ b,
+                                                       const uint8_t* comp, double* acc) {
+  const int v = blockIdx.y;
+  const double eb = reinterpret_cast<const double*>(comp + kHdr + kVarRec * v)[1];
+  const bool pointwise = P.eb_type != DLS_EB_NRMSE;
+  double mx = 0.0, se = 0.0, sx = 0.0;
+  unsigned long long over = 0;
+  const int64_t base = (int64_t)v * P.K;
+  for (int64_t i = blockIdx.x * 256ll + threadIdx.x; i < P.K; i += (int64_t)gridDim.x * 256) {
+    const double x = (double)a[base + i], y = (double)b[base + i];
+    const double d = fabs(x - y);
+    mx = fmax(mx, d);
+    if (pointwise && d > eb) ++over;
+    se = fma(d, d, se);
+    sx = fma(x, x, sx);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    se += __shfl_xor_sync(0xffffffffu, se, o);
+    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+    over += __shfl_xor_sync(0xffffffffu, over, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    unsigned long long* u = reinterpret_cast<unsigned long long*>(acc + 16 * v);
+    atomicMax(&u[0], dkey(mx));
+    atomicAdd(&u[1], over);
+    atomicAdd(&acc[16 * v + 2], se);
+    atomicAdd(&acc[16 * v + 3], sx);
+  }
+}
+
+__global__ void k_verify_stream(Plan P, const uint8_t* comp, unsigned long long comp_bytes, int es, double* acc) {
+  const int64_t bi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (bi >= P.nb) return;
+  const Geom g = block_geom(P, P.b0 + bi);
+  const uint64_t* offs = reinterpret_cast<const uint64_t*>(comp + P.offsets_pos);
+  const uint64_t o0 = offs[bi], o1 = offs[bi + 1];
+  if (o1 < o0 + 16 || (uint64_t)P.payload_pos + o1 > comp_bytes || (o0 & 15) != 0) return;
+  const uint8_t* rec = comp + P.payload_pos + o0;
+  const uint32_t* rec32 = reinterpret_cast<const uint32_t*>(rec);
+  double* t = acc + 16 * P.nvars;
+  const int r = rec[0], flags = rec[1];
+  if (!(flags & kFlagRaw) && (r > kMaxN || 16 + align_up(r, 8) > (int64_t)(o1 - o0))) return;
+  if (flags & kFlagRaw) {
+    atomicAdd(&t[0], 1.0);
+    atomicAdd(&t[8], (double)rec32[3]);
+    return;
+  }
+  const RecLayout lay = rec_layout(r, g.n, g.L, g.N, es, rec + 16, rec[2], rec[3], rec32[1], rec32[2]);
+  atomicAdd(&t[1], (double)r);
+  atomicAdd(&t[2], (double)rec32[1]);
+  atomicAdd(&t[3], (double)rec32[2]);
+  atomicAdd(&t[4], (double)(lay.off_q - lay.off_v));
+  atomicAdd(&t[5], (double)(lay.off_c - lay.off_q));
+  atomicAdd(&t[6], (double)(lay.off_ei - lay.off_c));
+  atomicAdd(&t[7], (double)(lay.size - lay.off_ei));
+  atomicAdd(&t[9], (double)lay.off_v);
+}
+
+}  // namespace
+
+int launch_decode(const Plan& p, const void* d_comp, unsigned long long comp_bytes, void* d_out,
+                        Status* st, cudaStream_t s) {
+  if (p.nb == 0) return DLS_OK;
+  const unsigned grid = (unsigned)p.nb;
+  const uint8_t* c = (const uint8_t*)d_comp;
+  if (p.dtype == DLS_F32) {
+    if (p.nmax <= 16) k_decode<float, 16><<<grid, kDecThreads, 0, s>>>(p, c, comp_bytes, (float*)d_out, st);
+    else k_decode<float, 32><<<grid, kDecThreads, 0, s>>>(p, c, comp_bytes, (float*)d_out, st);
+  } else {
+    if (p.nmax <= 16) k_decode<double, 16><<<grid, kDecThreads, 0, s>>>(p, c, comp_bytes, (double*)d_out, st);
+    else k_decode<double, 32><<<grid, kDecThreads, 0, s>>>(p, c, comp_bytes, (double*)d_out, st);
+  }
+  return cudaGetLastError() == cudaSuccess ? DLS_OK : DLS_ERR_CUDA;
+}
+
+int launch_verify(const Plan& p, const void* d_orig, const void* d_recon, const void* d_comp,
+                  unsigned long long comp_bytes, double* acc, cudaStream_t s) {
+  dim3 grid(1024, p.nvars);
+  if (p.dtype == DLS_F32)
+    k_verify_points<float><<<grid, 256, 0, s>>>(p, (const float*)d_orig, (const float*)d_recon, (const uint8_t*)d_comp, acc);
+  else
+    k_verify_points<double><<<grid, 256, 0, s>>>(p, (const double*)d_orig, (const double*)d_recon, (const uint8_t*)d_comp, acc);
+  if (p.nb > 0)
+    k_verify_stream<<<(unsigned)cdiv(p.nb, 256), 256, 0, s>>>(p, (const uint8_t*)d_comp, comp_bytes, p.dtype == DLS_F32 ? 4 : 8, acc);
+  return cudaGetLastError() == cudaSuccess ? DLS_OK : DLS_ERR_CUDA;
+}
+
+}  // namespace dls

@@ -1,0 +1,236 @@
+"""Thin Python binding of the libdls C ABI (include/dls.h).
+
+Argument marshalling only: torch tensors supply device memory and the current
+CUDA stream; every step of compression, decompression and verification runs
+in the library's CUDA kernels.  If libdls.so is not built this module raises;
+there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+F32, F64 = 0, 1
+EB_ABS, EB_REL_RANGE, EB_NRMSE = 0, 1, 2
+PREC_FP64, PREC_TF32X3, PREC_BF16X3 = 0, 1, 2
+RANK_SEARCH, RANK_LEARNED = 0, 1
+OK = 0
+ERR = {-1: "INVALID_ARG", -2: "CAPACITY", -3: "NONFINITE", -4: "CORRUPT", -5: "CUDA", -6: "TIMEOUT",
+       -7: "BOUND_VIOLATED", -8: "WORKSPACE", -9: "NO_MODEL"}
+
+
+class DlsError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {ERR.get(status, status)} ({status})")
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("nvars", C.c_int32),
+        ("dims", C.c_int64 * 4),
+        ("block", C.c_int32 * 4),
+        ("dtype", C.c_int32),
+        ("eb_type", C.c_int32),
+        ("eb", C.POINTER(C.c_double)),
+        ("rank_cap", C.c_int32),
+        ("precision", C.c_int32),
+        ("rank_mode", C.c_int32),
+        ("block_begin", C.c_int64),
+        ("block_end", C.c_int64),
+    ]
+
+
+class Report(C.Structure):
+    _fields_ = [
+        ("max_abs_err", C.c_double), ("n_over_bound", C.c_int64), ("nrmse", C.c_double), ("ratio", C.c_double),
+        ("sum_sq_err", C.c_double), ("sum_sq", C.c_double), ("n_points", C.c_int64),
+        ("n_blocks", C.c_int64), ("n_raw_blocks", C.c_int64), ("n_corr", C.c_int64), ("n_esc", C.c_int64),
+        ("mean_rank", C.c_double),
+        ("bytes_header", C.c_int64), ("bytes_basis", C.c_int64), ("bytes_coeff", C.c_int64),
+        ("bytes_corr", C.c_int64), ("bytes_esc", C.c_int64), ("bytes_raw", C.c_int64),
+        ("var_max_abs_err", C.c_double * 8), ("var_nrmse", C.c_double * 8), ("var_over", C.c_int64 * 8),
+        ("var_eb", C.c_double * 8),
+    ]
+
+
+class StreamInfo(C.Structure):
+    _fields_ = [
+        ("version", C.c_int32), ("nvars", C.c_int32), ("dtype", C.c_int32), ("eb_type", C.c_int32),
+        ("precision", C.c_int32), ("rank_mode", C.c_int32), ("rank_cap", C.c_int32),
+        ("dims", C.c_int64 * 4), ("block", C.c_int32 * 4),
+        ("block_begin", C.c_int64), ("block_end", C.c_int64), ("total_blocks", C.c_int64),
+        ("total_bytes", C.c_uint64),
+        ("eb", C.c_double * 64), ("delta", C.c_double * 64), ("step", C.c_double * 64),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+# Every symbol include/dls.h declares, with its ctypes signature.
+_SIGS = {
+    "dls_compress_bound": (C.c_size_t, [C.POINTER(Params)]),
+    "dls_workspace_size": (C.c_size_t, [C.POINTER(Params)]),
+    "dls_compress": (C.c_int, [C.POINTER(Params), C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t),
+                               C.c_void_p, C.c_size_t, C.c_void_p]),
+    "dls_host_staging_size": (C.c_size_t, [C.POINTER(Params)]),
+    "dls_compress_host": (C.c_int, [C.POINTER(Params), C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t),
+                                    C.c_void_p, C.c_size_t, C.c_void_p]),
+    "dls_decompress": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "dls_verify": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(Report), C.c_void_p]),
+    "dls_stream_info_get": (C.c_int, [C.c_void_p, C.c_size_t, C.POINTER(StreamInfo)]),
+    "dls_status_string": (C.c_char_p, [C.c_int]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Loads libdls.so; raises if it has not been built (no CPU fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError(f"libdls.so is not built ({_build.LIB}); run __graft_entry__.build()")
+            L = C.CDLL(_build.LIB)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def status_string(st: int) -> str:
+    return lib().dls_status_string(st).decode()
+
+
+def _dtype_code(t: torch.dtype) -> int:
+    if t == torch.float32:
+        return F32
+    if t == torch.float64:
+        return F64
+    raise TypeError(f"unsupported field dtype {t}")
+
+
+def make_params(shape, dtype, block, eb, eb_type=EB_ABS, rank_cap=32, precision=PREC_FP64,
+                rank_mode=RANK_SEARCH, block_begin=0, block_end=-1):
+    """shape = (nvars, nt, nz, ny, nx) of the field tensor."""
+    nvars, nt, nz, ny, nx = shape
+    p = Params()
+    p.nvars = nvars
+    for a, d in enumerate((nx, ny, nz, nt)):
+        p.dims[a] = int(d)
+    for a, b in enumerate(block):
+        p.block[a] = int(b)
+    p.dtype = dtype if isinstance(dtype, int) else _dtype_code(dtype)
+    p.eb_type = eb_type
+    ebv = [float(eb)] * nvars if not hasattr(eb, "__len__") else [float(e) for e in eb]
+    arr = (C.c_double * nvars)(*ebv)
+    p.eb = C.cast(arr, C.POINTER(C.c_double))
+    p._eb_keep = arr
+    p.rank_cap = rank_cap
+    p.precision = precision
+    p.rank_mode = rank_mode
+    p.block_begin = block_begin
+    p.block_end = block_end
+    return p
+
+
+def compress_bound(p: Params) -> int:
+    return lib().dls_compress_bound(C.byref(p))
+
+
+def workspace_size(p: Params) -> int:
+    return lib().dls_workspace_size(C.byref(p))
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def compress_into(p: Params, field: torch.Tensor, out: torch.Tensor, workspace: torch.Tensor, stream=None):
+    """Raw call: returns (status, nbytes)."""
+    nb = C.c_size_t(0)
+    st = lib().dls_compress(C.byref(p), C.c_void_p(field.data_ptr()), C.c_void_p(out.data_ptr()), out.numel(),
+                            C.byref(nb), C.c_void_p(workspace.data_ptr()), workspace.numel(), _stream(stream))
+    return st, nb.value
+
+
+def compress(field: torch.Tensor, block, eb, eb_type=EB_ABS, rank_cap=32, precision=PREC_FP64,
+             rank_mode=RANK_SEARCH, block_begin=0, block_end=-1):
+    """Compresses a CUDA field (nvars, nt, nz, ny, nx); returns a uint8 CUDA tensor."""
+    if not field.is_cuda or not field.is_contiguous() or field.dim() != 5:
+        raise ValueError("field must be a contiguous CUDA tensor (nvars, nt, nz, ny, nx)")
+    p = make_params(tuple(field.shape), field.dtype, block, eb, eb_type, rank_cap, precision, rank_mode,
+                    block_begin, block_end)
+    cap = compress_bound(p)
+    ws = workspace_size(p)
+    if cap == 0 or ws == 0:
+        raise DlsError(-1, "dls_compress")
+    out = torch.empty(cap, dtype=torch.uint8, device=field.device)
+    work = torch.empty(ws, dtype=torch.uint8, device=field.device)
+    st, nb = compress_into(p, field, out, work)
+    if st != OK:
+        raise DlsError(st, "dls_compress")
+    return out[:nb]
+
+
+def host_staging_size(p: Params) -> int:
+    return lib().dls_host_staging_size(C.byref(p))
+
+
+def compress_host_into(p: Params, h_field: torch.Tensor, h_out: torch.Tensor, staging: torch.Tensor, stream=None):
+    """End-to-end call on host tensors (pinned for full bandwidth): (status, nbytes)."""
+    nb = C.c_size_t(0)
+    st = lib().dls_compress_host(C.byref(p), C.c_void_p(h_field.data_ptr()), C.c_void_p(h_out.data_ptr()),
+                                 h_out.numel(), C.byref(nb), C.c_void_p(staging.data_ptr()), staging.numel(),
+                                 _stream(stream))
+    return st, nb.value
+
+
+def stream_info(comp: torch.Tensor) -> StreamInfo:
+    info = StreamInfo()
+    st = lib().dls_stream_info_get(C.c_void_p(comp.data_ptr()), comp.numel(), C.byref(info))
+    if st != OK:
+        raise DlsError(st, "dls_stream_info_get")
+    return info
+
+
+def decompress_into(comp: torch.Tensor, out: torch.Tensor, stream=None) -> int:
+    return lib().dls_decompress(C.c_void_p(comp.data_ptr()), comp.numel(), C.c_void_p(out.data_ptr()),
+                                out.numel() * out.element_size(), _stream(stream))
+
+
+def decompress(comp: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+    if out is None:
+        info = stream_info(comp)
+        dt = torch.float32 if info.dtype == F32 else torch.float64
+        nx, ny, nz, nt = (info.dims[a] for a in range(4))
+        out = torch.zeros((info.nvars, nt, nz, ny, nx), dtype=dt, device=comp.device)
+    st = decompress_into(comp, out)
+    if st != OK:
+        raise DlsError(st, "dls_decompress")
+    return out
+
+
+def verify(orig: torch.Tensor, recon: torch.Tensor, comp: torch.Tensor) -> dict:
+    rep = Report()
+    st = lib().dls_verify(C.c_void_p(orig.data_ptr()), C.c_void_p(recon.data_ptr()), C.c_void_p(comp.data_ptr()),
+                          comp.numel(), C.byref(rep), _stream(None))
+    if st not in (OK, -7):
+        raise DlsError(st, "dls_verify")
+    d = {name: getattr(rep, name) for name, _ in Report._fields_}
+    for k in ("var_max_abs_err", "var_nrmse", "var_over", "var_eb"):
+        d[k] = list(d[k])
+    d["status"] = st
+    return d

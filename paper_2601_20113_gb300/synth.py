@@ -38,11 +38,14 @@ def _wavevectors(rng, count, kmax):
     return np.array(ks, dtype=np.int64)
 
 
-def _modes(rng, dims, count, kmax, period, device):
+def _modes(rng, dims, count, kmax, period, device, window=None):
     """sum_k a_k sin(2 pi k.x + omega_k t + phi_k), a_k ~ |k|^(-5/3), unit RMS.
 
-    Evaluated per timestep as a complex separable product (one small matmul)."""
+    Evaluated per timestep as a complex separable product (one small matmul).
+    `window` = ((x0, y0, z0, t0), (wx, wy, wz, wt)) evaluates a sub-box of the
+    same field."""
     nx, ny, nz, nt = dims
+    (x0, y0, z0, t0), (wx, wy, wz, wt) = window if window else ((0, 0, 0, 0), dims)
     ks = _wavevectors(rng, count, kmax)
     kn = np.sqrt((ks * ks).sum(1)).astype(np.float64)
     amp = kn ** (-5.0 / 3.0)
@@ -54,20 +57,20 @@ def _modes(rng, dims, count, kmax, period, device):
     kx = torch.tensor(ks[:, 0], dtype=torch.float64, device=device)
     ky = torch.tensor(ks[:, 1], dtype=torch.float64, device=device)
     kz = torch.tensor(ks[:, 2], dtype=torch.float64, device=device)
-    ix = torch.arange(nx, dtype=torch.float64, device=device)
-    iy = torch.arange(ny, dtype=torch.float64, device=device)
-    iz = torch.arange(nz, dtype=torch.float64, device=device)
-    EX = torch.polar(torch.ones(count, nx, dtype=torch.float64, device=device), 2 * math.pi * kx[:, None] * ix[None] / nx)
-    EY = torch.polar(torch.ones(count, ny, dtype=torch.float64, device=device), 2 * math.pi * ky[:, None] * iy[None] / ny)
-    EZ = torch.polar(torch.ones(count, nz, dtype=torch.float64, device=device), 2 * math.pi * kz[:, None] * iz[None] / nz)
-    B = (EZ[:, :, None] * EY[:, None, :]).reshape(count, nz * ny)      # (K, nz*ny)
+    ix = torch.arange(x0, x0 + wx, dtype=torch.float64, device=device)
+    iy = torch.arange(y0, y0 + wy, dtype=torch.float64, device=device)
+    iz = torch.arange(z0, z0 + wz, dtype=torch.float64, device=device)
+    EX = torch.polar(torch.ones(count, wx, dtype=torch.float64, device=device), 2 * math.pi * kx[:, None] * ix[None] / nx)
+    EY = torch.polar(torch.ones(count, wy, dtype=torch.float64, device=device), 2 * math.pi * ky[:, None] * iy[None] / ny)
+    EZ = torch.polar(torch.ones(count, wz, dtype=torch.float64, device=device), 2 * math.pi * kz[:, None] * iz[None] / nz)
+    B = (EZ[:, :, None] * EY[:, None, :]).reshape(count, wz * wy)      # (K, wz*wy)
     a = torch.tensor(amp, dtype=torch.float64, device=device)
     ph = torch.tensor(phase, dtype=torch.float64, device=device)
     om = torch.tensor(omega, dtype=torch.float64, device=device)
-    for t in range(nt):
-        w = torch.polar(a, om * t + ph).to(cd)                         # (K,)
-        U = (B * w[:, None]).transpose(0, 1) @ EX                      # (nz*ny, nx)
-        yield t, U.imag.reshape(nz, ny, nx)
+    for t in range(wt):
+        w = torch.polar(a, om * (t0 + t) + ph).to(cd)                  # (K,)
+        U = (B * w[:, None]).transpose(0, 1) @ EX                      # (wz*wy, wx)
+        yield t, U.imag.reshape(wz, wy, wx)
 
 
 def _vortices(rng, dims, count, wrange, vrange, arange, dt, device, three_d=True):
@@ -114,16 +117,19 @@ def vortex2d(nx=64, ny=64, nt=32, seed=1, count=6, noise=1e-4, device="cpu", dty
 
 
 def modes3d(nx=256, ny=256, nz=256, nt=64, seed=2, count=64, kmax=8, period=64, noise=1e-3,
-            device="cpu", dtype=torch.float32):
+            device="cpu", dtype=torch.float32, window=None):
     """3-D field: `count` integer wavevectors with 1 <= |k| <= kmax, amplitudes
     ~ |k|^(-5/3), random phases, temporal frequencies U[0,2] cycles per 64
-    steps, normalised to unit RMS, plus N(0, noise^2)."""
+    steps, normalised to unit RMS, plus N(0, noise^2).  With `window` =
+    ((x0, y0, z0, t0), (wx, wy, wz, wt)) only that sub-box is evaluated (same
+    modes; its noise is drawn for the window alone)."""
     rng = _rng(seed)
-    out = torch.empty((1, nt, nz, ny, nx), dtype=dtype, device=device)
+    wx, wy, wz, wt = window[1] if window else (nx, ny, nz, nt)
+    out = torch.empty((1, wt, wz, wy, wx), dtype=dtype, device=device)
     rngt = torch.Generator(device=device)
-    rngt.manual_seed(int(seed) * 7919 + 2)
-    for t, f in _modes(rng, (nx, ny, nz, nt), count, kmax, period, device):
-        nz_ = torch.randn((nz, ny, nx), generator=rngt, dtype=torch.float64, device=device)
+    rngt.manual_seed(int(seed) * 7919 + 2 + (0 if window is None else 1 + hash(tuple(window[0])) % 1000003))
+    for t, f in _modes(rng, (nx, ny, nz, nt), count, kmax, period, device, window):
+        nz_ = torch.randn((wz, wy, wx), generator=rngt, dtype=torch.float64, device=device)
         out[0, t] = (f + noise * nz_).to(dtype)
     return out
 
