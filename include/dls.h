@@ -112,6 +112,24 @@ size_t dls_host_staging_size(const dls_params* p);
 int dls_compress_host(const dls_params* p, const void* h_in, void* h_out, size_t out_cap, size_t* out_bytes,
                       void* d_staging, size_t staging_bytes, dls_stream_t stream);
 
+/* Compression that allocates nothing (the paper has no counterpart: this is a
+ * library convenience).  For callers that cannot allocate device memory when
+ * they compress, e.g. an in-situ hook inside a simulation whose memory pools
+ * already hold the whole device, or code running where CUDA allocation calls
+ * are not allowed.  Same arguments and result as dls_compress, without the
+ * workspace: the workspace is a 64 MiB device array inside this library.
+ *   - Fields whose dls_workspace_size(p) exceeds 64 MiB are rejected with
+ *     DLS_ERR_WORKSPACE (float32 blocks of 16^3 x 16 need about 8.2 bytes of
+ *     workspace per point: up to roughly 8 million points).
+ *   - The first call on each device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - Every call on a device shares the array: calls that overlap on the GPU
+ *     (different streams or host threads) race and must be serialised by the
+ *     caller.  Each call clears what it needs and overwrites the rest.
+ *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call. */
+int dls_compress_noalloc(const dls_params* p, const void* d_in, void* d_out, size_t out_cap,
+                         size_t* out_bytes, dls_stream_t stream);
+
 /* Decompress a device stream into a device field (Sec. 2.6, Algorithm 2).
  * d_out must hold nvars * nx*ny*nz*nt values of the stream's dtype; blocks
  * outside the stream's block range are left untouched.  Reads the header

@@ -82,6 +82,8 @@ _SIGS = {
     "dls_host_staging_size": (C.c_size_t, [C.POINTER(Params)]),
     "dls_compress_host": (C.c_int, [C.POINTER(Params), C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t),
                                     C.c_void_p, C.c_size_t, C.c_void_p]),
+    "dls_compress_noalloc": (C.c_int, [C.POINTER(Params), C.c_void_p, C.c_void_p, C.c_size_t,
+                                       C.POINTER(C.c_size_t), C.c_void_p]),
     "dls_decompress": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t, C.c_void_p]),
     "dls_verify": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(Report), C.c_void_p]),
     "dls_stream_info_get": (C.c_int, [C.c_void_p, C.c_size_t, C.POINTER(StreamInfo)]),
@@ -183,6 +185,15 @@ def compress(field: torch.Tensor, block, eb, eb_type=EB_ABS, rank_cap=32, precis
     if st != OK:
         raise DlsError(st, "dls_compress")
     return out[:nb]
+
+
+def compress_noalloc_into(p: Params, field: torch.Tensor, out: torch.Tensor, stream=None):
+    """Compression with the library's built-in 64 MiB workspace, for callers
+    that cannot allocate device memory: (status, nbytes)."""
+    nb = C.c_size_t(0)
+    st = lib().dls_compress_noalloc(C.byref(p), C.c_void_p(field.data_ptr()), C.c_void_p(out.data_ptr()),
+                                    out.numel(), C.byref(nb), _stream(stream))
+    return st, nb.value
 
 
 def host_staging_size(p: Params) -> int:
