@@ -211,7 +211,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dims", default=None, help="nx,ny,nz,nt override (profiling on a small case)")
     args = ap.parse_args()
+    if args.dims:
+        global DIMS
+        DIMS = tuple(int(v) for v in args.dims.split(","))
     if args.impl == "reference":
         return run_reference(args)
 
