@@ -35,6 +35,16 @@ BLOCK = (16, 16, 16, 16)
 REL_BOUND = 1e-3
 RANK_CAP = 16
 SEED = 2
+# (precision, rank mode) of each form
+FORMS = {"plain": (0, 0), "fp32": (3, 0), "learned": (3, 1), "tail": (3, 2)}
+FORM_TEXT = {
+    "plain": "plain FP64 (Gram, Jacobi, projection, bisection, correction in FP64)",
+    "fp32": "FP32 products, FP32 Jacobi + FP64 refinement, bisection on E(r) for all r, FP64-semantics decisions",
+    "learned": "FP32 products, FP32 Jacobi + FP64 refinement, MLP-predicted rank checked exactly (bisection "
+               "fallback), FP64-semantics decisions",
+    "tail": "FP32 products, FP32 Jacobi + FP64 refinement, eigenvalue-tail rank estimate checked exactly "
+            "(bisection fallback), FP64-semantics decisions",
+}
 
 
 def _peaks():
@@ -197,10 +207,10 @@ def run_reference(args):
     return 0
 
 
-def _config():
+def _config(form="learned"):
     return {"workload": "modes3d 256^3 x 64 float32 (4 GiB), 64 modes |k|<=8, k^-5/3, N(0,1e-3^2) noise, "
                         "blocks 16^3x16 (16384), abs bound 1e-3 x range, rank cap 16",
-            "form": "plain FP64 (Gram, Jacobi, projection, bisection, correction in FP64)",
+            "form": FORM_TEXT[form],
             "l2": "inputs 4 GiB > 129 MB L2 (no flush)"}
 
 
@@ -212,6 +222,8 @@ def main():
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dims", default=None, help="nx,ny,nz,nt override (profiling on a small case)")
+    ap.add_argument("--form", default="learned", choices=sorted(FORMS))
+    ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP64 form beside")
     args = ap.parse_args()
     if args.dims:
         global DIMS
@@ -238,7 +250,14 @@ def main():
     field = make_field(dev, seed=SEED + 1000 * rank)
     rng = float(field.max() - field.min())
     eb = REL_BOUND * rng
-    p = dls.make_params(tuple(field.shape), torch.float32, BLOCK, eb, dls.EB_ABS, RANK_CAP)
+    if args.form == "learned":
+        from paper_2601_20113_gb300 import train_rank
+        if not os.path.exists(train_rank.DEFAULT_MODEL):
+            raise SystemExit("learned form needs paper_2601_20113_gb300/rank_model.bin (train_rank.py)")
+        dls.set_rank_model(train_rank.load_model())
+    form = FORMS[args.form]
+    p = dls.make_params(tuple(field.shape), torch.float32, BLOCK, eb, dls.EB_ABS, RANK_CAP,
+                        precision=form[0], rank_mode=form[1])
     cap = dls.compress_bound(p)
     out = torch.empty(cap, dtype=torch.uint8, device=dev)
     ws = torch.empty(dls.workspace_size(p), dtype=torch.uint8, device=dev)
@@ -305,7 +324,8 @@ def main():
     line = {
         "metric": METRIC, "value": in_bytes * world / (ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _config(),
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.form == "plain" else "f32+f64",
+        "data": "synthetic", "config": _config(args.form),
         "ratio": ratio, "max_abs_err": rep["max_abs_err"], "eb": eb, "n_over_bound": rep["n_over_bound"],
         "mean_rank": rep["mean_rank"], "decompress_gbs": in_bytes / (dms * 1e-3) / 1e9,
         "roofline": {"bound": "hbm", "achieved": in_bytes / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
@@ -316,6 +336,21 @@ def main():
         "gpu_launches": 4 * args.steps,
         "clocks": clk,
     }
+    if args.form != "plain" and not args.no_plain:
+        pp = dls.make_params(tuple(field.shape), torch.float32, BLOCK, eb, dls.EB_ABS, RANK_CAP)
+        wsp = torch.empty(dls.workspace_size(pp), dtype=torch.uint8, device=dev)
+        st, pnb = dls.compress_into(pp, field, out, wsp)
+        assert st == 0
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        st, pnb = dls.compress_into(pp, field, out, wsp)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        pms = p0.elapsed_time(p1)
+        line["plain_fp64"] = {"value": in_bytes / (pms * 1e-3) / 1e9, "unit": "GB/s", "ratio": in_bytes / pnb,
+                              "ms_per_step": pms, "speedup_of_headline": pms / ms}
+        del wsp
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         fcpu = field[:, :16, :16].cpu().numpy()
         v, cores, desc, el = oracle_sample_bench(fcpu, eb)

@@ -45,15 +45,25 @@ enum { DLS_F32 = 0, DLS_F64 = 1 };
  * paper's global L2 target in percent, eps = eps_t ||u|| / 100 (Sec. 2.4);
  * no pointwise correction in that mode. */
 enum { DLS_EB_ABS = 0, DLS_EB_REL_RANGE = 1, DLS_EB_NRMSE = 2 };
-/* Arithmetic of the Gram and projection products.  FP64: plain double
- * precision everywhere.  TF32X3 / BF16X3: split-precision products on the
- * tensor cores with FP32 accumulation (3 terms), eigensolve, residual and
- * bound checks keep FP64 semantics. */
-enum { DLS_PREC_FP64 = 0, DLS_PREC_TF32X3 = 1, DLS_PREC_BF16X3 = 2 };
-/* Rank selection.  SEARCH: bisection of Algorithm 1.  LEARNED: a small MLP
- * predicts the rank, which is accepted only if it is the smallest passing
- * rank around the prediction; otherwise the bisection decides. */
-enum { DLS_RANK_SEARCH = 0, DLS_RANK_LEARNED = 1 };
+/* Arithmetic of the Gram and projection products.
+ *   FP64:   double precision everywhere (the plain form).
+ *   FP32:   FP32 products on the CUDA cores with FP32 accumulation; FP32
+ *           Jacobi refined to FP64 accuracy; every stored decision (quantized
+ *           coefficient, rank test, correction, escape) keeps FP64 semantics.
+ *   TF32X3 / BF16X3: as FP32 with the Gram and projection products on the
+ *           tensor cores as 3-term split products (reserved: rejected with
+ *           DLS_ERR_INVALID_ARG by builds without those kernels).
+ * Non-FP64 modes apply to float32 fields with a Gram order <= 16; other
+ * fields take the FP64 form whatever the mode. */
+enum { DLS_PREC_FP64 = 0, DLS_PREC_TF32X3 = 1, DLS_PREC_BF16X3 = 2, DLS_PREC_FP32 = 3 };
+/* Rank selection.  SEARCH: bisection of Algorithm 1.  LEARNED: the loaded
+ * block-rank MLP (dls_set_rank_model) predicts the rank r; it is accepted
+ * only if pass(r) holds and pass(r-1) does not (the smallest passing rank next
+ * to the prediction), otherwise the bisection decides.  TAIL: as LEARNED with
+ * the prediction taken from the eigenvalue tails, sum_{i>=r} lambda_i plus a
+ * uniform quantization-noise estimate (a baseline without the network).
+ * LEARNED and TAIL apply to the non-FP64 precision modes. */
+enum { DLS_RANK_SEARCH = 0, DLS_RANK_LEARNED = 1, DLS_RANK_TAIL = 2 };
 
 enum {
   DLS_OK = 0,
@@ -98,6 +108,26 @@ size_t dls_workspace_size(const dls_params* p);
  * Synchronizes `stream` once to read the stream size. */
 int dls_compress(const dls_params* p, const void* d_in, void* d_out, size_t out_cap,
                  size_t* out_bytes, void* d_workspace, size_t ws_bytes, dls_stream_t stream);
+
+/* Reusable compression plan for fixed parameters and buffers (a time series
+ * of snapshots written into the same buffers, for example).  Creation
+ * validates like dls_compress, picks the occupancy variant of the per-block
+ * kernel by timing each on the real data (two full compressions per variant;
+ * the choice is cached as JSON lines in the file named by the environment
+ * variable DLS_AUTOTUNE_CACHE when set), then captures the whole compression
+ * (status reset, bound resolution, the persistent per-block kernel over every
+ * block of every variable, scan + header, record placement, status readback)
+ * in one CUDA graph.  Executing replays the graph and synchronizes `stream`.
+ * The plan owns a small pinned status buffer; buffers stay owned by the
+ * caller and must outlive the plan.  Creation writes d_out and d_workspace. */
+typedef struct dls_plan dls_plan;
+int dls_plan_create(const dls_params* p, const void* d_in, void* d_out, size_t out_cap, void* d_workspace,
+                    size_t ws_bytes, dls_stream_t stream, dls_plan** out_plan);
+int dls_plan_execute(dls_plan* plan, size_t* out_bytes, dls_stream_t stream);
+/* Chosen variant (1: one CTA per SM, 2: two) and the two timings in ms (0 if
+ * the choice came from the cache or the form has one variant). */
+int dls_plan_info(const dls_plan* plan, int32_t* variant, float* tune_ms);
+int dls_plan_destroy(dls_plan* plan);
 
 /* Device staging bytes dls_compress_host needs: the input field, the stream
  * bound and the workspace, each 256-byte aligned.  0 if parameters are invalid. */
@@ -160,6 +190,70 @@ typedef struct {
  * its bound; *h_out is filled in either case. */
 int dls_verify(const void* d_orig, const void* d_recon, const void* d_comp, size_t comp_bytes,
                dls_report* h_out, dls_stream_t stream);
+
+/* Stage entry points of the mixed-precision form, for exact tests of its
+ * FP64-semantics decisions.  Device arrays of n elements.
+ * dls_stage_quantize: q[i] = rint((double)c[i] / delta) (ties to even), the
+ *   quantizer of Sec. 2.5's coefficients; ovf[i] = 1 where |c/delta| >= 2^24.
+ * dls_stage_correct: the pointwise correction of a reconstruction xh against
+ *   x with bound eb: k[i] = rint((x - xh) / 2eb) evaluated in FP64, or
+ *   INT32_MIN where the point escapes (|x - xtilde| > eb or |k| > 2^20). */
+int dls_stage_quantize(const float* d_c, int64_t n, double delta, int32_t* d_q, int32_t* d_ovf,
+                       dls_stream_t stream);
+int dls_stage_correct(const float* d_x, const float* d_xh, int64_t n, double eb, int32_t* d_k,
+                      dls_stream_t stream);
+
+/* Block-rank MLP (not in the paper): 32 block features -> 64 -> 64 -> 1, ReLU,
+ * BF16 weights with FP32 accumulation.  Parameters are DLS_MLP_NPARAM floats:
+ * [mu 32][sigma 32][W1 64x32][b1 64][W2 64x64][b2 64][W3 64][b3 1], W row-major
+ * (output x input); mu and sigma standardise the features (not trained).
+ * Features of a block (computed in FP32/FP64 from its data and eigenvalues):
+ *   0: log10(sum lambda / eps_l^2); 1..16: log10(sum_{i>=r} lambda_i / eps_l^2),
+ *   r = 0..15; 17..24: sqrt(lambda_i / lambda_0), i = 1..8; 25: temporal and
+ *   26: x gradient energy over ||X||^2; 27: log10(L delta^2 / 12 / eps_l^2);
+ *   28: log10(value range / delta); 29: block size / 65536; 30: n / 16;
+ *   31: the eigenvalue-tail rank estimate. */
+#define DLS_MLP_NPARAM 6401
+#define DLS_MLP_NFEAT 32
+
+/* Loads the rank model on the current device (host array of DLS_MLP_NPARAM
+ * floats; sigma entries must be > 0).  Weights are rounded to BF16. */
+int dls_set_rank_model(const float* h_params, size_t count);
+
+/* Features and exact ranks of every block (rank by the bisection of
+ * Algorithm 1 in the FP32 mode; -1 for blocks stored raw).  d_feat: nb x 32
+ * floats, d_rank: nb int32 (nb = blocks in the parameters' range).  Needs the
+ * workspace dls_workspace_size(p) with p->precision = DLS_PREC_FP32. */
+int dls_block_features(const dls_params* p, const void* d_in, float* d_feat, int32_t* d_rank, void* d_workspace,
+                       size_t ws_bytes, dls_stream_t stream);
+
+/* MLP on n feature rows (d_feat n x 32) -> d_y (n), weights rounded to BF16. */
+int dls_mlp_forward(const float* d_params, const float* d_feat, int64_t n, float* d_y, dls_stream_t stream);
+
+/* Gradient of the mean squared error over one minibatch (1 <= n <= 128):
+ * d_grad (DLS_MLP_NPARAM floats, zero for mu and sigma), d_loss (1 float). */
+int dls_mlp_grad(const float* d_params, const float* d_feat, const float* d_target, int64_t n, float* d_grad,
+                 float* d_loss, dls_stream_t stream);
+
+/* `steps` Adam steps (beta 0.9 / 0.999, eps 1e-8, learning rate lr) on the MSE
+ * of the predicted rank, minibatches of `batch` (<= 128) rows taken in the
+ * order d_order[(s * batch + b) % n_order].  d_params and d_adam (2 x
+ * DLS_MLP_NPARAM floats: first and second moments) are updated in place;
+ * step0 is the number of steps already taken; d_loss (steps floats, may be
+ * NULL) receives each step's minibatch loss.  Runs in one CTA. */
+int dls_mlp_train(float* d_params, float* d_adam, const float* d_feat, const float* d_target, const int32_t* d_order,
+                  int64_t n_order, int32_t steps, int32_t batch, float lr, int32_t step0, float* d_loss,
+                  dls_stream_t stream);
+
+/* Cycle counters of the last compression in this workspace by the
+ * mixed-precision per-block kernel, summed over CTAs, in phase order: Gram
+ * pass, FP32 Jacobi, FP64 refinement, Rayleigh-Ritz step, rank prediction,
+ * encode pass at the predicted rank, exact pass tests, bisection fallback,
+ * record packing; then three counts: blocks whose predicted rank was
+ * accepted, blocks that fell back to the bisection, and FP64 re-evaluations
+ * of E(r) taken because the FP32 estimate could not decide.  count >= 12.
+ * Synchronous copy. */
+int dls_phase_cycles(const dls_params* p, const void* d_workspace, unsigned long long* h_cycles, int32_t count);
 
 /* Stream header as a host struct (reads the header with one synchronous copy). */
 typedef struct {

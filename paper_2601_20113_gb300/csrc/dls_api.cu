@@ -2,8 +2,10 @@
 // launch sequence and status readback.  See include/dls.h for the contract.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
+#include <string>
 #include <vector>
 
 #include "dls_internal.cuh"
@@ -17,7 +19,9 @@ int make_plan(const dls_params* p, Plan* out) {
   if (!p || p->nvars < 1 || p->nvars > kMaxVars || !p->eb) return DLS_ERR_INVALID_ARG;
   if (p->dtype != DLS_F32 && p->dtype != DLS_F64) return DLS_ERR_INVALID_ARG;
   if (p->eb_type < 0 || p->eb_type > 2 || p->rank_cap < 0) return DLS_ERR_INVALID_ARG;
-  if (p->precision < 0 || p->precision > 2 || p->rank_mode < 0 || p->rank_mode > 1) return DLS_ERR_INVALID_ARG;
+  if (p->precision < 0 || p->precision > 3 || p->rank_mode < 0 || p->rank_mode > 2) return DLS_ERR_INVALID_ARG;
+  // tensor-core split-precision modes are reserved until their kernels are built in
+  if (p->precision == DLS_PREC_TF32X3 || p->precision == DLS_PREC_BF16X3) return DLS_ERR_INVALID_ARG;
   for (int a = 0; a < 4; ++a)
     if (p->dims[a] < 1 || p->block[a] < 1 || p->block[a] > p->dims[a]) return DLS_ERR_INVALID_ARG;
   const int64_t M = (int64_t)p->block[0] * p->block[1] * p->block[2];
@@ -65,16 +69,54 @@ int make_plan(const dls_params* p, Plan* out) {
 
 struct Layout {
   size_t meta, vst, q, kc, offsets, vars, status, partial, total;
+  // mixed-precision form
+  size_t staging, q_scr, k8_scr, k32_scr, feat, ranks, phase;
+  int ctas;
+  bool mixed;
 };
+
+// The mixed-precision form serves float32 fields with Gram order <= 16.
+static bool use_mixed(const Plan& P) {
+  return P.precision != DLS_PREC_FP64 && P.dtype == DLS_F32 && P.nmax <= kMaxMixedN;
+}
+
+static int mixed_ctas() {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 152;
+  cudaGetLastError();
+  return 2 * sms;
+}
 
 static Layout work_layout(const Plan& P) {
   Layout L;
+  memset(&L, 0, sizeof(L));
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
     off = (size_t)align_up((int64_t)(off + bytes), 256);
     return o;
   };
+  if (use_mixed(P)) {
+    const int64_t nb1 = P.nb > 0 ? P.nb : 1;
+    const int64_t npt = (int64_t)P.nmax * P.lmax;
+    L.mixed = true;
+    L.ctas = mixed_ctas();
+    L.meta = take(sizeof(BlockMeta) * (size_t)nb1);
+    L.offsets = take(sizeof(unsigned long long) * (size_t)(P.nb + 1));
+    L.vars = take(sizeof(VarInfo) * kMaxVars);
+    L.status = take(sizeof(Status));
+    L.partial = take(sizeof(double) * (size_t)stats_partial_doubles(P));
+    L.staging = take((size_t)(align_up(P.pt_count * 4, 16) + 48 * nb1 + 64));
+    L.q_scr = take(sizeof(int32_t) * (size_t)L.ctas * kMaxMixedN * (size_t)P.lmax);
+    L.k8_scr = take((size_t)L.ctas * (size_t)npt);
+    L.k32_scr = take(sizeof(int32_t) * (size_t)L.ctas * (size_t)npt);
+    L.feat = take(sizeof(float) * 32 * (size_t)nb1);
+    L.ranks = take(sizeof(int32_t) * (size_t)nb1);
+    L.phase = take(sizeof(unsigned long long) * (size_t)L.ctas * kMixedPhases);
+    L.total = off;
+    return L;
+  }
   L.meta = take(sizeof(BlockMeta) * (size_t)(P.nb > 0 ? P.nb : 1));
   L.vst = take(sizeof(double) * (size_t)(P.nb > 0 ? P.nb : 1) * P.nmax * P.nmax);
   L.q = take(sizeof(int32_t) * (size_t)(P.pt_count > 0 ? P.pt_count : 1));
@@ -176,6 +218,119 @@ static int read_header(const void* d_comp, size_t comp_bytes, cudaStream_t s, Ho
   return DLS_OK;
 }
 
+static MixedWork mixed_work(const Plan& P, const Layout& L, void* ws) {
+  uint8_t* b = (uint8_t*)ws;
+  const Work w = carve(L, ws);
+  MixedWork mw;
+  mw.meta = w.meta;
+  mw.offsets = w.offsets;
+  mw.vars = w.vars;
+  mw.status = w.status;
+  mw.staging = b + L.staging;
+  mw.q_scr = (int32_t*)(b + L.q_scr);
+  mw.k8_scr = (int8_t*)(b + L.k8_scr);
+  mw.k32_scr = (int32_t*)(b + L.k32_scr);
+  mw.feat = (float*)(b + L.feat);
+  mw.ranks = (int32_t*)(b + L.ranks);
+  mw.lmax = P.lmax;
+  mw.nptmax = (int64_t)P.nmax * P.lmax;
+  mw.ctas = L.ctas;
+  mw.phase = (unsigned long long*)(b + L.phase);
+  return mw;
+}
+
+// Enqueues the whole compression on `s` (no host synchronisation): status
+// reset, bound resolution, the per-block kernel of the chosen form, the scan
+// writing header and offset table, and the record packer / compaction.
+static int enqueue_compress(const Plan& P, const Layout& L, const void* d_in, void* d_out, size_t out_cap,
+                            void* d_ws, int variant, cudaStream_t s) {
+  int st;
+  Work w = carve(L, d_ws);
+  CK(cudaMemsetAsync(w.status, 0, sizeof(Status), s));
+  double* partial = (double*)((uint8_t*)d_ws + L.partial);
+  if ((st = launch_stats_resolve(P, d_in, w, partial, s)) != DLS_OK) return st;
+  if (L.mixed) {
+    const MixedWork mw = mixed_work(P, L, d_ws);
+    CK(cudaMemsetAsync(mw.phase, 0, sizeof(unsigned long long) * (size_t)L.ctas * kMixedPhases, s));
+    const int mode = P.rank_mode == DLS_RANK_LEARNED ? kRankMlp : (P.rank_mode == DLS_RANK_TAIL ? kRankTail : kRankSearch);
+    if ((st = launch_mixed_compress(P, d_in, mw, mode, variant, s)) != DLS_OK) return st;
+    if ((st = launch_scan(P, w, out_cap, d_out, s)) != DLS_OK) return st;
+    if ((st = launch_compact(P, mw, d_out, s)) != DLS_OK) return st;
+  } else {
+    if ((st = launch_plain_compress(P, d_in, w, s)) != DLS_OK) return st;
+    if ((st = launch_scan(P, w, out_cap, d_out, s)) != DLS_OK) return st;
+    if ((st = launch_pack(P, d_in, w, d_out, out_cap, s)) != DLS_OK) return st;
+  }
+  return DLS_OK;
+}
+
+}  // namespace dls
+
+// ---------------------------------------------------------------- plans: autotune + CUDA graph
+struct dls_plan {
+  dls::Plan P;
+  dls::Layout L;
+  const void* d_in;
+  void* d_out;
+  size_t out_cap;
+  void* d_ws;
+  int variant;
+  float tune_ms[3];
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  dls::Status* h_status;   // pinned
+};
+
+namespace dls {
+
+static std::string tune_key(const Plan& P) {
+  int dev = 0;
+  cudaDeviceProp prop;
+  memset(&prop, 0, sizeof(prop));
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaGetDeviceProperties(&prop, dev);
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s|sm%d|nv%d|d%lldx%lldx%lldx%lld|b%dx%dx%dx%d|t%d|e%d|p%d|r%d|c%d", prop.name,
+           prop.multiProcessorCount, P.nvars, (long long)P.dims[0], (long long)P.dims[1], (long long)P.dims[2],
+           (long long)P.dims[3], P.block[0], P.block[1], P.block[2], P.block[3], P.dtype, P.eb_type, P.precision,
+           P.rank_mode, P.rank_cap);
+  for (char* c = buf; *c; ++c)
+    if (*c == '"' || *c == '\\') *c = '_';
+  return std::string(buf);
+}
+
+static const char* tune_cache_path() {
+  const char* e = getenv("DLS_AUTOTUNE_CACHE");
+  return (e && *e) ? e : nullptr;
+}
+
+// Cached variant for the key (JSON lines {"key": "...", "variant": v, ...}), or 0.
+static int tune_lookup(const std::string& key) {
+  const char* path = tune_cache_path();
+  if (!path) return 0;
+  FILE* f = fopen(path, "r");
+  if (!f) return 0;
+  char line[2048];
+  int found = 0;
+  const std::string pat = "\"key\": \"" + key + "\"";
+  while (fgets(line, sizeof(line), f)) {
+    if (strstr(line, pat.c_str())) {
+      const char* v = strstr(line, "\"variant\": ");
+      if (v) found = atoi(v + 11);
+    }
+  }
+  fclose(f);
+  return (found == 1 || found == 2) ? found : 0;
+}
+
+static void tune_store(const std::string& key, int variant, const float* ms) {
+  const char* path = tune_cache_path();
+  if (!path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "{\"key\": \"%s\", \"variant\": %d, \"ms\": [%.4f, %.4f]}\n", key.c_str(), variant, ms[1], ms[2]);
+  fclose(f);
+}
+
 }  // namespace dls
 
 using namespace dls;
@@ -217,17 +372,12 @@ int dls_compress(const dls_params* p, const void* d_in, void* d_out, size_t out_
   if (st != DLS_OK) return st;
   if (!d_in || !d_out || !out_bytes || ((uintptr_t)d_out & 15) || ((uintptr_t)d_in & (esize(P.dtype) - 1)))
     return DLS_ERR_INVALID_ARG;
-  if (P.precision != DLS_PREC_FP64 || P.rank_mode != DLS_RANK_SEARCH) return DLS_ERR_INVALID_ARG;
   const Layout L = work_layout(P);
   if (!d_workspace || ws_bytes < L.total || ((uintptr_t)d_workspace & 255)) return DLS_ERR_WORKSPACE;
+  if (L.mixed && P.rank_mode == DLS_RANK_LEARNED && !rank_model_loaded()) return DLS_ERR_NO_MODEL;
   cudaStream_t s = (cudaStream_t)stream;
   Work w = carve(L, d_workspace);
-  CK(cudaMemsetAsync(w.status, 0, sizeof(Status), s));
-  double* partial = (double*)((uint8_t*)d_workspace + L.partial);
-  if ((st = launch_stats_resolve(P, d_in, w, partial, s)) != DLS_OK) return st;
-  if ((st = launch_plain_compress(P, d_in, w, s)) != DLS_OK) return st;
-  if ((st = launch_scan(P, w, out_cap, d_out, s)) != DLS_OK) return st;
-  if ((st = launch_pack(P, d_in, w, d_out, out_cap, s)) != DLS_OK) return st;
+  if ((st = enqueue_compress(P, L, d_in, d_out, out_cap, d_workspace, 2, s)) != DLS_OK) return st;
   Status hs;
   CK(cudaMemcpyAsync(&hs, w.status, sizeof(Status), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -289,6 +439,203 @@ int dls_decompress(const void* d_comp, size_t comp_bytes, void* d_out, size_t ou
   CK(cudaStreamSynchronize(s));
   if (st != DLS_OK) return st;
   return hs.corrupt ? DLS_ERR_CORRUPT : DLS_OK;
+}
+
+int dls_block_features(const dls_params* p, const void* d_in, float* d_feat, int32_t* d_rank, void* d_workspace,
+                       size_t ws_bytes, dls_stream_t stream) {
+  Plan P;
+  int st = make_plan(p, &P);
+  if (st != DLS_OK) return st;
+  if (!d_in || !d_feat || !d_rank || !use_mixed(P)) return DLS_ERR_INVALID_ARG;
+  const Layout L = work_layout(P);
+  if (!d_workspace || ws_bytes < L.total || ((uintptr_t)d_workspace & 255)) return DLS_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  Work w = carve(L, d_workspace);
+  uint8_t* b = (uint8_t*)d_workspace;
+  CK(cudaMemsetAsync(w.status, 0, sizeof(Status), s));
+  if ((st = launch_stats_resolve(P, d_in, w, (double*)(b + L.partial), s)) != DLS_OK) return st;
+  MixedWork mw;
+  mw.meta = w.meta; mw.offsets = w.offsets; mw.vars = w.vars; mw.status = w.status;
+  mw.staging = b + L.staging; mw.q_scr = (int32_t*)(b + L.q_scr); mw.k8_scr = (int8_t*)(b + L.k8_scr);
+  mw.k32_scr = (int32_t*)(b + L.k32_scr); mw.feat = d_feat; mw.ranks = d_rank;
+  mw.lmax = P.lmax; mw.nptmax = (int64_t)P.nmax * P.lmax; mw.ctas = L.ctas;
+  mw.phase = (unsigned long long*)(b + L.phase);
+  if ((st = launch_mixed_compress(P, d_in, mw, kRankSearch, 2, s)) != DLS_OK) return st;
+  Status hs;
+  CK(cudaMemcpyAsync(&hs, w.status, sizeof(Status), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return hs.nonfinite ? DLS_ERR_NONFINITE : DLS_OK;
+}
+
+int dls_mlp_forward(const float* d_params, const float* d_feat, int64_t n, float* d_y, dls_stream_t stream) {
+  if (!d_params || n < 0 || (n > 0 && (!d_feat || !d_y))) return DLS_ERR_INVALID_ARG;
+  int st = launch_mlp_forward(d_params, d_feat, n, d_y, (cudaStream_t)stream);
+  if (st != DLS_OK) return st;
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return DLS_OK;
+}
+
+int dls_mlp_grad(const float* d_params, const float* d_feat, const float* d_target, int64_t n, float* d_grad,
+                 float* d_loss, dls_stream_t stream) {
+  if (!d_params || !d_feat || !d_target || !d_grad || !d_loss || n < 1 || n > mlp_max_batch())
+    return DLS_ERR_INVALID_ARG;
+  int st = launch_mlp_grad(d_params, d_feat, d_target, (int)n, d_grad, d_loss, (cudaStream_t)stream);
+  if (st != DLS_OK) return st;
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return DLS_OK;
+}
+
+int dls_mlp_train(float* d_params, float* d_adam, const float* d_feat, const float* d_target, const int32_t* d_order,
+                  int64_t n_order, int32_t steps, int32_t batch, float lr, int32_t step0, float* d_loss,
+                  dls_stream_t stream) {
+  if (!d_params || !d_adam || !d_feat || !d_target || !d_order || n_order < 1 || steps < 0 || batch < 1 ||
+      batch > mlp_max_batch() || !(lr > 0.0f) || step0 < 0)
+    return DLS_ERR_INVALID_ARG;
+  int st = launch_mlp_train(d_params, d_adam, d_feat, d_target, d_order, n_order, steps, batch, lr, step0, d_loss,
+                            (cudaStream_t)stream);
+  if (st != DLS_OK) return st;
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return DLS_OK;
+}
+
+int dls_stage_quantize(const float* d_c, int64_t n, double delta, int32_t* d_q, int32_t* d_ovf,
+                       dls_stream_t stream) {
+  if (n < 0 || (n > 0 && (!d_c || !d_q || !d_ovf)) || !(delta > 0.0) || !isfinite(delta)) return DLS_ERR_INVALID_ARG;
+  int st = launch_stage_quantize(d_c, n, delta, d_q, d_ovf, (cudaStream_t)stream);
+  if (st != DLS_OK) return st;
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return DLS_OK;
+}
+
+int dls_stage_correct(const float* d_x, const float* d_xh, int64_t n, double eb, int32_t* d_k, dls_stream_t stream) {
+  if (n < 0 || (n > 0 && (!d_x || !d_xh || !d_k)) || !(eb > 0.0) || !isfinite(eb)) return DLS_ERR_INVALID_ARG;
+  int st = launch_stage_correct(d_x, d_xh, n, eb, d_k, (cudaStream_t)stream);
+  if (st != DLS_OK) return st;
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return DLS_OK;
+}
+
+int dls_plan_create(const dls_params* p, const void* d_in, void* d_out, size_t out_cap, void* d_workspace,
+                    size_t ws_bytes, dls_stream_t stream, dls_plan** out_plan) {
+  if (!out_plan) return DLS_ERR_INVALID_ARG;
+  *out_plan = nullptr;
+  Plan P;
+  int st = make_plan(p, &P);
+  if (st != DLS_OK) return st;
+  if (!d_in || !d_out || ((uintptr_t)d_out & 15) || ((uintptr_t)d_in & (esize(P.dtype) - 1)))
+    return DLS_ERR_INVALID_ARG;
+  const Layout L = work_layout(P);
+  if (!d_workspace || ws_bytes < L.total || ((uintptr_t)d_workspace & 255)) return DLS_ERR_WORKSPACE;
+  if (L.mixed && P.rank_mode == DLS_RANK_LEARNED && !rank_model_loaded()) return DLS_ERR_NO_MODEL;
+  cudaStream_t s = (cudaStream_t)stream;
+  dls_plan* pl = new dls_plan();
+  pl->P = P;
+  pl->L = L;
+  pl->d_in = d_in;
+  pl->d_out = d_out;
+  pl->out_cap = out_cap;
+  pl->d_ws = d_workspace;
+  pl->variant = 2;
+  pl->tune_ms[0] = pl->tune_ms[1] = pl->tune_ms[2] = 0.0f;
+  pl->graph = nullptr;
+  pl->exec = nullptr;
+  pl->h_status = nullptr;
+  auto fail = [&](int code) {
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    if (pl->h_status) cudaFreeHost(pl->h_status);
+    delete pl;
+    return code;
+  };
+  if (cudaHostAlloc((void**)&pl->h_status, sizeof(Status), cudaHostAllocDefault) != cudaSuccess) return fail(DLS_ERR_CUDA);
+  // autotune: time each occupancy variant of the per-block kernel on the real work
+  if (L.mixed) {
+    const std::string key = tune_key(P);
+    int v = tune_lookup(key);
+    if (v == 0) {
+      cudaEvent_t e0, e1;
+      if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(DLS_ERR_CUDA);
+      for (int var = 1; var <= 2; ++var) {
+        if ((st = enqueue_compress(P, L, d_in, d_out, out_cap, d_workspace, var, s)) != DLS_OK) return fail(st);
+        cudaEventRecord(e0, s);
+        if ((st = enqueue_compress(P, L, d_in, d_out, out_cap, d_workspace, var, s)) != DLS_OK) return fail(st);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return fail(DLS_ERR_CUDA);
+        cudaEventElapsedTime(&pl->tune_ms[var], e0, e1);
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      v = pl->tune_ms[1] < pl->tune_ms[2] ? 1 : 2;
+      tune_store(key, v, pl->tune_ms);
+    }
+    pl->variant = v;
+  }
+  // capture the sequence, ending with the status copy into pinned memory, on a
+  // private stream (the legacy default stream cannot be captured)
+  if (cudaStreamSynchronize(s) != cudaSuccess) return fail(DLS_ERR_CUDA);
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return fail(DLS_ERR_CUDA);
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return fail(DLS_ERR_CUDA);
+  }
+  st = enqueue_compress(P, L, d_in, d_out, out_cap, d_workspace, pl->variant, cs);
+  Work w = carve(L, d_workspace);
+  cudaError_t ce = cudaMemcpyAsync(pl->h_status, w.status, sizeof(Status), cudaMemcpyDeviceToHost, cs);
+  cudaGraph_t g = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(cs, &g);
+  cudaStreamDestroy(cs);
+  if (st != DLS_OK || ce != cudaSuccess || ee != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    return fail(st != DLS_OK ? st : DLS_ERR_CUDA);
+  }
+  pl->graph = g;
+  if (cudaGraphInstantiate(&pl->exec, g, 0) != cudaSuccess) return fail(DLS_ERR_CUDA);
+  *out_plan = pl;
+  return DLS_OK;
+}
+
+int dls_plan_execute(dls_plan* pl, size_t* out_bytes, dls_stream_t stream) {
+  if (!pl || !out_bytes) return DLS_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaGraphLaunch(pl->exec, s));
+  CK(cudaStreamSynchronize(s));
+  const Status hs = *pl->h_status;
+  if (hs.nonfinite) return DLS_ERR_NONFINITE;
+  *out_bytes = (size_t)hs.total_bytes;
+  if (hs.capacity) return DLS_ERR_CAPACITY;
+  return DLS_OK;
+}
+
+int dls_plan_info(const dls_plan* pl, int32_t* variant, float* tune_ms) {
+  if (!pl) return DLS_ERR_INVALID_ARG;
+  if (variant) *variant = pl->variant;
+  if (tune_ms) { tune_ms[0] = pl->tune_ms[1]; tune_ms[1] = pl->tune_ms[2]; }
+  return DLS_OK;
+}
+
+int dls_plan_destroy(dls_plan* pl) {
+  if (!pl) return DLS_OK;
+  if (pl->exec) cudaGraphExecDestroy(pl->exec);
+  if (pl->graph) cudaGraphDestroy(pl->graph);
+  if (pl->h_status) cudaFreeHost(pl->h_status);
+  delete pl;
+  return DLS_OK;
+}
+
+int dls_phase_cycles(const dls_params* p, const void* d_workspace, unsigned long long* h_cycles, int32_t count) {
+  Plan P;
+  int st = make_plan(p, &P);
+  if (st != DLS_OK) return st;
+  const Layout L = work_layout(P);
+  if (!L.mixed || !d_workspace || !h_cycles || count < kMixedPhases) return DLS_ERR_INVALID_ARG;
+  std::vector<unsigned long long> v((size_t)L.ctas * kMixedPhases);
+  CK(cudaMemcpy(v.data(), (const uint8_t*)d_workspace + L.phase, v.size() * sizeof(unsigned long long),
+                cudaMemcpyDeviceToHost));
+  for (int i = 0; i < kMixedPhases; ++i) h_cycles[i] = 0;
+  for (int c = 0; c < L.ctas; ++c)
+    for (int i = 0; i < kMixedPhases; ++i) h_cycles[i] += v[(size_t)c * kMixedPhases + i];
+  return DLS_OK;
 }
 
 int dls_stream_info_get(const void* d_comp, size_t comp_bytes, dls_stream_info* out) {

@@ -197,7 +197,52 @@ __host__ __device__ inline RecLayout rec_layout(int r, int n, int64_t L, int64_t
 }
 __host__ __device__ inline int64_t raw_record_bytes(int64_t N, int es) { return align_up(16 + N * es, 16); }
 
+// Workspace of the mixed-precision form.
+struct MixedWork {
+  BlockMeta* meta;
+  unsigned long long* offsets;
+  VarInfo* vars;
+  Status* status;
+  uint8_t* staging;     // per-block record slots: align16(pt_rel * 4) + 48 * bi
+  int32_t* q_scr;       // ctas x kMaxMixedN x lmax
+  int8_t* k8_scr;       // ctas x nptmax
+  int32_t* k32_scr;     // ctas x nptmax
+  float* feat;          // nb x 32
+  int32_t* ranks;       // nb
+  int64_t lmax, nptmax;
+  int ctas;
+  unsigned long long* phase;   // ctas x kMixedPhases cycle counters
+};
+constexpr int kMaxMixedN = 16;
+constexpr int kMixedPhases = 12;
+
+// Block-rank MLP: 32 features -> 64 -> 64 -> 1 (ReLU).  Parameter vector layout
+// (floats): [mu 32][sigma 32][W1 64x32][b1 64][W2 64x64][b2 64][W3 64][b3 1].
+constexpr int kMlpF = 32, kMlpH = 64;
+constexpr int kMlpOffMu = 0, kMlpOffSig = kMlpF, kMlpOffW1 = 2 * kMlpF;
+constexpr int kMlpOffB1 = kMlpOffW1 + kMlpH * kMlpF;
+constexpr int kMlpOffW2 = kMlpOffB1 + kMlpH;
+constexpr int kMlpOffB2 = kMlpOffW2 + kMlpH * kMlpH;
+constexpr int kMlpOffW3 = kMlpOffB2 + kMlpH;
+constexpr int kMlpOffB3 = kMlpOffW3 + kMlpH;
+constexpr int kMlpNParam = kMlpOffB3 + 1;   // 6401
+// rank modes of the kernel
+constexpr int kRankSearch = 0, kRankMlp = 1, kRankTail = 2;
+
 // ---------------------------------------------------------------- launchers (defined in .cu files)
+int launch_mixed_compress(const Plan& p, const void* d_in, const MixedWork& w, int learned, int variant,
+                          cudaStream_t s);
+int launch_compact(const Plan& p, const MixedWork& w, void* d_out, cudaStream_t s);
+size_t mixed_smem_bytes();
+int launch_mlp_train(float* params, float* adam, const float* feat, const float* target, const int32_t* order,
+                     int64_t n_order, int steps, int B, float lr, int step0, float* loss, cudaStream_t s);
+int launch_mlp_grad(const float* params, const float* feat, const float* target, int B, float* grad, float* loss,
+                    cudaStream_t s);
+int launch_mlp_forward(const float* params, const float* feat, int64_t n, float* y, cudaStream_t s);
+int mlp_max_batch();
+bool rank_model_loaded();
+int launch_stage_quantize(const float* c, int64_t n, double delta, int32_t* q, int32_t* ovf, cudaStream_t s);
+int launch_stage_correct(const float* x, const float* xh, int64_t n, double eb, int32_t* k, cudaStream_t s);
 int launch_plain_compress(const Plan& p, const void* d_in, const Work& w, cudaStream_t s);
 int launch_scan(const Plan& p, const Work& w, size_t out_cap, void* d_out, cudaStream_t s);
 int launch_pack(const Plan& p, const void* d_in, const Work& w, void* d_out, size_t out_cap, cudaStream_t s);

@@ -17,8 +17,9 @@ from . import build as _build
 
 F32, F64 = 0, 1
 EB_ABS, EB_REL_RANGE, EB_NRMSE = 0, 1, 2
-PREC_FP64, PREC_TF32X3, PREC_BF16X3 = 0, 1, 2
-RANK_SEARCH, RANK_LEARNED = 0, 1
+PREC_FP64, PREC_TF32X3, PREC_BF16X3, PREC_FP32 = 0, 1, 2, 3
+RANK_SEARCH, RANK_LEARNED, RANK_TAIL = 0, 1, 2
+MLP_NPARAM, MLP_NFEAT = 6401, 32
 OK = 0
 ERR = {-1: "INVALID_ARG", -2: "CAPACITY", -3: "NONFINITE", -4: "CORRUPT", -5: "CUDA", -6: "TIMEOUT",
        -7: "BOUND_VIOLATED", -8: "WORKSPACE", -9: "NO_MODEL"}
@@ -87,6 +88,21 @@ _SIGS = {
     "dls_decompress": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t, C.c_void_p]),
     "dls_verify": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(Report), C.c_void_p]),
     "dls_stream_info_get": (C.c_int, [C.c_void_p, C.c_size_t, C.POINTER(StreamInfo)]),
+    "dls_set_rank_model": (C.c_int, [C.c_void_p, C.c_size_t]),
+    "dls_block_features": (C.c_int, [C.POINTER(Params), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
+                                     C.c_void_p]),
+    "dls_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "dls_mlp_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dls_mlp_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
+                                C.c_int32, C.c_float, C.c_int32, C.c_void_p, C.c_void_p]),
+    "dls_plan_create": (C.c_int, [C.POINTER(Params), C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t,
+                                  C.c_void_p, C.POINTER(C.c_void_p)]),
+    "dls_plan_execute": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t), C.c_void_p]),
+    "dls_plan_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
+    "dls_plan_destroy": (C.c_int, [C.c_void_p]),
+    "dls_phase_cycles": (C.c_int, [C.POINTER(Params), C.c_void_p, C.POINTER(C.c_ulonglong), C.c_int32]),
+    "dls_stage_quantize": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dls_stage_correct": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_void_p]),
     "dls_status_string": (C.c_char_p, [C.c_int]),
 }
 
@@ -245,3 +261,131 @@ def verify(orig: torch.Tensor, recon: torch.Tensor, comp: torch.Tensor) -> dict:
         d[k] = list(d[k])
     d["status"] = st
     return d
+
+
+def stage_quantize(c: torch.Tensor, delta: float):
+    """Mixed-form quantizer on float32 CUDA coefficients: (q, ovf) int32 tensors."""
+    q = torch.empty(c.shape, dtype=torch.int32, device=c.device)
+    ovf = torch.empty(c.shape, dtype=torch.int32, device=c.device)
+    st = lib().dls_stage_quantize(C.c_void_p(c.data_ptr()), c.numel(), float(delta), C.c_void_p(q.data_ptr()),
+                                  C.c_void_p(ovf.data_ptr()), _stream(None))
+    if st != OK:
+        raise DlsError(st, "dls_stage_quantize")
+    return q, ovf
+
+
+def stage_correct(x: torch.Tensor, xh: torch.Tensor, eb: float):
+    """Mixed-form pointwise correction of xh against x (float32 CUDA): int32 k, INT32_MIN = escape."""
+    k = torch.empty(x.shape, dtype=torch.int32, device=x.device)
+    st = lib().dls_stage_correct(C.c_void_p(x.data_ptr()), C.c_void_p(xh.data_ptr()), x.numel(), float(eb),
+                                 C.c_void_p(k.data_ptr()), _stream(None))
+    if st != OK:
+        raise DlsError(st, "dls_stage_correct")
+    return k
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def set_rank_model(params) -> None:
+    """Loads the block-rank MLP (DLS_MLP_NPARAM float32 values) on the current device."""
+    import numpy as np
+    arr = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+    st = lib().dls_set_rank_model(arr.ctypes.data_as(C.c_void_p), arr.size)
+    if st != OK:
+        raise DlsError(st, "dls_set_rank_model")
+
+
+def block_features(field: torch.Tensor, block, eb, eb_type=EB_ABS, rank_cap=16):
+    """Per-block features (nb x 32) and bisection ranks (nb) of a float32 CUDA field."""
+    p = make_params(tuple(field.shape), field.dtype, block, eb, eb_type, rank_cap, precision=PREC_FP32)
+    ws = torch.empty(workspace_size(p), dtype=torch.uint8, device=field.device)
+    nb = 1
+    for a in range(4):
+        nb *= -(-p.dims[a] // p.block[a])
+    nb *= p.nvars
+    feat = torch.empty((nb, MLP_NFEAT), dtype=torch.float32, device=field.device)
+    rank = torch.empty(nb, dtype=torch.int32, device=field.device)
+    st = lib().dls_block_features(C.byref(p), _ptr(field), _ptr(feat), _ptr(rank), _ptr(ws), ws.numel(), _stream(None))
+    if st != OK:
+        raise DlsError(st, "dls_block_features")
+    return feat, rank
+
+
+def mlp_forward(params: torch.Tensor, feat: torch.Tensor) -> torch.Tensor:
+    y = torch.empty(feat.shape[0], dtype=torch.float32, device=feat.device)
+    st = lib().dls_mlp_forward(_ptr(params), _ptr(feat), feat.shape[0], _ptr(y), _stream(None))
+    if st != OK:
+        raise DlsError(st, "dls_mlp_forward")
+    return y
+
+
+def mlp_grad(params: torch.Tensor, feat: torch.Tensor, target: torch.Tensor):
+    g = torch.empty(MLP_NPARAM, dtype=torch.float32, device=feat.device)
+    loss = torch.empty(1, dtype=torch.float32, device=feat.device)
+    st = lib().dls_mlp_grad(_ptr(params), _ptr(feat), _ptr(target), feat.shape[0], _ptr(g), _ptr(loss),
+                            _stream(None))
+    if st != OK:
+        raise DlsError(st, "dls_mlp_grad")
+    return float(loss.item()), g
+
+
+def mlp_train(params: torch.Tensor, adam: torch.Tensor, feat: torch.Tensor, target: torch.Tensor,
+              order: torch.Tensor, steps: int, batch: int, lr: float, step0: int = 0):
+    """Runs `steps` Adam steps on the GPU in place; returns the per-step losses."""
+    loss = torch.empty(max(steps, 1), dtype=torch.float32, device=feat.device)
+    st = lib().dls_mlp_train(_ptr(params), _ptr(adam), _ptr(feat), _ptr(target), _ptr(order), order.numel(),
+                             steps, batch, float(lr), step0, _ptr(loss), _stream(None))
+    if st != OK:
+        raise DlsError(st, "dls_mlp_train")
+    return loss[:steps]
+
+
+class CompressPlan:
+    """Graph-captured, autotuned compression of fixed buffers (dls_plan_*)."""
+
+    def __init__(self, p: Params, field: torch.Tensor, out: torch.Tensor, workspace: torch.Tensor, stream=None):
+        self._keep = (p, field, out, workspace)
+        self.handle = C.c_void_p()
+        st = lib().dls_plan_create(C.byref(p), _ptr(field), _ptr(out), out.numel(), _ptr(workspace),
+                                   workspace.numel(), _stream(stream), C.byref(self.handle))
+        if st != OK:
+            raise DlsError(st, "dls_plan_create")
+
+    def execute(self, stream=None) -> int:
+        nb = C.c_size_t(0)
+        st = lib().dls_plan_execute(self.handle, C.byref(nb), _stream(stream))
+        if st != OK:
+            raise DlsError(st, "dls_plan_execute")
+        return nb.value
+
+    def info(self):
+        v = C.c_int32(0)
+        ms = (C.c_float * 2)()
+        lib().dls_plan_info(self.handle, C.byref(v), ms)
+        return v.value, (ms[0], ms[1])
+
+    def close(self):
+        if self.handle:
+            lib().dls_plan_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+PHASES = ("gram", "jacobi", "refine", "rayleigh_ritz", "predict", "encode", "decide", "search", "pack",
+          "n_accepted", "n_searched", "n_exact_fallback")
+
+
+def phase_cycles(p: Params, workspace: torch.Tensor) -> dict:
+    """Per-phase cycle counts (summed over CTAs) of the last mixed-form compression."""
+    arr = (C.c_ulonglong * len(PHASES))()
+    st = lib().dls_phase_cycles(C.byref(p), _ptr(workspace), arr, len(PHASES))
+    if st != OK:
+        raise DlsError(st, "dls_phase_cycles")
+    return {k: int(arr[i]) for i, k in enumerate(PHASES)}

@@ -1,0 +1,174 @@
+"""Mixed-precision form (FP32 products, FP64-accurate eigenbasis, FP64-semantics
+decisions) against the CPU oracle, through the C ABI.
+
+Stage tests feed identical inputs to the GPU's FP32-filtered decisions and to
+the oracle's FP64 definitions and require identical results, with inputs placed
+on the rounding boundaries where a filter could go wrong.  End-to-end tests
+require the pointwise bound at every point and the compression ratio within 1%
+of the oracle's, and report the reconstruction difference from the oracle.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2601_20113_gb300 import dls, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2601_20113_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def _adversarial_coeffs(delta, n, seed):
+    rng = np.random.default_rng(seed)
+    k = rng.integers(-20000, 20000, size=n).astype(np.float64)
+    base = (k + 0.5) * delta                              # exact half-way points
+    c = base.astype(np.float32)
+    # nudge by a few ulps around the half-way points
+    nud = rng.integers(-3, 4, size=n).astype(np.int32)
+    for s in range(1, 4):
+        m = nud == s
+        c[m] = np.nextafter(c[m], np.float32(np.inf))
+        m = nud == -s
+        c[m] = np.nextafter(c[m], np.float32(-np.inf))
+    ints = (rng.integers(-1000, 1000, size=n) * delta).astype(np.float32)
+    rnd = (rng.standard_normal(n) * 300 * delta).astype(np.float32)
+    big = ((2.0 ** 24 + rng.integers(-4, 4, size=n)) * delta).astype(np.float32)
+    return np.concatenate([c, ints, rnd, big, -big])
+
+
+@pytest.mark.parametrize("delta", [1e-3, 7.3e-4, 0.25, 3.1e-7])
+def test_stage_quantizer_bit_exact(delta):
+    c = _adversarial_coeffs(delta, 20000, seed=int(delta * 1e7) % 1000)
+    q, ovf = dls.stage_quantize(torch.from_numpy(c).cuda(), delta)
+    qo, _ = oracle.quantize(c.astype(np.float64), delta, oracle.F32)
+    y = c.astype(np.float64) / delta
+    ovf_o = ~(np.abs(y) < 2.0 ** 24)
+    qg = q.cpu().numpy()
+    og = ovf.cpu().numpy().astype(bool)
+    np.testing.assert_array_equal(og, ovf_o)
+    np.testing.assert_array_equal(qg[~ovf_o], qo[~ovf_o])
+
+
+@pytest.mark.parametrize("eb", [1e-3, 3.7e-2, 2.5e-5])
+def test_stage_correction_bit_exact(eb):
+    rng = np.random.default_rng(int(eb * 1e6) % 997)
+    n = 30000
+    x = (rng.standard_normal(n) * 2.0).astype(np.float32)
+    # residuals on and around the decision points |R| = eb, 3eb, 5eb and far
+    kk = rng.integers(-3, 4, size=n)
+    r = (kk * 2 * eb + np.where(rng.random(n) < 0.5, eb, -eb)).astype(np.float64)
+    xh = (x.astype(np.float64) - r).astype(np.float32)
+    for s in range(1, 3):
+        m = rng.random(n) < 0.2
+        xh[m] = np.nextafter(xh[m], np.float32(np.inf) if s == 1 else np.float32(-np.inf))
+    xh[: n // 10] = (x[: n // 10].astype(np.float64) - rng.uniform(-3 * eb, 3 * eb, n // 10)).astype(np.float32)
+    xh[n // 10: n // 10 + 100] = x[n // 10: n // 10 + 100] + np.float32(1e9 * eb)     # beyond 2^20 steps
+    k = dls.stage_correct(torch.from_numpy(x).cuda(), torch.from_numpy(xh).cuda(), eb).cpu().numpy()
+    ko, esc = oracle.correct(x.astype(np.float64)[:, None], xh.astype(np.float64)[:, None], 0, n,
+                             oracle.F32, eb, 2 * eb)
+    esc = esc.astype(bool)
+    np.testing.assert_array_equal(k == np.iinfo(np.int32).min, esc)
+    np.testing.assert_array_equal(k[~esc], ko[~esc])
+
+
+def _mixed_vs_oracle(f, dims, block, eb, eb_type=oracle.EB_ABS, rank_cap=16, nvars=1, rank_mode=dls.RANK_SEARCH):
+    cfg = oracle.Config(dims, block, oracle.F32, eb=eb, eb_type=eb_type, rank_cap=rank_cap, nvars=nvars)
+    st, ref, trs = oracle.compress(cfg, f, traces=True)
+    assert st == 0
+    fd = torch.from_numpy(np.ascontiguousarray(f)).cuda()
+    comp = dls.compress(fd, block=block, eb=eb, eb_type=eb_type, rank_cap=rank_cap, precision=dls.PREC_FP32,
+                        rank_mode=rank_mode)
+    rec = dls.decompress(comp)
+    return ref, comp, rec, fd, trs
+
+
+@pytest.mark.parametrize("rel", [1e-2, 1e-3, 1e-4, 1e-5])
+def test_mixed_bound_and_ratio(rel):
+    dims = (40, 36, 20, 36)
+    f = synth.modes3d(*dims, seed=2, count=32).numpy()
+    eb = rel * float(f.max() - f.min())
+    ref, comp, rec, fd, trs = _mixed_vs_oracle(f, dims, (16, 16, 16, 16), eb)
+    err = (rec.double() - fd.double()).abs().max().item()
+    assert err <= eb
+    ratio_gpu = f.nbytes / comp.numel()
+    ratio_ref = f.nbytes / ref.size
+    assert abs(ratio_gpu / ratio_ref - 1) <= 0.01, (ratio_gpu, ratio_ref)
+    st, rref = oracle.decompress(ref)
+    diff = np.linalg.norm(rec.cpu().numpy().astype(np.float64) - rref) / np.linalg.norm(f.astype(np.float64))
+    print(f"rel {rel}: ratio gpu {ratio_gpu:.4f} oracle {ratio_ref:.4f}; ||x_gpu - x_oracle|| / ||x|| = {diff:.3e}")
+
+
+def _same_payload(a, b):
+    """Streams equal except header byte 67 (the rank mode used)."""
+    a = a.cpu().numpy().copy()
+    b = b.cpu().numpy().copy()
+    a[67] = b[67] = 0
+    return a.size == b.size and np.array_equal(a, b)
+
+
+def test_predicted_rank_equals_search_stream():
+    """A predicted rank is accepted only when it is the smallest passing rank
+    next to the prediction, so the prediction changes no stored byte."""
+    dims = (64, 64, 32, 32)
+    f = synth.modes3d(*dims, seed=5, count=48)
+    fd = f.cuda()
+    for rel in (1e-2, 1e-3, 1e-4):
+        eb = rel * float(f.max() - f.min())
+        a = dls.compress(fd, block=(16, 16, 16, 16), eb=eb, rank_cap=16, precision=dls.PREC_FP32,
+                         rank_mode=dls.RANK_SEARCH)
+        b = dls.compress(fd, block=(16, 16, 16, 16), eb=eb, rank_cap=16, precision=dls.PREC_FP32,
+                         rank_mode=dls.RANK_TAIL)
+        assert _same_payload(a, b)
+
+
+def test_mixed_multivariable_uneven_blocks():
+    """Five variables with edge blocks on every axis (T = 2 and short spatial
+    edges), per-variable relative bounds."""
+    f = synth.multivar(50, 38, 26, 18).numpy()
+    ebs = [1e-3, 1e-3, 1e-3, 1e-4, 1e-4]
+    cfg = oracle.Config((50, 38, 26, 18), (16, 16, 16, 16), oracle.F32, eb=ebs, eb_type=oracle.EB_REL_RANGE,
+                        rank_cap=16, nvars=5)
+    st, ref, _ = oracle.compress(cfg, f)
+    fd = torch.from_numpy(f).cuda()
+    comp = dls.compress(fd, block=(16, 16, 16, 16), eb=ebs, eb_type=dls.EB_REL_RANGE, rank_cap=16,
+                        precision=dls.PREC_FP32, rank_mode=dls.RANK_TAIL)
+    rec = dls.decompress(comp)
+    x = f.astype(np.float64)
+    y = rec.cpu().numpy().astype(np.float64)
+    for v in range(5):
+        assert np.abs(y[v] - x[v]).max() <= ebs[v] * (x[v].max() - x[v].min())
+    assert abs((f.nbytes / comp.numel()) / (f.nbytes / ref.size) - 1) <= 0.01
+
+
+def test_mixed_nrmse_mode():
+    dims = (32, 32, 16, 32)
+    f = synth.modes3d(*dims, seed=7, count=16).numpy()
+    fd = torch.from_numpy(f).cuda()
+    for eps in (0.5, 2.0):
+        comp = dls.compress(fd, block=(16, 16, 8, 16), eb=eps, eb_type=dls.EB_NRMSE, precision=dls.PREC_FP32,
+                            rank_mode=dls.RANK_TAIL)
+        rec = dls.decompress(comp)
+        x = f.astype(np.float64)
+        assert 100 * np.linalg.norm(rec.cpu().numpy() - x) / np.linalg.norm(x) <= eps
+
+
+def test_mixed_mode_on_f64_field_takes_fp64_form():
+    f = synth.vortex2d(64, 64, 32, seed=1).numpy()
+    eb = 1e-3 * float(f.max() - f.min())
+    cfg = oracle.Config((64, 64, 1, 32), (8, 8, 1, 32), oracle.F64, eb=eb, rank_cap=16)
+    st, ref, _ = oracle.compress(cfg, f)
+    comp = dls.compress(torch.from_numpy(f).cuda(), block=(8, 8, 1, 32), eb=eb, rank_cap=16,
+                        precision=dls.PREC_FP32)
+    got = comp.cpu().numpy()
+    assert got.size == ref.size and np.array_equal(got[128:], ref[128:])   # header differs in the precision byte
+
+
+def test_tensor_core_modes_are_reserved():
+    p = dls.make_params((1, 16, 16, 16, 16), dls.F32, (16, 16, 16, 16), 1e-3, precision=dls.PREC_TF32X3)
+    assert dls.workspace_size(p) == 0
