@@ -207,6 +207,56 @@ def run_reference(args):
     return 0
 
 
+KERNEL_SOURCES = {
+    "plain": ["k_plain.cu", "dls_internal.cuh"],
+    "mixed": ["k_tile.cu", "mixed_common.cuh", "dls_device.cuh", "dls_internal.cuh"],
+}
+PROFILE = {"plain": "profiles/k_plain_fp64_modes3d.md", "mixed": "profiles/k_tile_modes3d.md"}
+
+
+def _sources_sha(kind):
+    import hashlib
+    h = hashlib.sha256()
+    for fn in KERNEL_SOURCES[kind]:
+        with open(os.path.join(ROOT, "paper_2601_20113_gb300", "csrc", fn), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profile_traffic(kind, blocks):
+    """DRAM bytes per launch from the committed ncu summary of the kernel, scaled
+    from the captured case to `blocks` blocks; None when the summary is missing
+    or was taken on other sources."""
+    try:
+        txt = open(os.path.join(ROOT, PROFILE[kind])).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in txt.splitlines():
+        if ":" in line and line.strip().startswith(("source_sha256", "dram_bytes_per_block")):
+            k, v = line.strip().split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha256") != _sources_sha(kind) or "dram_bytes_per_block" not in vals:
+        return None
+    return float(vals["dram_bytes_per_block"]) * blocks
+
+
+def _roofline(form, in_bytes, out_bytes, kernel_ms, hbm, peak_kind, dims):
+    """Dominant kernel: the per-block compression kernel(s), timed by events
+    inside the captured graph.  Algorithmic bytes per launch = the field read
+    once + the records written (about the stream size)."""
+    kind = "plain" if form == "plain" else "mixed"
+    blocks = 1
+    for d, b in zip(dims, BLOCK):
+        blocks *= -(-d // b)
+    alg = in_bytes + out_bytes
+    ach = alg / (kernel_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": "k_plain" if kind == "plain" else "k_tile", "achieved": ach, "peak": hbm,
+            "unit": "GB/s", "frac": ach / hbm, "traffic": _profile_traffic(kind, blocks),
+            "algorithmic_bytes": alg, "kernel_ms": kernel_ms,
+            "note": f"peak = {peak_kind} HBM copy bandwidth; algorithmic bytes = input + records"}
+
+
 def _config(form="learned"):
     return {"workload": "modes3d 256^3 x 64 float32 (4 GiB), 64 modes |k|<=8, k^-5/3, N(0,1e-3^2) noise, "
                         "blocks 16^3x16 (16384), abs bound 1e-3 x range, rank cap 16",
@@ -264,9 +314,10 @@ def main():
     stream = torch.cuda.current_stream()
     in_bytes = field.numel() * field.element_size()
 
+    # the captured plan: autotuned variant, whole compression in one CUDA graph
+    plan = dls.CompressPlan(p, field, out, ws, stream)
     for _ in range(args.warmup):
-        st, nb = dls.compress_into(p, field, out, ws)
-        assert st == 0, dls.status_string(st)
+        nb = plan.execute(stream)
     torch.cuda.synchronize()
     clocks = Clocks(local)
     clocks.start()
@@ -275,22 +326,25 @@ def main():
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    kms = []
     e0.record(stream)
     for _ in range(args.steps):
-        st, nb = dls.compress_into(p, field, out, ws)
-        assert st == 0
+        nb = plan.execute(stream)
+        kms.append(plan.timing()[0])
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     clk = clocks.stop()
+    kernel_ms = sum(kms) / len(kms)
+    graph_kernels = plan.timing()[1]
+    variant, tune_ms = plan.info()
+    plan.close()
     if dist is not None:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
         dist.barrier()
 
-    # kernel-level timing of the dominant kernel, via the library's own
-    # per-phase event hook is not exposed; time the step split instead
     ratio = in_bytes / nb
     rec = dls.decompress(out[:nb])
     rep = dls.verify(field, rec, out[:nb])
@@ -328,12 +382,12 @@ def main():
         "data": "synthetic", "config": _config(args.form),
         "ratio": ratio, "max_abs_err": rep["max_abs_err"], "eb": eb, "n_over_bound": rep["n_over_bound"],
         "mean_rank": rep["mean_rank"], "decompress_gbs": in_bytes / (dms * 1e-3) / 1e9,
-        "roofline": {"bound": "hbm", "achieved": in_bytes / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-                     "frac": in_bytes / (ms * 1e-3) / 1e9 / hbm, "traffic": None,
-                     "note": f"whole step over input bytes; peak {peak_kind}"},
+        "roofline": _roofline(args.form, in_bytes, nb, kernel_ms, hbm, peak_kind, DIMS),
         "e2e": {"value": in_bytes * world / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": in_bytes,
                 "d2h_bytes_per_step": enb},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": graph_kernels * args.steps,
+        "plan": {"variant": variant, "tune_ms": list(tune_ms), "kernel_ms": kernel_ms,
+                 "graph_kernel_nodes": graph_kernels},
         "clocks": clk,
     }
     if args.form != "plain" and not args.no_plain:

@@ -124,9 +124,15 @@ typedef struct dls_plan dls_plan;
 int dls_plan_create(const dls_params* p, const void* d_in, void* d_out, size_t out_cap, void* d_workspace,
                     size_t ws_bytes, dls_stream_t stream, dls_plan** out_plan);
 int dls_plan_execute(dls_plan* plan, size_t* out_bytes, dls_stream_t stream);
-/* Chosen variant (1: one CTA per SM, 2: two) and the two timings in ms (0 if
- * the choice came from the cache or the form has one variant). */
+/* Chosen occupancy variant (1: fewer CTAs per SM with more registers each,
+ * 2: more CTAs per SM) and the two timings in ms (0 if the choice came from
+ * the cache or the form has one variant). */
 int dls_plan_info(const dls_plan* plan, int32_t* variant, float* tune_ms);
+/* Device time in ms of the per-block compression kernels during the most
+ * recent dls_plan_execute (events recorded around them inside the graph; waits
+ * for that execution), and the number of kernel nodes in the plan's graph.
+ * Either pointer may be null. */
+int dls_plan_timing(const dls_plan* plan, float* kernel_ms, int32_t* kernel_nodes);
 int dls_plan_destroy(dls_plan* plan);
 
 /* Device staging bytes dls_compress_host needs: the input field, the stream
@@ -251,8 +257,9 @@ int dls_mlp_train(float* d_params, float* d_adam, const float* d_feat, const flo
  * encode pass at the predicted rank, exact pass tests, bisection fallback,
  * record packing; then three counts: blocks whose predicted rank was
  * accepted, blocks that fell back to the bisection, and FP64 re-evaluations
- * of E(r) taken because the FP32 estimate could not decide.  count >= 12.
- * Synchronous copy. */
+ * of E(r) taken because the FP32 estimate could not decide; then the cycles
+ * spent waiting for staged tiles (included in the phases above; 0 for blocks
+ * the row-loading kernel serves).  count >= 13.  Synchronous copy. */
 int dls_phase_cycles(const dls_params* p, const void* d_workspace, unsigned long long* h_cycles, int32_t count);
 
 /* Stream header as a host struct (reads the header with one synchronous copy). */

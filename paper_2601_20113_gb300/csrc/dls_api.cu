@@ -85,7 +85,51 @@ static int mixed_ctas() {
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     sms = 152;
   cudaGetLastError();
-  return 2 * sms;
+  return 4 * sms;
+}
+
+// Kernels serving the mixed form: k_tile takes the blocks whose Gram side is
+// time when its chunk box fits the plan; k_mixed takes the others (or all).
+struct MixedRoute {
+  bool tile, legacy, spatial_only;
+};
+static MixedRoute mixed_route(const Plan& P) {
+  bool has0 = false, has1 = false;
+  for (int c = 0; c < 16; ++c) {
+    int64_t s[4];
+    bool exists = true;
+    for (int a = 0; a < 4; ++a) {
+      const int64_t edge = P.dims[a] % P.block[a];
+      if (c >> a & 1) {
+        if (edge == 0) exists = false;
+        s[a] = edge;
+      } else {
+        if (P.dims[a] < P.block[a]) exists = false;
+        s[a] = P.block[a];
+      }
+    }
+    if (!exists) continue;
+    const int64_t M = s[0] * s[1] * s[2], T = s[3];
+    if (T <= M) has0 = true;
+    else has1 = true;
+  }
+  int bxb, yc, zc, bt;
+  const bool fits = tile_chunk_box(P, &bxb, &yc, &zc, &bt);
+  MixedRoute r;
+  r.tile = fits && has0;
+  r.legacy = !fits || has1;
+  r.spatial_only = fits;
+  return r;
+}
+
+static int launch_mixed_all(const Plan& P, const void* d_in, const MixedWork& mw, int mode, int variant,
+                            cudaStream_t s) {
+  const MixedRoute rt = mixed_route(P);
+  int st;
+  if (rt.tile && (st = launch_tile_compress(P, d_in, mw, mode, variant, s)) != DLS_OK) return st;
+  if (rt.legacy && (st = launch_mixed_compress(P, d_in, mw, mode, variant, rt.spatial_only ? 1 : 0, s)) != DLS_OK)
+    return st;
+  return DLS_OK;
 }
 
 static Layout work_layout(const Plan& P) {
@@ -99,7 +143,7 @@ static Layout work_layout(const Plan& P) {
   };
   if (use_mixed(P)) {
     const int64_t nb1 = P.nb > 0 ? P.nb : 1;
-    const int64_t npt = (int64_t)P.nmax * P.lmax;
+    const int64_t npt = align_up((int64_t)P.nmax * P.lmax, 16);   // 16-byte rows of k8
     L.mixed = true;
     L.ctas = mixed_ctas();
     L.meta = take(sizeof(BlockMeta) * (size_t)nb1);
@@ -108,7 +152,7 @@ static Layout work_layout(const Plan& P) {
     L.status = take(sizeof(Status));
     L.partial = take(sizeof(double) * (size_t)stats_partial_doubles(P));
     L.staging = take((size_t)(align_up(P.pt_count * 4, 16) + 48 * nb1 + 64));
-    L.q_scr = take(sizeof(int32_t) * (size_t)L.ctas * kMaxMixedN * (size_t)P.lmax);
+    L.q_scr = take(sizeof(int32_t) * (size_t)L.ctas * kMaxMixedN * (size_t)align_up(P.lmax, 4));
     L.k8_scr = take((size_t)L.ctas * (size_t)npt);
     L.k32_scr = take(sizeof(int32_t) * (size_t)L.ctas * (size_t)npt);
     L.feat = take(sizeof(float) * 32 * (size_t)nb1);
@@ -232,8 +276,8 @@ static MixedWork mixed_work(const Plan& P, const Layout& L, void* ws) {
   mw.k32_scr = (int32_t*)(b + L.k32_scr);
   mw.feat = (float*)(b + L.feat);
   mw.ranks = (int32_t*)(b + L.ranks);
-  mw.lmax = P.lmax;
-  mw.nptmax = (int64_t)P.nmax * P.lmax;
+  mw.lmax = align_up(P.lmax, 4);
+  mw.nptmax = align_up((int64_t)P.nmax * P.lmax, 16);
   mw.ctas = L.ctas;
   mw.phase = (unsigned long long*)(b + L.phase);
   return mw;
@@ -243,7 +287,8 @@ static MixedWork mixed_work(const Plan& P, const Layout& L, void* ws) {
 // reset, bound resolution, the per-block kernel of the chosen form, the scan
 // writing header and offset table, and the record packer / compaction.
 static int enqueue_compress(const Plan& P, const Layout& L, const void* d_in, void* d_out, size_t out_cap,
-                            void* d_ws, int variant, cudaStream_t s) {
+                            void* d_ws, int variant, cudaStream_t s, cudaEvent_t ev0 = nullptr,
+                            cudaEvent_t ev1 = nullptr) {
   int st;
   Work w = carve(L, d_ws);
   CK(cudaMemsetAsync(w.status, 0, sizeof(Status), s));
@@ -253,11 +298,15 @@ static int enqueue_compress(const Plan& P, const Layout& L, const void* d_in, vo
     const MixedWork mw = mixed_work(P, L, d_ws);
     CK(cudaMemsetAsync(mw.phase, 0, sizeof(unsigned long long) * (size_t)L.ctas * kMixedPhases, s));
     const int mode = P.rank_mode == DLS_RANK_LEARNED ? kRankMlp : (P.rank_mode == DLS_RANK_TAIL ? kRankTail : kRankSearch);
-    if ((st = launch_mixed_compress(P, d_in, mw, mode, variant, s)) != DLS_OK) return st;
+    if (ev0) CK(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
+    if ((st = launch_mixed_all(P, d_in, mw, mode, variant, s)) != DLS_OK) return st;
+    if (ev1) CK(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
     if ((st = launch_scan(P, w, out_cap, d_out, s)) != DLS_OK) return st;
     if ((st = launch_compact(P, mw, d_out, s)) != DLS_OK) return st;
   } else {
+    if (ev0) CK(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
     if ((st = launch_plain_compress(P, d_in, w, s)) != DLS_OK) return st;
+    if (ev1) CK(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
     if ((st = launch_scan(P, w, out_cap, d_out, s)) != DLS_OK) return st;
     if ((st = launch_pack(P, d_in, w, d_out, out_cap, s)) != DLS_OK) return st;
   }
@@ -279,6 +328,8 @@ struct dls_plan {
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   dls::Status* h_status;   // pinned
+  cudaEvent_t kev[2];      // recorded around the per-block kernels inside the graph
+  int kernel_nodes;
 };
 
 namespace dls {
@@ -381,6 +432,7 @@ int dls_compress(const dls_params* p, const void* d_in, void* d_out, size_t out_
   Status hs;
   CK(cudaMemcpyAsync(&hs, w.status, sizeof(Status), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (hs.timeout) return DLS_ERR_TIMEOUT;
   if (hs.nonfinite) return DLS_ERR_NONFINITE;
   *out_bytes = (size_t)hs.total_bytes;
   if (hs.capacity) return DLS_ERR_CAPACITY;
@@ -458,12 +510,13 @@ int dls_block_features(const dls_params* p, const void* d_in, float* d_feat, int
   mw.meta = w.meta; mw.offsets = w.offsets; mw.vars = w.vars; mw.status = w.status;
   mw.staging = b + L.staging; mw.q_scr = (int32_t*)(b + L.q_scr); mw.k8_scr = (int8_t*)(b + L.k8_scr);
   mw.k32_scr = (int32_t*)(b + L.k32_scr); mw.feat = d_feat; mw.ranks = d_rank;
-  mw.lmax = P.lmax; mw.nptmax = (int64_t)P.nmax * P.lmax; mw.ctas = L.ctas;
+  mw.lmax = align_up(P.lmax, 4); mw.nptmax = align_up((int64_t)P.nmax * P.lmax, 16); mw.ctas = L.ctas;
   mw.phase = (unsigned long long*)(b + L.phase);
-  if ((st = launch_mixed_compress(P, d_in, mw, kRankSearch, 2, s)) != DLS_OK) return st;
+  if ((st = launch_mixed_all(P, d_in, mw, kRankSearch, 2, s)) != DLS_OK) return st;
   Status hs;
   CK(cudaMemcpyAsync(&hs, w.status, sizeof(Status), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (hs.timeout) return DLS_ERR_TIMEOUT;
   return hs.nonfinite ? DLS_ERR_NONFINITE : DLS_OK;
 }
 
@@ -540,13 +593,19 @@ int dls_plan_create(const dls_params* p, const void* d_in, void* d_out, size_t o
   pl->graph = nullptr;
   pl->exec = nullptr;
   pl->h_status = nullptr;
+  pl->kev[0] = pl->kev[1] = nullptr;
+  pl->kernel_nodes = 0;
   auto fail = [&](int code) {
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
     if (pl->graph) cudaGraphDestroy(pl->graph);
     if (pl->h_status) cudaFreeHost(pl->h_status);
+    for (int i = 0; i < 2; ++i)
+      if (pl->kev[i]) cudaEventDestroy(pl->kev[i]);
     delete pl;
     return code;
   };
+  if (cudaEventCreate(&pl->kev[0]) != cudaSuccess || cudaEventCreate(&pl->kev[1]) != cudaSuccess)
+    return fail(DLS_ERR_CUDA);
   if (cudaHostAlloc((void**)&pl->h_status, sizeof(Status), cudaHostAllocDefault) != cudaSuccess) return fail(DLS_ERR_CUDA);
   // autotune: time each occupancy variant of the per-block kernel on the real work
   if (L.mixed) {
@@ -579,7 +638,7 @@ int dls_plan_create(const dls_params* p, const void* d_in, void* d_out, size_t o
     cudaStreamDestroy(cs);
     return fail(DLS_ERR_CUDA);
   }
-  st = enqueue_compress(P, L, d_in, d_out, out_cap, d_workspace, pl->variant, cs);
+  st = enqueue_compress(P, L, d_in, d_out, out_cap, d_workspace, pl->variant, cs, pl->kev[0], pl->kev[1]);
   Work w = carve(L, d_workspace);
   cudaError_t ce = cudaMemcpyAsync(pl->h_status, w.status, sizeof(Status), cudaMemcpyDeviceToHost, cs);
   cudaGraph_t g = nullptr;
@@ -590,6 +649,15 @@ int dls_plan_create(const dls_params* p, const void* d_in, void* d_out, size_t o
     return fail(st != DLS_OK ? st : DLS_ERR_CUDA);
   }
   pl->graph = g;
+  size_t nn = 0;
+  if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+      for (size_t i = 0; i < nn; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++pl->kernel_nodes;
+      }
+  }
   if (cudaGraphInstantiate(&pl->exec, g, 0) != cudaSuccess) return fail(DLS_ERR_CUDA);
   *out_plan = pl;
   return DLS_OK;
@@ -601,6 +669,7 @@ int dls_plan_execute(dls_plan* pl, size_t* out_bytes, dls_stream_t stream) {
   CK(cudaGraphLaunch(pl->exec, s));
   CK(cudaStreamSynchronize(s));
   const Status hs = *pl->h_status;
+  if (hs.timeout) return DLS_ERR_TIMEOUT;
   if (hs.nonfinite) return DLS_ERR_NONFINITE;
   *out_bytes = (size_t)hs.total_bytes;
   if (hs.capacity) return DLS_ERR_CAPACITY;
@@ -614,11 +683,23 @@ int dls_plan_info(const dls_plan* pl, int32_t* variant, float* tune_ms) {
   return DLS_OK;
 }
 
+int dls_plan_timing(const dls_plan* pl, float* kernel_ms, int32_t* kernel_nodes) {
+  if (!pl) return DLS_ERR_INVALID_ARG;
+  if (kernel_nodes) *kernel_nodes = pl->kernel_nodes;
+  if (kernel_ms) {
+    CK(cudaEventSynchronize(pl->kev[1]));
+    CK(cudaEventElapsedTime(kernel_ms, pl->kev[0], pl->kev[1]));
+  }
+  return DLS_OK;
+}
+
 int dls_plan_destroy(dls_plan* pl) {
   if (!pl) return DLS_OK;
   if (pl->exec) cudaGraphExecDestroy(pl->exec);
   if (pl->graph) cudaGraphDestroy(pl->graph);
   if (pl->h_status) cudaFreeHost(pl->h_status);
+  for (int i = 0; i < 2; ++i)
+    if (pl->kev[i]) cudaEventDestroy(pl->kev[i]);
   delete pl;
   return DLS_OK;
 }

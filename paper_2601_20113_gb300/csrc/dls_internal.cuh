@@ -214,7 +214,7 @@ struct MixedWork {
   unsigned long long* phase;   // ctas x kMixedPhases cycle counters
 };
 constexpr int kMaxMixedN = 16;
-constexpr int kMixedPhases = 12;
+constexpr int kMixedPhases = 13;
 
 // Block-rank MLP: 32 features -> 64 -> 64 -> 1 (ReLU).  Parameter vector layout
 // (floats): [mu 32][sigma 32][W1 64x32][b1 64][W2 64x64][b2 64][W3 64][b3 1].
@@ -231,7 +231,10 @@ constexpr int kRankSearch = 0, kRankMlp = 1, kRankTail = 2;
 
 // ---------------------------------------------------------------- launchers (defined in .cu files)
 int launch_mixed_compress(const Plan& p, const void* d_in, const MixedWork& w, int learned, int variant,
-                          cudaStream_t s);
+                          int spatial_only, cudaStream_t s);
+int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, int learned, int variant,
+                         cudaStream_t s);
+bool tile_chunk_box(const Plan& p, int* bxb, int* yc, int* zc, int* bt);
 int launch_compact(const Plan& p, const MixedWork& w, void* d_out, cudaStream_t s);
 size_t mixed_smem_bytes();
 int launch_mlp_train(float* params, float* adam, const float* feat, const float* target, const int32_t* order,

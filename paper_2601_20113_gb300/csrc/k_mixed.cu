@@ -16,21 +16,17 @@
 // evaluation decides when its rounding error bound leaves no doubt, and the
 // FP64 definition is evaluated otherwise, so the decisions equal the ones the
 // FP64 definitions give on the same coefficients and reconstructions.
-#include <cuda_bf16.h>
-
 #include <mutex>
 
-#include "dls_device.cuh"
+#include "mixed_common.cuh"
 
 namespace dls {
 namespace {
 
 constexpr int kMT = 256;                 // threads per CTA
-constexpr int NM = 16;                   // largest Gram order on this path
 constexpr int kNP = NM * (NM + 1) / 2;   // packed upper triangle (136)
 constexpr int kHalf = kNP / 2;           // pairs per thread group (68)
 constexpr int kGrp = kMT / 2;            // threads per group
-constexpr float kTwo24 = 16777216.0f;
 constexpr int kTab = 8192;               // row-offset table entries (spatial points of a block)
 
 struct MxArgs {
@@ -48,22 +44,21 @@ struct MxArgs {
   int64_t lmax, nptmax;
   int learned;             // 1: check the predicted rank first
   unsigned long long* phase;   // per CTA: kPhases cycle counters (may be null)
+  int spatial_only;            // 1: take only blocks whose Gram side is space
 };
 // Phases timed by the per-CTA cycle counters.
 enum { kPhGram = 0, kPhJacobi, kPhRefine, kPhRR, kPhPredict, kPhEncode, kPhDecide, kPhSearch, kPhPack,
-       kCntAccepted, kCntSearched, kCntExact, kPhases };
+       kCntAccepted, kCntSearched, kCntExact, kPhTileWait, kPhases };
 
 struct MxSmem {
   float G32[NM * NM];
-  float Hj[NM * NM], G2j[NM * NM], Vj[NM * NM];
+  float Vj[NM * NM];
   double G64[NM * NM], X64[NM * NM], R64[NM * NM], GV64[NM * NM], S64[NM * NM], E64[NM * NM];
   double lam_t[NM];        // refined eigenvalues (unsorted)
   double lam[NM];          // sorted
   float Vst[NM * NM];      // stored basis, Vst[j*NM + k]
   float vsum[NM];          // sum_j Vst[j][k] (for the shifted projection)
   float red[8][kNP + 8];
-  float jc[NM / 2], js[NM / 2], jt[NM / 2];
-  int jp[NM / 2], jq[NM / 2], jact[NM / 2], rowpair[NM];
   double dlt;
   float ered[8][NM + 2];
   double Ered[NM + 2];
@@ -86,60 +81,7 @@ struct MxSmem {
 
 // ---------------------------------------------------------------- rank model
 // The trained block-rank MLP, one copy per device (set by dls_set_rank_model).
-struct MlpModel {
-  float mu[kMlpF], sig[kMlpF];
-  float b1[kMlpH], b2[kMlpH], W3[kMlpH], b3;
-  __nv_bfloat16 W1[kMlpH * kMlpF], W2[kMlpH * kMlpH];
-};
 static __device__ MlpModel g_rank_model;
-
-// ---------------------------------------------------------------- exact decisions
-// q = rint((double)c / delta) with ties to even; *ovf when |c / delta| >= 2^24.
-__device__ __forceinline__ int32_t quant_exact(float c, double delta, float inv_delta, int& ovf) {
-  const float y = __fmul_rn(c, inv_delta);
-  const float ay = fabsf(y);
-  const float m = __fmul_rn(ay, 4.0e-7f) + 1.0e-30f;   // > 3 * 2^-24 |y| + FP64 rounding
-  const float r = rintf(y);
-  const float fr = fabsf(__fsub_rn(y, r));
-  if (fr < 0.5f - m && ay < kTwo24 * 0.999999f) return (int32_t)r;
-  const double Y = __ddiv_rn((double)c, delta);
-  if (!(fabs(Y) < 16777216.0)) { ovf = 1; return 0; }
-  return (int32_t)rint(Y);
-}
-
-struct CorrConst {
-  double eb, step;
-  float step_f, inv_step_f, eb_lo_f, eb_hi_f;
-};
-
-// Pointwise correction with the FP64 definition: returns k (0 if none) or
-// kEscape.  xt receives the corrected value when not escaped.
-__device__ __forceinline__ int32_t corr_exact(float x, float xh, const CorrConst& cc) {
-  const float R = __fsub_rn(x, xh);
-  const float y = __fmul_rn(R, cc.inv_step_f);
-  const float ay = fabsf(y);
-  const float m = __fmul_rn(ay, 5.0e-7f) + 1.0e-30f;
-  if (ay < 0.5f - m) return 0;            // |x - xhat| < eb certainly: k = 0, in bound
-  double kk;
-  const float r = rintf(y);
-  const float fr = fabsf(__fsub_rn(y, r));
-  if (fr < 0.5f - m) kk = (double)r;
-  else kk = rint(__ddiv_rn(__dsub_rn((double)x, (double)xh), cc.step));
-  float xt;
-  if (kk == 0.0) {
-    xt = xh;
-  } else {
-    if (fabs(kk) > kKmax) return kEscape;
-    xt = __fmaf_rn((float)kk, cc.step_f, xh);
-  }
-  const float d = fabsf(__fsub_rn(x, xt));
-  bool ok;
-  if (d <= cc.eb_lo_f) ok = true;
-  else if (d >= cc.eb_hi_f) ok = false;
-  else ok = !(fabs(__dsub_rn((double)x, (double)xt)) > cc.eb);
-  if (!ok) return kEscape;
-  return (int32_t)kk;
-}
 
 // ---------------------------------------------------------------- block geometry helpers
 // Offset of spatial point ls from the block origin.
@@ -205,125 +147,6 @@ __device__ void cta_reduce_floats(MxSmem& S, float* v, int cnt) {
     S.Ered[tid] = (double)s;
   }
   __syncthreads();
-}
-
-// ---------------------------------------------------------------- FP32 Jacobi (warp 0)
-__device__ __forceinline__ void rr_pair(int round, int i, int m, int& p, int& q) {
-  int a, b;
-  if (i == 0) { a = m - 1; b = round; }
-  else { a = (round + i) % (m - 1); b = (round - i + (m - 1)) % (m - 1); }
-  p = a < b ? a : b;
-  q = a < b ? b : a;
-}
-
-// relative = false: skip |g_pq| <= 1e-6 trace(G); relative = true: skip
-// |g_pq| <= 1e-7 sqrt(g_pp g_qq) (accurate for nearly diagonal graded matrices).
-__device__ void jacobi32_warp(MxSmem& S, int n, int lane, bool relative) {
-  float* G = S.G32;
-  float* H = S.Hj;
-  float* G2 = S.G2j;
-  float* V = S.Vj;
-  if (lane < n)
-    for (int b = 0; b < n; ++b) V[lane * NM + b] = (lane == b) ? 1.0f : 0.0f;
-  float tr = 0.0f;
-  if (lane == 0)
-    for (int i = 0; i < n; ++i) tr += G[i * NM + i];
-  tr = __shfl_sync(0xffffffffu, tr, 0);
-  const float tol = 1.0e-5f * tr;
-  const int m = n + (n & 1);
-  __syncwarp();
-  for (int sweep = 0; sweep < 30 && n > 1; ++sweep) {
-    int rotated = 0;
-    for (int round = 0; round < m - 1; ++round) {
-      if (lane < n) S.rowpair[lane] = -1;
-      __syncwarp();
-      int act = 0;
-      if (lane < m / 2) {
-        int p, q;
-        rr_pair(round, lane, m, p, q);
-        S.jp[lane] = p;
-        S.jq[lane] = q;
-        if (q < n) {
-          const float apq = G[p * NM + q];
-          // relative: a threshold FP32 can reach on graded matrices (rounding of
-          // the rotated entries is ~2^-24 of the larger diagonal)
-          const float gpp = fabsf(G[p * NM + p]), gqq = fabsf(G[q * NM + q]);
-          const float thr = relative ? fmaxf(1.0e-7f * sqrtf(gpp * gqq), 4.0f * 5.9604645e-8f * fmaxf(gpp, gqq)) : tol;
-          if (fabsf(apq) > thr && apq != 0.0f) {
-            const float theta = (G[q * NM + q] - G[p * NM + p]) / (2.0f * apq);
-            float t;
-            if (fabsf(theta) > 1e18f) t = 0.5f / theta;
-            else t = (theta >= 0.0f ? 1.0f : -1.0f) / (fabsf(theta) + sqrtf(1.0f + theta * theta));
-            const float c = 1.0f / sqrtf(1.0f + t * t);
-            S.jc[lane] = c;
-            S.js[lane] = t * c;
-            S.jt[lane] = t;
-            act = 1;
-            S.rowpair[p] = lane;
-            S.rowpair[q] = lane;
-          }
-        }
-        S.jact[lane] = act;
-      }
-      rotated += __popc(__ballot_sync(0xffffffffu, act));
-      __syncwarp();
-      if (lane < n) {
-        const int a = lane, i = S.rowpair[a];
-        if (i >= 0) {
-          const int p = S.jp[i], q = S.jq[i];
-          const float c = S.jc[i], s = S.js[i];
-          if (a == p)
-            for (int b = 0; b < n; ++b) H[a * NM + b] = c * G[p * NM + b] - s * G[q * NM + b];
-          else
-            for (int b = 0; b < n; ++b) H[a * NM + b] = s * G[p * NM + b] + c * G[q * NM + b];
-        } else {
-          for (int b = 0; b < n; ++b) H[a * NM + b] = G[a * NM + b];
-        }
-      }
-      __syncwarp();
-      if (lane < n) {
-        const int a = lane;
-        for (int b = a; b < n; ++b) {
-          const int i = S.rowpair[b];
-          float v;
-          if (i >= 0) {
-            const int p = S.jp[i], q = S.jq[i];
-            const float c = S.jc[i], s = S.js[i];
-            v = (b == p) ? c * H[a * NM + p] - s * H[a * NM + q] : s * H[a * NM + p] + c * H[a * NM + q];
-          } else {
-            v = H[a * NM + b];
-          }
-          G2[a * NM + b] = v;
-          G2[b * NM + a] = v;
-        }
-      }
-      __syncwarp();
-      if (lane < m / 2 && S.jact[lane]) {
-        const int p = S.jp[lane], q = S.jq[lane];
-        const float t = S.jt[lane], gpq = G[p * NM + q];
-        G2[p * NM + p] = G[p * NM + p] - t * gpq;
-        G2[q * NM + q] = G[q * NM + q] + t * gpq;
-        G2[p * NM + q] = 0.0f;
-        G2[q * NM + p] = 0.0f;
-      }
-      if (lane < n) {
-        const int a = lane;
-        for (int i = 0; i < m / 2; ++i) {
-          if (!S.jact[i]) continue;
-          const int p = S.jp[i], q = S.jq[i];
-          const float c = S.jc[i], s = S.js[i];
-          const float vp = V[a * NM + p], vq = V[a * NM + q];
-          V[a * NM + p] = c * vp - s * vq;
-          V[a * NM + q] = s * vp + c * vq;
-        }
-      }
-      __syncwarp();
-      if (lane < n)
-        for (int b = 0; b < n; ++b) G[lane * NM + b] = G2[lane * NM + b];
-      __syncwarp();
-    }
-    if (rotated == 0) break;
-  }
 }
 
 // ---------------------------------------------------------------- FP64 refinement (all threads)
@@ -991,33 +814,6 @@ __device__ int predict_rank(const MxArgs& a, MxSmem& S, const Geom& g, int64_t b
   return rp;
 }
 
-// MLP prediction from S.featv by warp 0 (BF16 weights, FP32 accumulation).
-__device__ int mlp_rank(MxSmem& S, int lane, int rcap) {
-  const MlpModel& M = g_rank_model;
-  float z = 0.0f;
-  if (lane < kMlpF) z = (S.featv[lane] - M.mu[lane]) / M.sig[lane];
-  for (int hh = 0; hh < 2; ++hh) {
-    const int h = lane + 32 * hh;
-    float acc = M.b1[h];
-    for (int f = 0; f < kMlpF; ++f) acc = fmaf(__bfloat162float(M.W1[h * kMlpF + f]), __shfl_sync(0xffffffffu, z, f), acc);
-    S.mh1[h] = acc > 0.0f ? acc : 0.0f;
-  }
-  __syncwarp();
-  float out = 0.0f;
-  for (int hh = 0; hh < 2; ++hh) {
-    const int h = lane + 32 * hh;
-    float acc = M.b2[h];
-    for (int k = 0; k < kMlpH; ++k) acc = fmaf(__bfloat162float(M.W2[h * kMlpH + k]), S.mh1[k], acc);
-    acc = acc > 0.0f ? acc : 0.0f;
-    out = fmaf(M.W3[h], acc, out);
-  }
-  for (int o = 16; o > 0; o >>= 1) out += __shfl_xor_sync(0xffffffffu, out, o);
-  out += M.b3;
-  int r = (int)rintf(out);
-  r = r < 0 ? 0 : (r > rcap ? rcap : r);
-  return r;
-}
-
 // ---------------------------------------------------------------- the persistent kernel
 __device__ __forceinline__ void mixed_body(const MxArgs& a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1038,7 +834,14 @@ __device__ __forceinline__ void mixed_body(const MxArgs& a) {
     tck = now;
   };
   for (;;) {
-    if (tid == 0) S.bi = (int64_t)atomicAdd(&a.status->pad[0], 1ull);
+    if (tid == 0) {
+      int64_t b;
+      for (;;) {
+        b = (int64_t)atomicAdd(&a.status->pad[0], 1ull);
+        if (b >= P.nb || !a.spatial_only || block_geom(P, P.b0 + b).side == 1) break;
+      }
+      S.bi = b;
+    }
     __syncthreads();
     const int64_t bi = S.bi;
     if (bi >= P.nb) break;
@@ -1069,7 +872,7 @@ __device__ __forceinline__ void mixed_body(const MxArgs& a) {
       __syncthreads();
       continue;
     }
-    if (warp == 0) jacobi32_warp(S, n, lane, false);
+    if (warp == 0) jacobi_reg<NM>(S.G32, NM, n, true, 0.0f, S.Vj, NM, S.lam_t, lane);
     __syncthreads();
     mark(kPhJacobi);
     refine64(S, n);
@@ -1085,7 +888,7 @@ __device__ __forceinline__ void mixed_body(const MxArgs& a) {
       const double noise = (P.eb_type == DLS_EB_NRMSE ? el2 / n : budget);
       if (n > 1 && 4.0 * 5.9604644775390625e-8 * tr > 0.1 * noise) {
         pass_gram(a, S, g, true);
-        if (warp == 0) jacobi32_warp(S, n, lane, true);
+        if (warp == 0) jacobi_reg<NM>(S.G32, NM, n, true, 0.0f, S.Vj, NM, S.lam_t, lane);
         __syncthreads();
         // V = Vst W in FP64, eigenvalues from the rotated diagonal
         {
@@ -1095,7 +898,6 @@ __device__ __forceinline__ void mixed_body(const MxArgs& a) {
             for (int k = 0; k < n; ++k) v = fma((double)S.Vst[i * NM + k], (double)S.Vj[k * NM + j], v);
             S.X64[i * NM + j] = v;
           }
-          if (tid < n) S.lam_t[tid] = (double)S.G32[tid * NM + tid];
         }
         __syncthreads();
         // first-order orthonormalisation in FP64: V <- V (I + R/2), R = I - V^T V
@@ -1134,7 +936,7 @@ __device__ __forceinline__ void mixed_body(const MxArgs& a) {
     }
     __syncthreads();
     if (a.learned == kRankMlp && warp == 0) {
-      const int rm = mlp_rank(S, lane, rcap);
+      const int rm = mlp_rank_warp(&g_rank_model, S.featv, S.mh1, lane, rcap);
       if (lane == 0) S.r_pred = rm;
     }
     __syncthreads();
@@ -1223,13 +1025,7 @@ __global__ void k_stage_quantize(const float* c, int64_t n, double delta, int32_
 }
 
 __global__ void k_stage_correct(const float* x, const float* xh, int64_t n, double eb, int32_t* k) {
-  CorrConst cc;
-  cc.eb = eb;
-  cc.step = 2.0 * eb;
-  cc.step_f = __double2float_rn(cc.step);
-  cc.inv_step_f = __double2float_rn(1.0 / cc.step);
-  cc.eb_lo_f = __double2float_rd(eb * (1.0 - 1e-6));
-  cc.eb_hi_f = __double2float_ru(eb * (1.0 + 1e-6));
+  const CorrConst cc = make_corr_const(eb, 2.0 * eb, true);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     k[i] = corr_exact(x[i], xh[i], cc);
 }
@@ -1254,6 +1050,15 @@ namespace {
 std::mutex g_model_mu;
 bool g_model_loaded[64] = {};
 }  // namespace
+
+const MlpModel* rank_model_device() {
+  void* p = nullptr;
+  if (!rank_model_loaded() || cudaGetSymbolAddress(&p, g_rank_model) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return reinterpret_cast<const MlpModel*>(p);
+}
 
 bool rank_model_loaded() {
   int dev = 0;
@@ -1293,9 +1098,10 @@ extern "C" int dls_set_rank_model(const float* h_params, size_t count) {
 namespace dls {
 
 int launch_mixed_compress(const Plan& p, const void* d_in, const MixedWork& w, int learned, int variant,
-                          cudaStream_t s) {
+                          int spatial_only, cudaStream_t s) {
   if (p.nb == 0) return DLS_OK;
   MxArgs a;
+  a.spatial_only = spatial_only;
   a.P = p;
   a.in = (const float*)d_in;
   a.staging = w.staging;
@@ -1312,7 +1118,11 @@ int launch_mixed_compress(const Plan& p, const void* d_in, const MixedWork& w, i
   a.learned = learned;
   a.phase = w.phase;
   const size_t smem = sizeof(MxSmem);
-  const int ctas = variant == 1 ? w.ctas / 2 : w.ctas;
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return DLS_ERR_CUDA;
+  int ctas = variant == 1 ? sms : 2 * sms;
+  if (ctas > w.ctas) ctas = w.ctas;
   const int grid = (int)(p.nb < ctas ? p.nb : ctas);
   if (variant == 1) {
     if (cudaFuncSetAttribute(k_mixed<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)

@@ -1,0 +1,1482 @@
+// Staged-tile mixed-precision kernel for float32 fields: the blocks whose
+// Gram side is time (T_b <= M_b, Gram order n = T_b <= 16), which is every
+// block of the usual shapes.  (Blocks with M_b < T_b go to k_mixed.cu.)
+//
+// Per block (Algorithm 1 step 3 of arXiv 2601.20113, pointwise-bound reading),
+// one CTA of 4 warps, several CTAs per SM, persistent over an atomic counter:
+//   Gram pass    the block streams through a two-stage shared-memory ring
+//                (TMA tensor tiles, or cp.async where the field's x extent is
+//                not 16-byte aligned); FP32 Gram G = A^T A (Sec. 2.7.1) and
+//                the block statistics
+//   eigensolve   register Jacobi in FP32 (one warp), one FP64 Ogita-Aishima
+//                refinement, and a Rayleigh-Ritz pass for tight bounds
+//   rank         predicted rank checked exactly, else the bisection of
+//                Algorithm 1 on E(r)
+//   encode pass  projection, quantization, decode, E(r-1), E(r), pointwise
+//                correction, one row per thread from the staged tile
+//   pack         the record, written into the block's staging slot with
+//                word-aligned bit packing and warp-level compaction
+// Every stored decision has FP64 semantics (see mixed_common.cuh).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "mixed_common.cuh"
+
+namespace dls {
+namespace {
+
+constexpr int kTT = 128;                  // threads per CTA
+constexpr int kWarps = kTT / 32;
+constexpr int kStages = 2;
+constexpr int kStageFloats = 4096;        // 16 KiB per stage
+constexpr int kNP = NM * (NM + 1) / 2;    // packed Gram pairs (136)
+constexpr int kHalf = kNP / 2;            // pairs per thread group (68)
+constexpr int kGT = kTT / 2;              // threads per Gram group
+constexpr unsigned FULL = 0xffffffffu;
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+enum { kPhGram = 0, kPhJacobi, kPhRefine, kPhRR, kPhPredict, kPhEncode, kPhDecide, kPhSearch, kPhPack,
+       kCntAccepted, kCntSearched, kCntExact, kPhTileWait, kPhases };
+static_assert(kPhases == kMixedPhases, "phase counter layout");
+
+struct TileArgs {
+  Plan P;
+  const float* in;
+  uint8_t* staging;
+  BlockMeta* meta;
+  VarInfo* vars;
+  Status* status;
+  int32_t* q_scr;
+  int8_t* k8_scr;
+  int32_t* k32_scr;
+  float* feat;
+  int32_t* ranks;
+  int64_t lmax, nptmax;
+  int learned;
+  unsigned long long* phase;
+  const MlpModel* model;
+  int use_tma;
+  int bxb, yc, zc, bt;     // chunk box (x, y, z, t)
+  int rc;                  // rows per chunk = bxb * yc * zc
+  uint32_t mbx, myc;       // ceil(2^32 / bxb), ceil(2^32 / yc) (0 for a divisor of 1)
+  double jfloor;           // Jacobi skip floor as a fraction of the per-mode budget
+};
+
+struct __align__(128) TileSmem {
+  float ring[kStages][kStageFloats];
+  unsigned long long full[kStages];
+  float G32[NM * NM];
+  float Vj[NM * NM];
+  __align__(16) float VstT[NM * NM];     // VstT[k * NM + j] = Vst[j][k]
+  float vsum[NM];
+  double G64[NM * NM], X64[NM * NM], R64[NM * NM], T64[NM * NM];
+  double lam_t[NM], lam[NM];
+  float red[kWarps][kNP + 8];
+  float ered[kWarps][NM + 2];
+  double Ered[NM + 2];
+  double dlt;
+  float featv[kMlpF];
+  float mh1[kMlpH];
+  float st_min[kWarps], st_max[kWarps], st_tg[kWarps], st_xg[kWarps], st_rowmax[kWarps];
+  int wq[NM];
+  uint32_t qor[kWarps][NM];
+  int kmax, ncorr, nesc, ovf, nonfinite, abort_flag;
+  int64_t bi, bnext;
+  int r_pred;
+  unsigned nexact;
+  int warp_cnt[kWarps];
+  int64_t colbase[NM + 1];
+  unsigned long long ph[kPhases];   // cycle counters of this CTA (thread 0)
+  BlockMeta m;
+  RecLayout lay;
+};
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false after kWaitLimit polls.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity) {
+  for (uint32_t i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(b, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, unsigned long long* bar, int c0, int c1,
+                                            int c2, int c3, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6, %7}], "
+      "[%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+      : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_arrive(unsigned long long* b) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+// ---------------------------------------------------------------- chunk geometry
+// A block is cut into chunks of zc z-planes x yc y-lines (all x, all t); the
+// chunk's tile in shared memory is [t][z][y][x] with bxb x-values per line,
+// so row r of the chunk (x fastest) has its t-th value at t * rc + r.
+struct Chunks {
+  int ncy, ncz, n;
+};
+__device__ __forceinline__ Chunks chunks_of(const TileArgs& a, const Geom& g) {
+  Chunks c;
+  c.ncy = (int)cdiv(g.sy, a.yc);
+  c.ncz = (int)cdiv(g.sz, a.zc);
+  c.n = c.ncy * c.ncz;
+  return c;
+}
+// floor(r / d) for r, d < 2^12 by a multiply-high with m = ceil(2^32 / d)
+// (exact while r d < 2^32; m = 0 encodes d = 1).
+__device__ __forceinline__ int fdiv(int r, uint32_t m) { return m ? (int)__umulhi((uint32_t)r, m) : r; }
+
+// Row r of chunk c: its dense block row index l (x fastest over the block), or -1.
+__device__ __forceinline__ int row_index(const TileArgs& a, const Geom& g, const Chunks& ch, int c, int r, int* xo) {
+  const int t2 = fdiv(r, a.mbx);
+  const int x = r - t2 * a.bxb;
+  const int zl = fdiv(t2, a.myc);
+  const int yl = t2 - zl * a.yc;
+  const int cz = c / ch.ncy;
+  const int y = (c - cz * ch.ncy) * a.yc + yl, z = cz * a.zc + zl;
+  *xo = x;
+  if (x >= g.sx || y >= g.sy || z >= g.sz) return -1;
+  return (z * g.sy + y) * g.sx + x;
+}
+
+// Global index of block entry (row l, column j) of a side-0 block.
+__device__ __forceinline__ int64_t gidx_row(const TileArgs& a, const Geom& g, int64_t l, int j) {
+  const int64_t x = l % g.sx, r = l / g.sx;
+  const int64_t y = r % g.sy, z = r / g.sy;
+  return (int64_t)g.v * a.P.K + (g.t0 + j) * a.P.P + ((g.z0 + z) * a.P.dims[1] + (g.y0 + y)) * a.P.dims[0] +
+         (g.x0 + x);
+}
+
+__device__ void issue_chunk(const TileArgs& a, const CUtensorMap* tm, TileSmem& S, const Geom& g, const Chunks& ch,
+                            int c, uint32_t& iss) {
+  const int stage = (int)(iss % kStages);
+  const int yb = (c % ch.ncy) * a.yc, zb = (c / ch.ncy) * a.zc;
+  if (a.use_tma) {
+    if (threadIdx.x == 0) {
+      mbar_expect_tx(&S.full[stage], (unsigned)(a.rc * a.bt * 4));
+      tma_load_5d(&S.ring[stage][0], tm, &S.full[stage], (int)g.x0, (int)(g.y0 + yb), (int)(g.z0 + zb), (int)g.t0,
+                  g.v);
+    }
+  } else {
+    const Plan& P = a.P;
+    const int tot = a.rc * a.bt;
+    for (int e = threadIdx.x; e < tot; e += kTT) {
+      const int t = e / a.rc, r = e - t * a.rc;
+      const int x = r % a.bxb, t2 = r / a.bxb;
+      const int64_t gx = g.x0 + x, gy = g.y0 + yb + t2 % a.yc, gz = g.z0 + zb + t2 / a.yc, gt = g.t0 + t;
+      const bool ok = gx < P.dims[0] && gy < P.dims[1] && gz < P.dims[2] && gt < P.dims[3];
+      const float* src = ok ? a.in + (int64_t)g.v * P.K + gt * P.P + (gz * P.dims[1] + gy) * P.dims[0] + gx : a.in;
+      cp_async4(&S.ring[stage][e], src, ok);
+    }
+    cp_async_arrive(&S.full[stage]);
+  }
+  ++iss;
+}
+
+// Waits for the oldest chunk in flight; false (and the CTA's abort flag) on
+// timeout.  Thread 0 adds the cycles it waited to the tile-wait counter.
+__device__ __forceinline__ bool wait_chunk(TileSmem& S, uint32_t con) {
+  const int stage = (int)(con % kStages);
+  const long long t0 = threadIdx.x == 0 ? clock64() : 0;
+  const bool ok = mbar_wait(&S.full[stage], (con / kStages) & 1u);
+  if (!ok) S.abort_flag = 1;
+  if (threadIdx.x == 0) S.ph[kPhTileWait] += (unsigned long long)(clock64() - t0);
+  return ok;
+}
+
+// Ring cursor: chunks [0, pf_cnt) of block pf_blk are in flight.
+struct Cursor {
+  uint32_t iss, con;
+  int64_t pf_blk;
+  int pf_cnt;
+};
+
+__device__ void prefetch(const TileArgs& a, const CUtensorMap* tm, TileSmem& S, Cursor& cu, int64_t bi, const Geom& g) {
+  const Chunks ch = chunks_of(a, g);
+  const int k = ch.n < kStages ? ch.n : kStages;
+  for (int c = 0; c < k; ++c) issue_chunk(a, tm, S, g, ch, c, cu.iss);
+  cu.pf_blk = bi;
+  cu.pf_cnt = k;
+}
+
+// Drops chunks in flight that belong to another block.
+__device__ void drain(TileSmem& S, Cursor& cu) {
+  for (int i = 0; i < cu.pf_cnt; ++i) {
+    wait_chunk(S, cu.con);
+    ++cu.con;
+  }
+  cu.pf_cnt = 0;
+  cu.pf_blk = -1;
+  __syncthreads();
+}
+
+// Streams every chunk of block bi through the ring, calling body(c, tile) for
+// each; all threads call.  Returns false if a wait timed out.
+template <class F>
+__device__ bool stream_block(const TileArgs& a, const CUtensorMap* tm, TileSmem& S, Cursor& cu, int64_t bi,
+                             const Geom& g, F&& body) {
+  const Chunks ch = chunks_of(a, g);
+  if (cu.pf_blk != bi && cu.pf_cnt > 0) drain(S, cu);
+  const int have = cu.pf_blk == bi ? cu.pf_cnt : 0;
+  const int k = ch.n < kStages ? ch.n : kStages;
+  for (int c = have; c < k; ++c) issue_chunk(a, tm, S, g, ch, c, cu.iss);
+  cu.pf_cnt = 0;
+  cu.pf_blk = -1;
+  for (int c = 0; c < ch.n; ++c) {
+    wait_chunk(S, cu.con);
+    __syncthreads();
+    if (S.abort_flag) return false;
+    body(c, ch, &S.ring[cu.con % kStages][0]);
+    __syncthreads();
+    ++cu.con;
+    if (c + kStages < ch.n) issue_chunk(a, tm, S, g, ch, c + kStages, cu.iss);
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------- reductions
+// Fixed-order CTA reduction of cnt per-thread floats into S.Ered (double).
+__device__ void cta_reduce(TileSmem& S, const float* v, int cnt) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = 0; i < NM + 2; ++i) {
+    if (i >= cnt) break;
+    float x = v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = __fadd_rn(x, __shfl_xor_sync(FULL, x, o));
+    if (lane == 0) S.ered[warp][i] = x;
+  }
+  __syncthreads();
+  if (tid < cnt) {
+    float s = 0.0f;
+    for (int w = 0; w < kWarps; ++w) s = __fadd_rn(s, S.ered[w][tid]);
+    S.Ered[tid] = (double)s;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- Gram pass
+// Group g (2 warps) accumulates packed pairs [68 g, 68 g + 68) over every row;
+// each group gathers the statistics of every other row.  With `project`, rows
+// are first projected onto the current basis (Rayleigh-Ritz matrix).
+// NF = 16: the Gram order is 16 and known at compile time (no per-column
+// predicates); NF = 0: any order n <= 16.
+template <bool PROJECT, int NF>
+__device__ __noinline__ bool pass_gram(const TileArgs& a, const CUtensorMap* tm, TileSmem& S, Cursor& cu, int64_t bi,
+                          const Geom& g) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int grp = tid / kGT, gt = tid % kGT;
+  const int n = NF ? NF : g.n;
+  float acc[kHalf];
+#pragma unroll
+  for (int p = 0; p < kHalf; ++p) acc[p] = 0.0f;
+  float mn = INFINITY, mx = -INFINITY, xg = 0.0f;
+  const bool ok = stream_block(a, tm, S, cu, bi, g, [&](int c, const Chunks& ch, const float* tile) {
+    int ii = 0;
+    for (int r = gt; r < a.rc; r += kGT, ++ii) {
+      int xx;
+      const int l = row_index(a, g, ch, c, r, &xx);
+      if (l < 0) continue;
+      float x[NM];
+#pragma unroll
+      for (int j = 0; j < NM; ++j) x[j] = j < n ? tile[j * a.rc + r] : 0.0f;
+      if (PROJECT) {
+        const float a0 = x[0];
+        float cc[NM];
+#pragma unroll
+        for (int k = 0; k < NM; ++k) {
+          float v = 0.0f;
+          if (k < n) {
+#pragma unroll
+            for (int j = 0; j < NM; ++j)
+              if (j < n) v = __fmaf_rn(__fsub_rn(x[j], a0), S.VstT[k * NM + j], v);
+            v = __fmaf_rn(a0, S.vsum[k], v);
+          }
+          cc[k] = v;
+        }
+#pragma unroll
+        for (int k = 0; k < NM; ++k) x[k] = cc[k];
+      } else if ((ii & 1) == grp) {
+        // per-element statistics: range and x-gradient energy (the time
+        // gradient, the row-norm bound and the non-finite screen come from
+        // the Gram afterwards)
+#pragma unroll
+        for (int j = 0; j < NM; ++j) {
+          if (j < n) {
+            mn = fminf(mn, x[j]);
+            mx = fmaxf(mx, x[j]);
+          }
+        }
+        if (xx + 1 < g.sx) {
+#pragma unroll
+          for (int j = 0; j < NM; ++j)
+            if (j < n) { const float d = tile[j * a.rc + r + 1] - x[j]; xg = __fmaf_rn(d, d, xg); }
+        }
+      }
+      if (grp == 0) {
+#pragma unroll
+        for (int i = 0, p = 0; i < NM; ++i)
+#pragma unroll
+          for (int j = i; j < NM; ++j, ++p)
+            if (p < kHalf) acc[p] = __fmaf_rn(x[i], x[j], acc[p]);
+      } else {
+#pragma unroll
+        for (int i = 0, p = 0; i < NM; ++i)
+#pragma unroll
+          for (int j = i; j < NM; ++j, ++p)
+            if (p >= kHalf) acc[p - kHalf] = __fmaf_rn(x[i], x[j], acc[p - kHalf]);
+      }
+    }
+  });
+  if (!ok) return false;
+#pragma unroll
+  for (int p = 0; p < kHalf; ++p) {
+    float v = acc[p];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(FULL, v, o));
+    if (lane == 0) S.red[warp][p] = v;
+  }
+  if (!PROJECT) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mn = fminf(mn, __shfl_xor_sync(FULL, mn, o));
+      mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, o));
+      xg += __shfl_xor_sync(FULL, xg, o);
+    }
+    if (lane == 0) {
+      S.st_min[warp] = mn; S.st_max[warp] = mx; S.st_xg[warp] = xg;
+      S.st_tg[warp] = 0.0f; S.st_rowmax[warp] = 0.0f;
+    }
+  }
+  __syncthreads();
+  for (int p = tid; p < kNP; p += kTT) {
+    const int gw = (p / kHalf) * 2, pp = p % kHalf;
+    const float v = __fadd_rn(S.red[gw][pp], S.red[gw + 1][pp]);
+    int i = 0, rem = p;
+    while (rem >= NM - i) { rem -= NM - i; ++i; }
+    const int j = i + rem;
+    if (i < n && j < n) {
+      S.G32[i * NM + j] = v; S.G32[j * NM + i] = v;
+      S.G64[i * NM + j] = (double)v; S.G64[j * NM + i] = (double)v;
+    }
+  }
+  __syncthreads();
+  if (!PROJECT && tid == 0) {
+    // time-gradient energy sum_rows sum_j (x_{j+1} - x_j)^2 from the Gram;
+    // row-norm bound n max|x|^2; non-finite screen on the diagonal
+    float tg = 0.0f;
+    bool screen = false;
+    for (int j = 0; j < n; ++j) {
+      if (!isfinite(S.G32[j * NM + j])) screen = true;
+      if (j + 1 < n) tg += S.G32[(j + 1) * NM + j + 1] + S.G32[j * NM + j] - 2.0f * S.G32[j * NM + j + 1];
+    }
+    float mnn = S.st_min[0], mxx = S.st_max[0];
+    for (int w = 1; w < kWarps; ++w) { mnn = fminf(mnn, S.st_min[w]); mxx = fmaxf(mxx, S.st_max[w]); }
+    const float am = fmaxf(fabsf(mnn), fabsf(mxx));
+    S.st_tg[0] = fmaxf(tg, 0.0f);
+    S.st_rowmax[0] = (float)n * am * am;
+    S.nonfinite = screen ? 2 : 0;
+  }
+  __syncthreads();
+  if (!PROJECT && S.nonfinite == 2) {
+    // a non-finite diagonal: look for a non-finite input value exactly (a
+    // finite block whose squares overflow is not an input error)
+    int bad = 0;
+    for (int64_t e = tid; e < g.N; e += kTT) {
+      const int64_t lt = e / g.M, ls = e - lt * g.M;
+      if (!isfinite(__ldg(a.in + gidx_row(a, g, ls, (int)lt)))) bad = 1;
+    }
+    bad = __syncthreads_or(bad);
+    if (tid == 0) S.nonfinite = bad;
+    __syncthreads();
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------- FP64 refinement
+// One Ogita-Aishima step on A = G64 and the FP32 eigenvectors Vj:
+// R = I - X^T X, S = X^T A X, lambda_i = s_ii / (1 - r_ii),
+// E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) when the gap exceeds
+// delta = 2 (||S - diag S||_F + ||A||_F ||R||_F), else r_ij / 2; X <- X + X E.
+__device__ __noinline__ void refine64(TileSmem& S, int n) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < NM * NM; e += kTT) {
+    const int i = e / NM, j = e % NM;
+    if (i < n && j < n) S.X64[e] = (double)S.Vj[e];
+  }
+  __syncthreads();
+  for (int e = tid; e < NM * NM; e += kTT) {
+    const int i = e / NM, j = e % NM;
+    if (i < n && j < n) {
+      double gv = 0.0;
+      for (int k = 0; k < n; ++k) gv = fma(S.G64[i * NM + k], S.X64[k * NM + j], gv);
+      S.T64[e] = gv;
+      if (i <= j) {
+        double r = 0.0;
+        for (int k = 0; k < n; ++k) r = fma(S.X64[k * NM + i], S.X64[k * NM + j], r);
+        r = (i == j ? 1.0 : 0.0) - r;
+        S.R64[i * NM + j] = r;
+        S.R64[j * NM + i] = r;
+      }
+    }
+  }
+  __syncthreads();
+  // S = X^T (A X) (symmetric: upper triangle, mirrored) replaces A X in T64
+  double sv[2] = {0.0, 0.0};
+  int cnt = 0;
+  for (int e = tid; e < NM * NM; e += kTT, ++cnt) {
+    const int i = e / NM, j = e % NM;
+    double s = 0.0;
+    if (i < n && j < n && i <= j)
+      for (int k = 0; k < n; ++k) s = fma(S.X64[k * NM + i], S.T64[k * NM + j], s);
+    sv[cnt] = s;
+  }
+  __syncthreads();
+  cnt = 0;
+  for (int e = tid; e < NM * NM; e += kTT, ++cnt) {
+    const int i = e / NM, j = e % NM;
+    if (i < n && j < n && i <= j) { S.T64[i * NM + j] = sv[cnt]; S.T64[j * NM + i] = sv[cnt]; }
+  }
+  __syncthreads();
+  if (tid < 32) {
+    double offs = 0.0, g2 = 0.0, r2 = 0.0;
+    if (tid < n) {
+      S.lam_t[tid] = S.T64[tid * NM + tid] / (1.0 - S.R64[tid * NM + tid]);
+      for (int b = 0; b < n; ++b) {
+        if (b != tid) offs = fma(S.T64[tid * NM + b], S.T64[tid * NM + b], offs);
+        g2 = fma(S.G64[tid * NM + b], S.G64[tid * NM + b], g2);
+        r2 = fma(S.R64[tid * NM + b], S.R64[tid * NM + b], r2);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      offs += __shfl_xor_sync(FULL, offs, o);
+      g2 += __shfl_xor_sync(FULL, g2, o);
+      r2 += __shfl_xor_sync(FULL, r2, o);
+    }
+    if (tid == 0) S.dlt = 2.0 * (sqrt(offs) + sqrt(g2) * sqrt(r2));
+  }
+  __syncthreads();
+  // E into T64 (S no longer needed after this read)
+  double ev[2] = {0.0, 0.0};
+  cnt = 0;
+  for (int e = tid; e < NM * NM; e += kTT, ++cnt) {
+    const int i = e / NM, j = e % NM;
+    double v = 0.0;
+    if (i < n && j < n) {
+      if (i == j) {
+        v = 0.5 * S.R64[e];
+      } else {
+        const double li = S.lam_t[i], lj = S.lam_t[j];
+        const double d = lj - li;
+        if (fabs(d) > S.dlt) v = (S.T64[e] + lj * S.R64[e]) / d;
+        else v = 0.5 * S.R64[e];
+      }
+    }
+    ev[cnt] = v;
+  }
+  __syncthreads();
+  cnt = 0;
+  for (int e = tid; e < NM * NM; e += kTT, ++cnt) S.T64[e] = ev[cnt];
+  __syncthreads();
+  double xn[2] = {0.0, 0.0};
+  cnt = 0;
+  for (int e = tid; e < NM * NM; e += kTT, ++cnt) {
+    const int i = e / NM, j = e % NM;
+    if (i < n && j < n) {
+      double v = S.X64[e];
+      for (int k = 0; k < n; ++k) v = fma(S.X64[i * NM + k], S.T64[k * NM + j], v);
+      xn[cnt] = v;
+    }
+  }
+  __syncthreads();
+  cnt = 0;
+  for (int e = tid; e < NM * NM; e += kTT, ++cnt) {
+    const int i = e / NM, j = e % NM;
+    if (i < n && j < n) S.X64[e] = xn[cnt];
+  }
+  __syncthreads();
+}
+
+// Sort (stable, descending, lambda < 0 -> 0), sign-normalise, round to f32 (warp 0).
+__device__ void order_basis(TileSmem& S, int n, int lane) {
+  if (lane < n) {
+    const int k = lane;
+    double dk = S.lam_t[k];
+    dk = dk < 0.0 ? 0.0 : dk;
+    int pos = 0;
+    for (int j = 0; j < n; ++j) {
+      double dj = S.lam_t[j];
+      dj = dj < 0.0 ? 0.0 : dj;
+      if (dj > dk || (dj == dk && j < k)) ++pos;
+    }
+    int imax = 0;
+    double amax = -1.0;
+    for (int r = 0; r < n; ++r) {
+      const double av = fabs(S.X64[r * NM + k]);
+      if (av > amax) { amax = av; imax = r; }
+    }
+    const bool neg = S.X64[imax * NM + k] < 0.0;
+    S.lam[pos] = dk;
+    double cs = 0.0;
+    for (int r = 0; r < NM; ++r) {
+      float vf = 0.0f;
+      if (r < n) {
+        const double v = S.X64[r * NM + k];
+        vf = __double2float_rn(neg ? -v : v);
+        cs += (double)vf;
+      }
+      S.VstT[pos * NM + r] = vf;
+    }
+    S.vsum[pos] = (float)cs;
+  }
+  if (lane >= n && lane < NM) {
+    for (int r = 0; r < NM; ++r) S.VstT[lane * NM + r] = 0.0f;
+    S.vsum[lane] = 0.0f;
+  }
+  __syncwarp();
+}
+
+// ---------------------------------------------------------------- row arithmetic
+struct RowConst {
+  double delta;
+  float inv_delta, delta_f;
+};
+
+// Coefficient k of one row (shifted projection: sum_j (x_j - x_0) Vst[j][k]
+// + x_0 sum_j Vst[j][k], the differences exact when the row carries a large
+// common part), quantized with FP64 semantics and dequantized in float.
+// The encode, search and exact passes all call this, so all see the same numbers.
+template <int NF>
+__device__ __forceinline__ float coeff_q(const TileSmem& S, const float* d, float a0, int n_, int k,
+                                         const RowConst& rc, int32_t& q, int& ovf) {
+  const int n = NF ? NF : n_;
+  const float4* vp = reinterpret_cast<const float4*>(&S.VstT[k * NM]);
+  float c = 0.0f;
+#pragma unroll
+  for (int j4 = 0; j4 < NM / 4; ++j4) {
+    const float4 v = vp[j4];
+    if (4 * j4 + 0 < n) c = __fmaf_rn(d[4 * j4 + 0], v.x, c);
+    if (4 * j4 + 1 < n) c = __fmaf_rn(d[4 * j4 + 1], v.y, c);
+    if (4 * j4 + 2 < n) c = __fmaf_rn(d[4 * j4 + 2], v.z, c);
+    if (4 * j4 + 3 < n) c = __fmaf_rn(d[4 * j4 + 3], v.w, c);
+  }
+  c = __fmaf_rn(a0, S.vsum[k], c);
+  q = quant_exact(c, rc.delta, rc.inv_delta, ovf);
+  return __fmul_rn(__int2float_rn(q), rc.delta_f);
+}
+
+__device__ __forceinline__ void shifted(const float* x, float* d) {
+#pragma unroll
+  for (int j = 0; j < NM; ++j) d[j] = __fsub_rn(x[j], x[0]);
+}
+
+// acc[j] <- fma(ch[k], Vst[j][k], acc[j]) for one k (decode contract order).
+__device__ __forceinline__ void row_decode_step(const TileSmem& S, int k, float chk, float* acc) {
+  const float4* vp = reinterpret_cast<const float4*>(&S.VstT[k * NM]);
+#pragma unroll
+  for (int j4 = 0; j4 < NM / 4; ++j4) {
+    const float4 v = vp[j4];
+    acc[4 * j4 + 0] = __fmaf_rn(chk, v.x, acc[4 * j4 + 0]);
+    acc[4 * j4 + 1] = __fmaf_rn(chk, v.y, acc[4 * j4 + 1]);
+    acc[4 * j4 + 2] = __fmaf_rn(chk, v.z, acc[4 * j4 + 2]);
+    acc[4 * j4 + 3] = __fmaf_rn(chk, v.w, acc[4 * j4 + 3]);
+  }
+}
+
+
+// ---------------------------------------------------------------- encode pass
+// Projection, quantization and decode at rank r, q into the CTA scratch,
+// corrections into k8/k32; with `check`, FP32 estimates of E(r-1), E(r) land
+// in S.Ered[0], S.Ered[1].  One row per thread; the column loop is not
+// unrolled (r is small), and each basis row is read once per column for both
+// the projection and the decode step.  Column widths: OR of zigzag(q) over
+// the warp (same bit width as the maximum) into S.qor.
+template <int NF>
+__device__ __noinline__ bool pass_encode(const TileArgs& a, const CUtensorMap* tm, TileSmem& S, Cursor& cu, int64_t bi,
+                            const Geom& g, int r, bool check, const RowConst& rcst, const CorrConst& cc, bool pointwise,
+                            int32_t* qs, int8_t* k8, int32_t* k32) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = NF ? NF : g.n;
+  for (int i = tid; i < kWarps * NM; i += kTT) (&S.qor[0][0])[i] = 0u;
+  if (tid == 0) { S.kmax = 0; S.ncorr = 0; S.nesc = 0; }
+  __syncthreads();
+  float e1 = 0.0f, e2 = 0.0f;
+  int nc = 0, ne = 0, ovf = 0;
+  uint32_t kmx = 0;
+  const int M = (int)g.M, Lq = (int)align_up(g.L, 4), rc = a.rc;
+  const bool ok = stream_block(a, tm, S, cu, bi, g, [&](int c, const Chunks& ch, const float* tile) {
+    for (int rb = 0; rb < rc; rb += kTT) {          // same trip count in every lane
+      const int rr = rb + tid;
+      int xx = 0;
+      const int l = rr < rc ? row_index(a, g, ch, c, rr, &xx) : -1;
+      const bool valid = l >= 0;
+      const float* xr = tile + (valid ? rr : 0);
+      const float a0 = valid ? xr[0] : 0.0f;
+      float d[NM], acc[NM];
+#pragma unroll
+      for (int j = 0; j < NM; ++j) {
+        d[j] = (valid && j < n) ? __fsub_rn(xr[j * rc], a0) : 0.0f;
+        acc[j] = 0.0f;
+      }
+#pragma unroll 1
+      for (int k = 0; k < r; ++k) {
+        float v[NM];
+        const float4* vp = reinterpret_cast<const float4*>(&S.VstT[k * NM]);
+#pragma unroll
+        for (int j4 = 0; j4 < NM / 4; ++j4) {
+          const float4 t = vp[j4];
+          v[4 * j4 + 0] = t.x; v[4 * j4 + 1] = t.y; v[4 * j4 + 2] = t.z; v[4 * j4 + 3] = t.w;
+        }
+        float cf = 0.0f;
+#pragma unroll
+        for (int j = 0; j < NM; ++j)
+          if (j < n) cf = __fmaf_rn(d[j], v[j], cf);
+        cf = __fmaf_rn(a0, S.vsum[k], cf);
+        const int32_t q = quant_exact(cf, rcst.delta, rcst.inv_delta, ovf);
+        if (valid) qs[k * Lq + l] = q;
+        const uint32_t wor = __reduce_or_sync(FULL, valid ? zigzag(q) : 0u);
+        if (lane == 0) S.qor[warp][k] |= wor;
+        const float chk = __fmul_rn(__int2float_rn(q), rcst.delta_f);
+        if (check && k == r - 1 && valid) {
+#pragma unroll
+          for (int j = 0; j < NM; ++j)
+            if (j < n) { const float dd = __fsub_rn(xr[j * rc], acc[j]); e1 = __fmaf_rn(dd, dd, e1); }
+        }
+#pragma unroll
+        for (int j = 0; j < NM; ++j) acc[j] = __fmaf_rn(chk, v[j], acc[j]);
+      }
+      if (valid) {
+#pragma unroll
+        for (int j = 0; j < NM; ++j) {
+          if (j < n) {
+            const float xj = xr[j * rc];
+            if (check) { const float dd = __fsub_rn(xj, acc[j]); e2 = __fmaf_rn(dd, dd, e2); }
+            const int32_t kv = pointwise ? corr_exact(xj, acc[j], cc) : 0;
+            const int e = j * M + l;
+            const bool big = kv < -127 || kv > 127;          // includes escapes
+            k8[e] = big ? (int8_t)-128 : (int8_t)kv;
+            if (big) k32[e] = kv;
+            const bool esc = kv == kEscape, corr = kv != 0 && !esc;
+            ne += esc ? 1 : 0;
+            nc += corr ? 1 : 0;
+            const uint32_t z = corr ? zigzag(kv) : 0u;
+            kmx = z > kmx ? z : kmx;
+          }
+        }
+      }
+    }
+  });
+  if (!ok) return false;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    nc += __shfl_xor_sync(FULL, nc, o);
+    ne += __shfl_xor_sync(FULL, ne, o);
+    kmx = max(kmx, __shfl_xor_sync(FULL, kmx, o));
+    ovf |= __shfl_xor_sync(FULL, ovf, o);
+  }
+  if (lane == 0) {
+    if (nc) atomicAdd(&S.ncorr, nc);
+    if (ne) atomicAdd(&S.nesc, ne);
+    if (kmx) atomicMax(&S.kmax, (int)kmx);
+    if (ovf) S.ovf = 1;
+  }
+  __syncthreads();
+  if (tid < NM) {
+    uint32_t o = 0;
+    for (int w = 0; w < kWarps; ++w) o |= S.qor[w][tid];
+    S.wq[tid] = tid < r ? bit_width(o) : 0;
+  }
+  const float ev[2] = {e1, e2};
+  if (check) cta_reduce(S, ev, 2);
+  else __syncthreads();
+  return true;
+}
+
+// E(r) for every r in [0, rcap] (FP32 estimates into S.Ered).
+template <int NF>
+__device__ __noinline__ bool pass_all_errors(const TileArgs& a, const CUtensorMap* tm, TileSmem& S, Cursor& cu, int64_t bi,
+                                const Geom& g, int rcap, const RowConst& rcst, int& ovf) {
+  const int tid = threadIdx.x, n = NF ? NF : g.n;
+  float E[NM + 1];
+#pragma unroll
+  for (int r = 0; r <= NM; ++r) E[r] = 0.0f;
+  const bool ok = stream_block(a, tm, S, cu, bi, g, [&](int c, const Chunks& ch, const float* tile) {
+    for (int rr = tid; rr < a.rc; rr += kTT) {
+      int xx;
+      const int l = row_index(a, g, ch, c, rr, &xx);
+      if (l < 0) continue;
+      const float* xr = tile + rr;
+      const float a0 = xr[0];
+      float d[NM];
+      float acc[NM];
+#pragma unroll
+      for (int j = 0; j < NM; ++j) {
+        acc[j] = 0.0f;
+        d[j] = 0.0f;
+        if (j < n) {
+          const float xj = xr[j * a.rc];
+          d[j] = __fsub_rn(xj, a0);
+          E[0] = __fmaf_rn(xj, xj, E[0]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < NM; ++k) {
+        if (k < rcap) {
+          int32_t q;
+          const float chk = coeff_q<NF>(S, d, a0, n, k, rcst, q, ovf);
+          row_decode_step(S, k, chk, acc);
+#pragma unroll
+          for (int j = 0; j < NM; ++j)
+            if (j < n) { const float dd = __fsub_rn(xr[j * a.rc], acc[j]); E[k + 1] = __fmaf_rn(dd, dd, E[k + 1]); }
+        }
+      }
+    }
+  });
+  if (!ok) return false;
+  cta_reduce(S, E, rcap + 1);
+  return true;
+}
+
+// FP64 evaluation of E(r) in the fixed order of the definition (per column,
+// rows in chunks of 32, chunk sums in order, column sums in order), from the
+// input in global memory.  Used only when the FP32 estimate cannot decide.
+__device__ __noinline__ double exact_error(const TileArgs& a, TileSmem& S, const Geom& g, int r, const RowConst& rcst) {
+  const int tid = threadIdx.x, n = g.n;
+  const int64_t nch = cdiv(g.L, 32);
+  double* part = S.T64;                       // kTT doubles of scratch
+  static_assert(NM * NM >= kTT, "scratch");
+  double colsum = 0.0;
+  for (int j = 0; j < n; ++j) {
+    for (int64_t c0 = 0; c0 < nch; c0 += kTT) {
+      const int64_t c = c0 + tid;
+      if (c < nch) {
+        double pc = 0.0;
+        const int64_t l1 = (c + 1) * 32 < g.L ? (c + 1) * 32 : g.L;
+        for (int64_t l = c * 32; l < l1; ++l) {
+          float x[NM];
+#pragma unroll
+          for (int jj = 0; jj < NM; ++jj) x[jj] = jj < n ? __ldg(a.in + gidx_row(a, g, l, jj)) : 0.0f;
+          float d[NM];
+          shifted(x, d);
+          int ovf = 0;
+          float acc[NM];
+#pragma unroll
+          for (int jj = 0; jj < NM; ++jj) acc[jj] = 0.0f;
+          for (int k = 0; k < r; ++k) {
+            int32_t q;
+            const float chk = coeff_q<0>(S, d, x[0], n, k, rcst, q, ovf);
+            row_decode_step(S, k, chk, acc);
+          }
+          float aj = acc[0];
+#pragma unroll
+          for (int jj = 1; jj < NM; ++jj) aj = (jj == j) ? acc[jj] : aj;
+          const double dd = __dsub_rn((double)x[j], (double)aj);
+          pc = __fma_rn(dd, dd, pc);
+        }
+        part[tid] = pc;
+      }
+      __syncthreads();
+      if (tid == j) {
+        const int64_t cend = (nch - c0) < kTT ? (nch - c0) : kTT;
+        for (int64_t cc = 0; cc < cend; ++cc) colsum = __dadd_rn(colsum, part[cc]);
+      }
+      __syncthreads();
+    }
+  }
+  if (tid < n) S.lam_t[tid] = colsum;           // lam_t is free once the basis is ordered
+  __syncthreads();
+  double E = 0.0;
+  for (int j = 0; j < n; ++j) E = __dadd_rn(E, S.lam_t[j]);
+  __syncthreads();
+  return E;
+}
+
+__device__ bool decide_pass(const TileArgs& a, TileSmem& S, const Geom& g, int r, double E32, double bnd, double el2,
+                            const RowConst& rcst) {
+  const double lo = E32 / (1.0 + bnd), hi = E32 / (1.0 - bnd);
+  if (hi < el2 * (1.0 - 1e-12)) return true;
+  if (lo > el2 * (1.0 + 1e-12)) return false;
+  if (threadIdx.x == 0) S.nexact += 1;
+  return exact_error(a, S, g, r, rcst) <= el2;
+}
+
+// ---------------------------------------------------------------- rank prediction
+// Warp 0: eigenvalue-tail rank estimate E(r) ~ sum_{i>=r} lambda_i + r L delta^2/12
+// and the 32 block features, one per lane (FP32; they only steer a prediction
+// that is then checked exactly).
+__device__ __noinline__ int predict_rank(const TileArgs& a, TileSmem& S, const Geom& g, int64_t bi, int rcap, double el2,
+                            double delta, int lane) {
+  const int n = g.n;
+  double t = lane < n ? S.lam[lane] : 0.0;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double y = __shfl_down_sync(FULL, t, o);
+    if (lane + o < 32) t += y;
+  }
+  const double qn = (double)g.L * delta * delta / 12.0;
+  const bool ok = lane <= rcap && (lane < n ? t : 0.0) + lane * qn <= el2;
+  const unsigned m = __ballot_sync(FULL, ok);
+  const int rp = m ? (__ffs(m) - 1) : rcap;
+  const double tot = __shfl_sync(FULL, t, 0);
+  const double l0 = S.lam[0];
+  float mn = S.st_min[0], mx = S.st_max[0], tg = 0.0f, xg = 0.0f;
+  for (int w = 0; w < kWarps; ++w) {
+    mn = fminf(mn, S.st_min[w]); mx = fmaxf(mx, S.st_max[w]);
+    tg += S.st_tg[w]; xg += S.st_xg[w];
+  }
+  const float tot_f = (float)(tot > 0.0 ? tot : 1e-30);
+  const float el2_f = (float)el2;
+  float f = 0.0f;
+  if (lane == 0) f = log10f(tot_f / el2_f + 1e-30f);
+  const double tr = __shfl_sync(FULL, t, (lane - 1) & 31);
+  if (lane >= 1 && lane <= 16) f = log10f((lane - 1 < n ? (float)tr : 0.0f) / el2_f + 1e-30f);
+  if (lane >= 17 && lane <= 24) {
+    const int i = lane - 16;
+    f = (i < n && l0 > 0.0) ? sqrtf((float)(S.lam[i] / l0)) : 0.0f;
+  }
+  if (lane == 25) f = tg / tot_f;
+  if (lane == 26) f = xg / tot_f;
+  if (lane == 27) f = log10f((float)(qn / el2) + 1e-30f);
+  if (lane == 28) f = log10f((float)(((double)mx - (double)mn) / delta) + 1e-30f);
+  if (lane == 29) f = (float)((double)g.L * n / 65536.0);
+  if (lane == 30) f = (float)n / 16.0f;
+  if (lane == 31) f = (float)rp;
+  S.featv[lane] = f;
+  if (a.feat) a.feat[bi * kMlpF + lane] = f;
+  __syncwarp();
+  return rp;
+}
+
+// ---------------------------------------------------------------- record
+// Each warp compacts a contiguous range of [0, N) in steps of 512 elements,
+// 16 consecutive per lane from one 16-byte load of k8: elements for which
+// sel(k8[e], e) holds get consecutive indices in element order, and
+// emit(e, index) writes them.  k8 is 16-byte aligned; reads stay below
+// align16(N).
+template <class Sel, class Emit>
+__device__ void compact16(TileSmem& S, const int8_t* k8, int N, Sel sel, Emit emit) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int per = (int)(cdiv(cdiv(N, kWarps), 512) * 512);
+  const int b0 = warp * per;
+  const int b1 = (b0 + per) < N ? (b0 + per) : N;
+  auto mask16 = [&](int e0) -> uint32_t {
+    uint32_t m = 0;
+    if (e0 < b1) {
+      const uint4 w = *reinterpret_cast<const uint4*>(k8 + e0);
+      const uint32_t wd[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int8_t b = (int8_t)(wd[i >> 2] >> (8 * (i & 3)));
+        if (e0 + i < b1 && sel(b, e0 + i)) m |= 1u << i;
+      }
+    }
+    return m;
+  };
+  int cnt = 0;
+  for (int s0 = b0; s0 < b1; s0 += 512) cnt += __popc(mask16(s0 + lane * 16));
+  cnt = __reduce_add_sync(FULL, cnt);
+  if (lane == 0) S.warp_cnt[warp] = cnt;
+  __syncthreads();
+  int base = 0;
+  for (int w = 0; w < warp; ++w) base += S.warp_cnt[w];
+  for (int s0 = b0; s0 < b1; s0 += 512) {
+    uint32_t m = mask16(s0 + lane * 16);
+    const int c = __popc(m);
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += y;
+    }
+    int idx = base + incl - c;
+    while (m) {
+      const int i = __ffs(m) - 1;
+      m &= m - 1;
+      emit(s0 + lane * 16 + i, idx++);
+    }
+    base += __shfl_sync(FULL, incl, 31);
+  }
+  __syncthreads();
+}
+
+// Packs 32 consecutive w-bit values per task into exactly w words.
+__device__ __forceinline__ void flush32(uint64_t& acc, int& nbits, uint32_t* dst, int& wo) {
+  if (nbits >= 32) { dst[wo++] = (uint32_t)acc; acc >>= 32; nbits -= 32; }
+}
+
+__device__ __noinline__ void write_record(const TileArgs& a, TileSmem& S, const Geom& g, int64_t bi, bool raw, int r,
+                             int32_t* qs, const int8_t* k8, const int32_t* k32) {
+  const int tid = threadIdx.x;
+  const int n = g.n;
+  const int64_t L = g.L, N = g.N, M = g.M;
+  uint8_t* rec = a.staging + align_up((g.pt_off - a.P.pt_base) * 4, 16) + 48 * bi;
+  BlockMeta& m = S.m;
+  RecLayout& lay = S.lay;
+  if (tid == 0) {
+    const int64_t rawsz = raw_record_bytes(N, 4);
+    m.rcap = a.P.rank_cap < n ? a.P.rank_cap : n;
+    m.nprobes = 0;
+    for (int k = 0; k < kMaxN; ++k) m.wq[k] = 0;
+    m.flags = 0;
+    m.r = 0; m.wk = 0; m.ib = 0; m.ncorr = 0; m.nesc = 0;
+    bool israw = raw;
+    if (!israw) {
+      for (int k = 0; k < r; ++k) m.wq[k] = (uint8_t)S.wq[k];
+      const int wk = bit_width((uint32_t)S.kmax);
+      const int ib = bit_width((uint32_t)(N - 1));
+      lay = rec_layout(r, n, L, N, 4, m.wq, wk, ib, S.ncorr, S.nesc);
+      if (lay.size >= rawsz) {
+        israw = true;
+      } else {
+        m.r = r; m.wk = wk; m.ib = ib; m.ncorr = S.ncorr; m.nesc = S.nesc;
+        m.flags |= lay.dense ? (int)kFlagDense : 0;
+        m.nbytes = lay.size;
+      }
+    }
+    if (israw) {
+      m.r = 0; m.wk = 0; m.ib = 0; m.ncorr = 0; m.nesc = 0;
+      for (int k = 0; k < kMaxN; ++k) m.wq[k] = 0;
+      m.flags = (int)kFlagRaw;
+      m.nbytes = rawsz;
+    }
+    a.meta[bi] = m;
+    if (a.ranks) a.ranks[bi] = (m.flags & kFlagRaw) ? -1 : m.r;
+    int64_t wb = 0;
+    for (int c = 0; c < m.r; ++c) { S.colbase[c] = wb; wb += (L * m.wq[c] + 31) / 32; }
+    S.colbase[m.r] = wb;
+  }
+  __syncthreads();
+  if (m.flags & kFlagRaw) {
+    if (tid == 0) {
+      reinterpret_cast<uint32_t*>(rec)[0] = (uint32_t)m.flags << 8;
+      reinterpret_cast<uint32_t*>(rec)[1] = 0;
+      reinterpret_cast<uint32_t*>(rec)[2] = 0;
+      reinterpret_cast<uint32_t*>(rec)[3] = (uint32_t)m.nbytes;
+    }
+    float* vals = reinterpret_cast<float*>(rec + 16);
+    for (int64_t e = tid; e < N; e += kTT) {
+      const int64_t lt = e / M, ls = e - lt * M;
+      vals[e] = a.in[gidx_row(a, g, ls, (int)lt)];
+    }
+    if (tid == 0 && (16 + N * 4) % 16) {
+      // zero the padding after the last value
+      for (int64_t b = 16 + N * 4; b < m.nbytes; ++b) rec[b] = 0;
+    }
+    __syncthreads();
+    return;
+  }
+  const int rr = m.r;
+  // zero the 16-byte words that hold padding between sections (written over
+  // by the sections themselves after the barrier)
+  if (tid == 0) {
+    const int64_t qwords = S.colbase[rr];
+    const int64_t ends[6] = {lay.off_wq + rr, lay.off_v + (int64_t)n * rr * 4, lay.off_q + qwords * 4,
+                             lay.off_c + lay.corr_words * 4, lay.off_ei + (int64_t)m.nesc * 4,
+                             lay.off_ev + (int64_t)m.nesc * 4};
+    for (int i = 0; i < 6; ++i) {
+      const int64_t w = ends[i] / 16 * 16;
+      if (w < m.nbytes) *reinterpret_cast<uint4*>(rec + w) = make_uint4(0, 0, 0, 0);
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    rec[0] = (uint8_t)m.r;
+    rec[1] = (uint8_t)m.flags;
+    rec[2] = (uint8_t)m.wk;
+    rec[3] = (uint8_t)m.ib;
+    reinterpret_cast<uint32_t*>(rec)[1] = (uint32_t)m.ncorr;
+    reinterpret_cast<uint32_t*>(rec)[2] = (uint32_t)m.nesc;
+    reinterpret_cast<uint32_t*>(rec)[3] = (uint32_t)m.nbytes;
+  }
+  for (int c = tid; c < rr; c += kTT) rec[lay.off_wq + c] = m.wq[c];
+  float* vout = reinterpret_cast<float*>(rec + lay.off_v);
+  for (int i = tid; i < n * rr; i += kTT) {
+    const int c = i / n, j = i - c * n;
+    vout[i] = S.VstT[c * NM + j];
+  }
+  // q: 32 consecutive values of one column per task -> exactly w words
+  uint32_t* qw = reinterpret_cast<uint32_t*>(rec + lay.off_q);
+  {
+    const int64_t runs = cdiv(L, 32);
+    for (int64_t task = tid; task < runs * rr; task += kTT) {
+      const int c = (int)(task / runs);
+      const int64_t first = (task - (int64_t)c * runs) * 32;
+      const int wdt = m.wq[c];
+      if (wdt == 0) continue;
+      const int32_t* col = qs + (int64_t)c * align_up(L, 4) + first;
+      const int cnt = (int)((L - first) < 32 ? (L - first) : 32);
+      uint32_t* dst = qw + S.colbase[c] + (first / 32) * wdt;
+      uint32_t z[32];
+      if (cnt == 32) {
+        const uint4* cv = reinterpret_cast<const uint4*>(col);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const uint4 v = cv[i];
+          z[4 * i + 0] = zigzag((int32_t)v.x);
+          z[4 * i + 1] = zigzag((int32_t)v.y);
+          z[4 * i + 2] = zigzag((int32_t)v.z);
+          z[4 * i + 3] = zigzag((int32_t)v.w);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) z[i] = i < cnt ? zigzag(col[i]) : 0u;
+      }
+      uint64_t acc = 0;
+      int nbits = 0, wo = 0;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        if (i < cnt) {
+          acc |= (uint64_t)z[i] << nbits;
+          nbits += wdt;
+          flush32(acc, nbits, dst, wo);
+        }
+      }
+      if (nbits > 0) dst[wo] = (uint32_t)acc;
+    }
+  }
+  __syncthreads();   // q scratch is free from here on
+  auto kval = [&](int64_t e) -> int32_t {
+    const int8_t v = k8[e];
+    return v == (int8_t)-128 ? k32[e] : (int32_t)v;
+  };
+  uint32_t* cw = reinterpret_cast<uint32_t*>(rec + lay.off_c);
+  if (m.wk > 0) {
+    if (lay.dense) {
+      const int wk = m.wk;
+      const int64_t runs = cdiv(N, 32);
+      for (int64_t task = tid; task < runs; task += kTT) {
+        const int64_t first = task * 32;
+        const int cnt = (int)((N - first) < 32 ? (N - first) : 32);
+        uint32_t* dst = cw + task * wk;
+        int8_t kb[32];
+        if (cnt == 32) {
+          const uint4* kv4 = reinterpret_cast<const uint4*>(k8 + first);
+          const uint4 w0 = kv4[0], w1 = kv4[1];
+          const uint32_t wd[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+          for (int i = 0; i < 32; ++i) kb[i] = (int8_t)(wd[i >> 2] >> (8 * (i & 3)));
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) kb[i] = i < cnt ? k8[first + i] : (int8_t)0;
+        }
+        uint64_t acc = 0;
+        int nbits = 0, wo = 0;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          if (i < cnt) {
+            int32_t kv = kb[i];
+            if (kv == -128) kv = k32[first + i];
+            acc |= (uint64_t)(kv == kEscape ? 0u : zigzag(kv)) << nbits;
+            nbits += wk;
+            flush32(acc, nbits, dst, wo);
+          }
+        }
+        if (nbits > 0) dst[wo] = (uint32_t)acc;
+      }
+    } else {
+      // entry list (element indices) into the q scratch, then 32 entries of
+      // ib + wk bits per task -> exactly ib + wk words
+      uint32_t* list = reinterpret_cast<uint32_t*>(qs);
+      compact16(
+          S, k8, (int)N, [&](int8_t b, int e) { return b != 0 && (b != (int8_t)-128 || k32[e] != kEscape); },
+          [&](int e, int idx) { list[idx] = (uint32_t)e; });
+      const int ib = m.ib, wk = m.wk, W = ib + wk;
+      const int64_t nc = m.ncorr;
+      for (int64_t task = tid; task < cdiv(nc, 32); task += kTT) {
+        const int64_t first = task * 32;
+        const int cnt = (int)((nc - first) < 32 ? (nc - first) : 32);
+        uint32_t* dst = cw + task * W;
+        uint64_t acc = 0;
+        int nbits = 0, wo = 0;
+        for (int i = 0; i < cnt; ++i) {
+          const uint32_t e = list[first + i];
+          acc |= (uint64_t)e << nbits;
+          nbits += ib;
+          flush32(acc, nbits, dst, wo);
+          acc |= (uint64_t)zigzag(kval(e)) << nbits;
+          nbits += wk;
+          flush32(acc, nbits, dst, wo);
+        }
+        if (nbits > 0) dst[wo] = (uint32_t)acc;
+      }
+    }
+  }
+  if (m.nesc > 0) {
+    uint32_t* ei = reinterpret_cast<uint32_t*>(rec + lay.off_ei);
+    float* ev = reinterpret_cast<float*>(rec + lay.off_ev);
+    compact16(
+        S, k8, (int)N, [&](int8_t b, int e) { return b == (int8_t)-128 && k32[e] == kEscape; },
+        [&](int e, int idx) {
+          ei[idx] = (uint32_t)e;
+          const int64_t lt = e / M, ls = e - lt * M;
+          ev[idx] = a.in[gidx_row(a, g, ls, (int)lt)];
+        });
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- the kernel
+template <int MINB>
+__global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUtensorMap tmap, const TileArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // TMA destinations: align the tile ring to 1024 bytes explicitly
+  const uint32_t sbase = smem_u32(smem_raw);
+  TileSmem& S = *reinterpret_cast<TileSmem*>(smem_raw + (((sbase + 1023u) & ~1023u) - sbase));
+  const CUtensorMap* tm = &tmap;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int32_t* qs = a.q_scr + (int64_t)blockIdx.x * NM * a.lmax;
+  int8_t* k8 = a.k8_scr + (int64_t)blockIdx.x * a.nptmax;
+  int32_t* k32 = a.k32_scr + (int64_t)blockIdx.x * a.nptmax;
+  const Plan& P = a.P;
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&S.full[s], a.use_tma ? 1u : (unsigned)kTT);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    S.nexact = 0;
+    S.abort_flag = 0;
+  }
+  __syncthreads();
+  if (tid < kPhases) S.ph[tid] = 0;
+  long long tck = clock64();
+  auto mark = [&](int p) {
+    if (tid == 0) {
+      const long long now = clock64();
+      S.ph[p] += (unsigned long long)(now - tck);
+      tck = now;
+    }
+  };
+  // blocks whose Gram side is time; the others are left to k_mixed
+  auto grab = [&]() -> int64_t {
+    for (;;) {
+      const int64_t b = (int64_t)atomicAdd(&a.status->pad[1], 1ull);
+      if (b >= P.nb) return P.nb;
+      if (block_geom(P, P.b0 + b).side == 0) return b;
+    }
+  };
+  Cursor cu;
+  cu.iss = 0; cu.con = 0; cu.pf_blk = -1; cu.pf_cnt = 0;
+  if (tid == 0) S.bnext = grab();
+  __syncthreads();
+  for (;;) {
+    const int64_t bi = S.bnext;
+    __syncthreads();
+    if (bi >= P.nb) break;
+    if (tid == 0) S.bnext = grab();
+    const Geom g = block_geom(P, P.b0 + bi);
+    const VarInfo vi = a.vars[g.v];
+    const int n = g.n;
+    const int rcap = P.rank_cap < n ? P.rank_cap : n;
+    const bool pointwise = P.eb_type != DLS_EB_NRMSE;
+    RowConst rcst;
+    rcst.delta = vi.delta;
+    rcst.inv_delta = __double2float_rn(1.0 / vi.delta);
+    rcst.delta_f = __double2float_rn(vi.delta);
+    const CorrConst cc = make_corr_const(vi.eb, vi.step, pointwise);
+    const double el2 = (P.eb_type == DLS_EB_NRMSE) ? (vi.eb * vi.eb) * ((double)g.N / (double)P.K)
+                                                   : (vi.eb * vi.eb) * (double)g.N;
+    if (tid == 0) { S.nonfinite = 0; S.ovf = 0; }
+    __syncthreads();
+
+    if (tid == 0) tck = clock64();
+    const bool full = n == NM;   // Gram order 16: the passes without per-column predicates
+    if (!(full ? pass_gram<false, NM>(a, tm, S, cu, bi, g) : pass_gram<false, 0>(a, tm, S, cu, bi, g))) break;
+    mark(kPhGram);
+    if (S.nonfinite) {
+      if (tid == 0) atomicOr(&a.status->nonfinite, 1u);
+      __syncthreads();
+      continue;
+    }
+    // the encode pass reads the same block again: start its first chunks now
+    prefetch(a, tm, S, cu, bi, g);
+    // rotations below 1% of the per-mode budget eb^2 L change no decision
+    // worth a sweep; the decisions themselves stay exact
+    const float jfloor = (float)(a.jfloor * (P.eb_type == DLS_EB_NRMSE ? el2 / n : vi.eb * vi.eb * (double)g.L));
+    if (warp == 0) jacobi_reg<NM>(S.G32, NM, n, true, 0.0f, S.Vj, NM, S.lam_t, lane, jfloor);
+    __syncthreads();
+    mark(kPhJacobi);
+    refine64(S, n);
+    if (warp == 0) order_basis(S, n, lane);
+    __syncthreads();
+    mark(kPhRefine);
+    // Tight bounds need the modes an FP32 Gram cannot resolve (eigenvalues near
+    // 2^-24 trace G): one Rayleigh-Ritz step on the projected data fixes them.
+    {
+      double tr = 0.0;
+      for (int i = 0; i < n; ++i) tr += S.lam[i];
+      const double budget = (vi.eb * vi.eb) * (double)g.L;
+      const double noise = (P.eb_type == DLS_EB_NRMSE ? el2 / n : budget);
+      if (n > 1 && 4.0 * 5.9604644775390625e-8 * tr > 0.1 * noise) {
+        if (!(full ? pass_gram<true, NM>(a, tm, S, cu, bi, g) : pass_gram<true, 0>(a, tm, S, cu, bi, g))) break;
+        prefetch(a, tm, S, cu, bi, g);
+        if (warp == 0) jacobi_reg<NM>(S.G32, NM, n, true, 0.0f, S.Vj, NM, S.lam_t, lane, jfloor);
+        __syncthreads();
+        // V = Vst W in FP64; eigenvalues from the Rayleigh-Ritz diagonal
+        for (int e = tid; e < NM * NM; e += kTT) {
+          const int i = e / NM, j = e % NM;
+          if (i < n && j < n) {
+            double v = 0.0;
+            for (int k = 0; k < n; ++k) v = fma((double)S.VstT[k * NM + i], (double)S.Vj[k * NM + j], v);
+            S.X64[e] = v;
+          }
+        }
+        __syncthreads();
+        // first-order orthonormalisation in FP64: V <- V (I + R/2), R = I - V^T V
+        for (int e = tid; e < NM * NM; e += kTT) {
+          const int i = e / NM, j = e % NM;
+          if (i < n && j < n && i <= j) {
+            double rr = 0.0;
+            for (int k = 0; k < n; ++k) rr = fma(S.X64[k * NM + i], S.X64[k * NM + j], rr);
+            rr = (i == j ? 1.0 : 0.0) - rr;
+            S.R64[i * NM + j] = rr;
+            S.R64[j * NM + i] = rr;
+          }
+        }
+        __syncthreads();
+        double xn[2] = {0.0, 0.0};
+        int cnt = 0;
+        for (int e = tid; e < NM * NM; e += kTT, ++cnt) {
+          const int i = e / NM, j = e % NM;
+          if (i < n && j < n) {
+            double v = S.X64[e];
+            for (int k = 0; k < n; ++k) v = fma(S.X64[i * NM + k], 0.5 * S.R64[k * NM + j], v);
+            xn[cnt] = v;
+          }
+        }
+        __syncthreads();
+        cnt = 0;
+        for (int e = tid; e < NM * NM; e += kTT, ++cnt) {
+          const int i = e / NM, j = e % NM;
+          if (i < n && j < n) S.X64[e] = xn[cnt];
+        }
+        __syncthreads();
+        if (warp == 0) order_basis(S, n, lane);
+        __syncthreads();
+      }
+    }
+    mark(kPhRR);
+
+    float rowmax = 0.0f;
+    for (int w = 0; w < kWarps; ++w) rowmax = fmaxf(rowmax, S.st_rowmax[w]);
+    const bool may_overflow = !((double)sqrtf(rowmax) * 1.0001 / vi.delta < 16777216.0 * 0.999);
+
+    if (warp == 0) {
+      const int rp = predict_rank(a, S, g, bi, rcap, el2, vi.delta, lane);
+      int rm = rp;
+      if (a.learned == kRankMlp && a.model) rm = mlp_rank_warp(a.model, S.featv, S.mh1, lane, rcap);
+      if (lane == 0) S.r_pred = rm;
+    }
+    __syncthreads();
+    mark(kPhPredict);
+
+    const Chunks chk = chunks_of(a, g);
+    const int64_t rows_per_thread = cdiv(a.rc, kTT) * chk.n;
+    const double bnd = (double)(rows_per_thread * n + 40) * 6.6e-8;
+    bool accepted = false;
+    int r = 0;
+    if (a.learned != kRankSearch && !may_overflow) {
+      const int rp = S.r_pred;
+      if (!(full ? pass_encode<NM>(a, tm, S, cu, bi, g, rp, true, rcst, cc, pointwise, qs, k8, k32)
+                 : pass_encode<0>(a, tm, S, cu, bi, g, rp, true, rcst, cc, pointwise, qs, k8, k32)))
+        break;
+      mark(kPhEncode);
+      const double E_rm1 = S.Ered[0], E_r = S.Ered[1];
+      if (!S.ovf) {
+        const bool p_r = decide_pass(a, S, g, rp, E_r, bnd, el2, rcst);
+        bool p_rm1 = false;
+        if (rp > 0 && p_r) p_rm1 = decide_pass(a, S, g, rp - 1, E_rm1, bnd, el2, rcst);
+        accepted = p_r && !p_rm1;
+        r = rp;
+      }
+      mark(kPhDecide);
+    }
+    bool raw = false;
+    if (!accepted) {
+      if (tid == 0) S.ovf = 0;
+      __syncthreads();
+      int ovf = 0;
+      if (!(full ? pass_all_errors<NM>(a, tm, S, cu, bi, g, rcap, rcst, ovf)
+                 : pass_all_errors<0>(a, tm, S, cu, bi, g, rcap, rcst, ovf)))
+        break;
+      if (ovf) S.ovf = 1;
+      __syncthreads();
+      double Eall[NM + 1];
+      for (int i = 0; i <= rcap; ++i) Eall[i] = S.Ered[i];
+      if (S.ovf) {
+        raw = true;
+      } else {
+        int lo = 0, hi = rcap;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (decide_pass(a, S, g, mid, Eall[mid], bnd, el2, rcst)) hi = mid;
+          else lo = mid + 1;
+        }
+        r = lo;
+        if (!pointwise && !decide_pass(a, S, g, r, Eall[r], bnd, el2, rcst)) raw = true;
+        if (!raw && !(full ? pass_encode<NM>(a, tm, S, cu, bi, g, r, false, rcst, cc, pointwise, qs, k8, k32)
+                           : pass_encode<0>(a, tm, S, cu, bi, g, r, false, rcst, cc, pointwise, qs, k8, k32)))
+          break;
+      }
+      mark(kPhSearch);
+    }
+    // the next block's first chunks load while this record is packed
+    {
+      const int64_t bn = S.bnext;
+      if (bn < P.nb) prefetch(a, tm, S, cu, bn, block_geom(P, P.b0 + bn));
+    }
+    write_record(a, S, g, bi, raw, r, qs, k8, k32);
+    mark(kPhPack);
+    if (tid == 0) S.ph[accepted ? kCntAccepted : kCntSearched] += 1;
+  }
+  if (S.abort_flag) {
+    if (tid == 0) atomicOr(&a.status->timeout, 1u);
+  }
+  // leave no copy in flight
+  while (cu.con < cu.iss) {
+    mbar_wait(&S.full[cu.con % kStages], (cu.con / kStages) & 1u);
+    ++cu.con;
+  }
+  if (tid == 0) {
+    S.ph[kCntExact] = S.nexact;
+    if (a.phase)
+      for (int i = 0; i < kPhases; ++i) a.phase[(int64_t)blockIdx.x * kPhases + i] += S.ph[i];
+  }
+}
+
+// ---------------------------------------------------------------- host side
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+}  // namespace
+
+// Chunk box of the plan: (bxb, yc, zc, bt) with bxb * yc * zc * bt <= one stage.
+bool tile_chunk_box(const Plan& p, int* bxb, int* yc, int* zc, int* bt) {
+  const int bx = p.block[0], by = p.block[1], bz = p.block[2], btt = p.block[3];
+  if (btt > NM || bx * btt > kStageFloats) return false;
+  *bxb = bx;
+  *bt = btt;
+  if (bx * by * btt <= kStageFloats) {
+    *yc = by;
+    const int z = kStageFloats / (bx * by * btt);
+    *zc = z < bz ? z : bz;
+  } else {
+    *yc = kStageFloats / (bx * btt);
+    *zc = 1;
+  }
+  return true;
+}
+
+size_t tile_smem_bytes() { return sizeof(TileSmem) + 1024; }
+
+int tile_ctas_per_sm(int variant) {
+  int nb = 0;
+  const size_t smem = tile_smem_bytes();
+  if (variant == 1) {
+    if (cudaFuncSetAttribute(k_tile<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tile<2>, kTT, smem) != cudaSuccess)
+      nb = 0;
+  } else {
+    if (cudaFuncSetAttribute(k_tile<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tile<4>, kTT, smem) != cudaSuccess)
+      nb = 0;
+  }
+  cudaGetLastError();
+  return nb;
+}
+
+int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, int learned, int variant,
+                         cudaStream_t s) {
+  if (p.nb == 0) return DLS_OK;
+  TileArgs a;
+  memset(&a, 0, sizeof(a));
+  a.P = p;
+  a.in = (const float*)d_in;
+  a.staging = w.staging;
+  a.meta = w.meta;
+  a.vars = w.vars;
+  a.status = w.status;
+  a.q_scr = w.q_scr;
+  a.k8_scr = w.k8_scr;
+  a.k32_scr = w.k32_scr;
+  a.feat = w.feat;
+  a.ranks = w.ranks;
+  a.lmax = w.lmax;
+  a.nptmax = w.nptmax;
+  a.learned = learned;
+  a.phase = w.phase;
+  a.model = rank_model_device();
+  if (!tile_chunk_box(p, &a.bxb, &a.yc, &a.zc, &a.bt)) return DLS_ERR_INVALID_ARG;
+  a.rc = a.bxb * a.yc * a.zc;
+  auto magic = [](int d) -> uint32_t { return d <= 1 ? 0u : (uint32_t)((0x100000000ull + (uint64_t)d - 1) / (uint64_t)d); };
+  a.mbx = magic(a.bxb);
+  a.myc = magic(a.yc);
+  a.jfloor = 1e-2;
+  CUtensorMap tmap;
+  memset(&tmap, 0, sizeof(tmap));
+  const bool aligned = (p.dims[0] % 4 == 0) && (p.block[0] % 4 == 0) && (((uintptr_t)d_in & 15) == 0);
+  a.use_tma = 0;
+  if (aligned) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (enc) {
+      const cuuint64_t dims[5] = {(cuuint64_t)p.dims[0], (cuuint64_t)p.dims[1], (cuuint64_t)p.dims[2],
+                                  (cuuint64_t)p.dims[3], (cuuint64_t)p.nvars};
+      const cuuint64_t strides[4] = {(cuuint64_t)p.dims[0] * 4, (cuuint64_t)(p.dims[0] * p.dims[1]) * 4,
+                                     (cuuint64_t)p.P * 4, (cuuint64_t)p.K * 4};
+      const cuuint32_t box[5] = {(cuuint32_t)a.bxb, (cuuint32_t)a.yc, (cuuint32_t)a.zc, (cuuint32_t)a.bt, 1u};
+      const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+      const CUresult rc = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void*>(d_in), dims, strides, box,
+                              es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      a.use_tma = rc == CUDA_SUCCESS ? 1 : 0;
+    }
+  }
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return DLS_ERR_CUDA;
+  const int per_sm = tile_ctas_per_sm(variant);
+  if (per_sm < 1) return DLS_ERR_CUDA;
+  int ctas = sms * per_sm;
+  if (ctas > w.ctas) ctas = w.ctas;
+  if ((int64_t)ctas > p.nb) ctas = (int)p.nb;
+  const size_t smem = tile_smem_bytes();
+  if (variant == 1) k_tile<2><<<ctas, kTT, smem, s>>>(tmap, a);
+  else k_tile<4><<<ctas, kTT, smem, s>>>(tmap, a);
+  return cudaGetLastError() == cudaSuccess ? DLS_OK : DLS_ERR_CUDA;
+}
+
+}  // namespace dls

@@ -99,6 +99,7 @@ _SIGS = {
                                   C.c_void_p, C.POINTER(C.c_void_p)]),
     "dls_plan_execute": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t), C.c_void_p]),
     "dls_plan_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
+    "dls_plan_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_int32)]),
     "dls_plan_destroy": (C.c_int, [C.c_void_p]),
     "dls_phase_cycles": (C.c_int, [C.POINTER(Params), C.c_void_p, C.POINTER(C.c_ulonglong), C.c_int32]),
     "dls_stage_quantize": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -366,6 +367,15 @@ class CompressPlan:
         lib().dls_plan_info(self.handle, C.byref(v), ms)
         return v.value, (ms[0], ms[1])
 
+    def timing(self):
+        """(device ms of the per-block kernels in the last execute, kernel nodes in the graph)."""
+        ms = C.c_float(0.0)
+        nk = C.c_int32(0)
+        st = lib().dls_plan_timing(self.handle, C.byref(ms), C.byref(nk))
+        if st != OK:
+            raise DlsError(st, "dls_plan_timing")
+        return ms.value, nk.value
+
     def close(self):
         if self.handle:
             lib().dls_plan_destroy(self.handle)
@@ -379,7 +389,7 @@ class CompressPlan:
 
 
 PHASES = ("gram", "jacobi", "refine", "rayleigh_ritz", "predict", "encode", "decide", "search", "pack",
-          "n_accepted", "n_searched", "n_exact_fallback")
+          "n_accepted", "n_searched", "n_exact_fallback", "tile_wait")
 
 
 def phase_cycles(p: Params, workspace: torch.Tensor) -> dict:

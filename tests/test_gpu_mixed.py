@@ -172,3 +172,26 @@ def test_mixed_mode_on_f64_field_takes_fp64_form():
 def test_tensor_core_modes_are_reserved():
     p = dls.make_params((1, 16, 16, 16, 16), dls.F32, (16, 16, 16, 16), 1e-3, precision=dls.PREC_TF32X3)
     assert dls.workspace_size(p) == 0
+
+
+def test_mixed_both_block_sides():
+    """Edge blocks of 2 x 4 x 1 points over 16 steps take the spatial Gram side
+    (M = 8 < T = 16) while the full 4 x 4 x 1 blocks tie and take time; both
+    kinds run in one call."""
+    dims = (10, 8, 3, 32)
+    f = synth.modes3d(*dims, seed=11, count=8).numpy()
+    eb = 1e-3 * float(f.max() - f.min())
+    ref, comp, rec, fd, _ = _mixed_vs_oracle(f, dims, (4, 4, 1, 16), eb)
+    assert (rec.double() - fd.double()).abs().max().item() <= eb
+    assert abs((f.nbytes / comp.numel()) / (f.nbytes / ref.size) - 1) <= 0.01
+
+
+@pytest.mark.parametrize("dims,block", [((48, 20, 20, 16), (12, 8, 8, 16)),     # TMA, several z-planes per chunk
+                                        ((37, 21, 9, 20), (16, 16, 8, 16)),     # cp.async, ragged edges
+                                        ((64, 64, 16, 40), (16, 16, 16, 16))])  # T edge of 8 steps
+def test_mixed_chunk_shapes(dims, block):
+    f = synth.modes3d(*dims, seed=13, count=24).numpy()
+    eb = 1e-3 * float(f.max() - f.min())
+    ref, comp, rec, fd, _ = _mixed_vs_oracle(f, dims, block, eb, rank_mode=dls.RANK_TAIL)
+    assert (rec.double() - fd.double()).abs().max().item() <= eb
+    assert abs((f.nbytes / comp.numel()) / (f.nbytes / ref.size) - 1) <= 0.01
