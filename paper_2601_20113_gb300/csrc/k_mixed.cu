@@ -77,6 +77,7 @@ struct MxSmem {
   int32_t rowoff[kTab];
   int tab_sx, tab_sy, tab_sz, tab_ok;
   int64_t base0;
+  JacPairs jp;
 };
 
 // ---------------------------------------------------------------- rank model
@@ -872,8 +873,7 @@ __device__ __forceinline__ void mixed_body(const MxArgs& a) {
       __syncthreads();
       continue;
     }
-    if (warp == 0) jacobi_reg<NM>(S.G32, NM, n, true, 0.0f, S.Vj, NM, S.lam_t, lane);
-    __syncthreads();
+    jacobi_cta<kMT>(S.G32, S.Vj, S.lam_t, n, 0.0f, S.jp);
     mark(kPhJacobi);
     refine64(S, n);
     if (warp == 0) order_basis(S, n, lane);
@@ -888,8 +888,7 @@ __device__ __forceinline__ void mixed_body(const MxArgs& a) {
       const double noise = (P.eb_type == DLS_EB_NRMSE ? el2 / n : budget);
       if (n > 1 && 4.0 * 5.9604644775390625e-8 * tr > 0.1 * noise) {
         pass_gram(a, S, g, true);
-        if (warp == 0) jacobi_reg<NM>(S.G32, NM, n, true, 0.0f, S.Vj, NM, S.lam_t, lane);
-        __syncthreads();
+        jacobi_cta<kMT>(S.G32, S.Vj, S.lam_t, n, 0.0f, S.jp);
         // V = Vst W in FP64, eigenvalues from the rotated diagonal
         {
           const int i = tid / NM, j = tid % NM;

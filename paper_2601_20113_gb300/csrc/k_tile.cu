@@ -89,6 +89,7 @@ struct __align__(128) TileSmem {
   int warp_cnt[kWarps];
   int64_t colbase[NM + 1];
   unsigned long long ph[kPhases];   // cycle counters of this CTA (thread 0)
+  JacPairs jp;
   BlockMeta m;
   RecLayout lay;
 };
@@ -898,13 +899,19 @@ __device__ void compact16(TileSmem& S, const int8_t* k8, int N, Sel sel, Emit em
     return m;
   };
   int cnt = 0;
-  for (int s0 = b0; s0 < b1; s0 += 512) cnt += __popc(mask16(s0 + lane * 16));
+  int s0 = b0;
+  for (; s0 + 3 * 512 < b1; s0 += 4 * 512) {       // four loads in flight
+    const uint32_t m0 = mask16(s0 + lane * 16), m1 = mask16(s0 + 512 + lane * 16);
+    const uint32_t m2 = mask16(s0 + 1024 + lane * 16), m3 = mask16(s0 + 1536 + lane * 16);
+    cnt += __popc(m0) + __popc(m1) + __popc(m2) + __popc(m3);
+  }
+  for (; s0 < b1; s0 += 512) cnt += __popc(mask16(s0 + lane * 16));
   cnt = __reduce_add_sync(FULL, cnt);
   if (lane == 0) S.warp_cnt[warp] = cnt;
   __syncthreads();
   int base = 0;
   for (int w = 0; w < warp; ++w) base += S.warp_cnt[w];
-  for (int s0 = b0; s0 < b1; s0 += 512) {
+  for (int s0 = b0; s0 < b1; s0 += 512) {        // second read: mostly L1 hits
     uint32_t m = mask16(s0 + lane * 16);
     const int c = __popc(m);
     int incl = c;
@@ -1104,23 +1111,44 @@ __device__ __noinline__ void write_record(const TileArgs& a, TileSmem& S, const 
       uint32_t* list = reinterpret_cast<uint32_t*>(qs);
       compact16(
           S, k8, (int)N, [&](int8_t b, int e) { return b != 0 && (b != (int8_t)-128 || k32[e] != kEscape); },
-          [&](int e, int idx) { list[idx] = (uint32_t)e; });
+          [&](int e, int idx) {
+            if (idx < m.ncorr) list[idx] = (uint32_t)e;   // the count and the bytes agree by construction
+          });
       const int ib = m.ib, wk = m.wk, W = ib + wk;
       const int64_t nc = m.ncorr;
       for (int64_t task = tid; task < cdiv(nc, 32); task += kTT) {
         const int64_t first = task * 32;
         const int cnt = (int)((nc - first) < 32 ? (nc - first) : 32);
         uint32_t* dst = cw + task * W;
+        // all 32 entries, then all 32 correction bytes, before the bit packing
+        uint32_t ee[32];
+        if (cnt == 32) {
+          const uint4* lv = reinterpret_cast<const uint4*>(list + first);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const uint4 v = lv[i];
+            ee[4 * i + 0] = v.x; ee[4 * i + 1] = v.y; ee[4 * i + 2] = v.z; ee[4 * i + 3] = v.w;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) ee[i] = i < cnt ? list[first + i] : 0u;
+        }
+        int8_t kb[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) kb[i] = i < cnt ? k8[ee[i]] : (int8_t)0;
         uint64_t acc = 0;
         int nbits = 0, wo = 0;
-        for (int i = 0; i < cnt; ++i) {
-          const uint32_t e = list[first + i];
-          acc |= (uint64_t)e << nbits;
-          nbits += ib;
-          flush32(acc, nbits, dst, wo);
-          acc |= (uint64_t)zigzag(kval(e)) << nbits;
-          nbits += wk;
-          flush32(acc, nbits, dst, wo);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          if (i < cnt) {
+            const int32_t kv = kb[i] == (int8_t)-128 ? k32[ee[i]] : (int32_t)kb[i];
+            acc |= (uint64_t)ee[i] << nbits;
+            nbits += ib;
+            flush32(acc, nbits, dst, wo);
+            acc |= (uint64_t)zigzag(kv) << nbits;
+            nbits += wk;
+            flush32(acc, nbits, dst, wo);
+          }
         }
         if (nbits > 0) dst[wo] = (uint32_t)acc;
       }
@@ -1132,6 +1160,7 @@ __device__ __noinline__ void write_record(const TileArgs& a, TileSmem& S, const 
     compact16(
         S, k8, (int)N, [&](int8_t b, int e) { return b == (int8_t)-128 && k32[e] == kEscape; },
         [&](int e, int idx) {
+          if (idx >= m.nesc) return;                      // the count and the bytes agree by construction
           ei[idx] = (uint32_t)e;
           const int64_t lt = e / M, ls = e - lt * M;
           ev[idx] = a.in[gidx_row(a, g, ls, (int)lt)];
@@ -1216,8 +1245,7 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
     // rotations below 1% of the per-mode budget eb^2 L change no decision
     // worth a sweep; the decisions themselves stay exact
     const float jfloor = (float)(a.jfloor * (P.eb_type == DLS_EB_NRMSE ? el2 / n : vi.eb * vi.eb * (double)g.L));
-    if (warp == 0) jacobi_reg<NM>(S.G32, NM, n, true, 0.0f, S.Vj, NM, S.lam_t, lane, jfloor);
-    __syncthreads();
+    jacobi_cta<kTT>(S.G32, S.Vj, S.lam_t, n, jfloor, S.jp);
     mark(kPhJacobi);
     refine64(S, n);
     if (warp == 0) order_basis(S, n, lane);
@@ -1233,8 +1261,7 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
       if (n > 1 && 4.0 * 5.9604644775390625e-8 * tr > 0.1 * noise) {
         if (!(full ? pass_gram<true, NM>(a, tm, S, cu, bi, g) : pass_gram<true, 0>(a, tm, S, cu, bi, g))) break;
         prefetch(a, tm, S, cu, bi, g);
-        if (warp == 0) jacobi_reg<NM>(S.G32, NM, n, true, 0.0f, S.Vj, NM, S.lam_t, lane, jfloor);
-        __syncthreads();
+        jacobi_cta<kTT>(S.G32, S.Vj, S.lam_t, n, jfloor, S.jp);
         // V = Vst W in FP64; eigenvalues from the Rayleigh-Ritz diagonal
         for (int e = tid; e < NM * NM; e += kTT) {
           const int i = e / NM, j = e % NM;

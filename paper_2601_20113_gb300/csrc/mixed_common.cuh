@@ -274,4 +274,105 @@ __device__ void jacobi_reg(const float* G, int ldg, int n, bool relative, float 
   __syncwarp();
 }
 
+// ---------------------------------------------------------------- CTA Jacobi
+// Scratch of the CTA Jacobi (shared).
+struct JacPairs {
+  int p[NM / 2], q[NM / 2], act[NM / 2];
+  float c[NM / 2], s[NM / 2], t[NM / 2], app[NM / 2], aqq[NM / 2], apq[NM / 2];
+};
+
+// Pair i of round `round` of the round-robin circle over m positions (m even).
+__device__ __forceinline__ void circle_pair(int round, int i, int m, int& p, int& q) {
+  int a, b;
+  if (i == 0) { a = m - 1; b = round; }
+  else { a = (round + i) % (m - 1); b = (round - i + (m - 1)) % (m - 1); }
+  p = a < b ? a : b;
+  q = a < b ? b : a;
+}
+
+// Parallel cyclic Jacobi of the symmetric matrix A (order n <= NM, row stride
+// NM, shared, overwritten) by all NT threads of the CTA, in FP32; V (shared)
+// receives the eigenvectors as columns and lam the eigenvalues (diagonal),
+// both by index.  Each round rotates m/2 disjoint pairs of the round-robin
+// circle (m = n rounded up to even): rotation parameters by m/2 threads, then
+// the two rows of every pair, then the two columns of every pair of A and V,
+// with the exact 2x2 result written for the rotated pairs.  Thresholds as in
+// jacobi_reg (relative, with floor_abs).  Stops after a sweep without rotation
+// or 30 sweeps.  All threads call.
+template <int NT>
+__device__ void jacobi_cta(float* A, float* V, double* lam, int n, float floor_abs, JacPairs& J) {
+  const int tid = threadIdx.x;
+  const int m = n + (n & 1);
+  const int h = m / 2;
+  for (int e = tid; e < NM * NM; e += NT) {
+    const int i = e / NM, j = e % NM;
+    V[e] = (i == j) ? 1.0f : 0.0f;
+    if (i >= n || j >= n) A[e] = 0.0f;
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < 30 && n > 1; ++sweep) {
+    int any = 0;
+    for (int round = 0; round < m - 1; ++round) {
+      int act = 0;
+      if (tid < h) {
+        int p, q;
+        circle_pair(round, tid, m, p, q);
+        const float app = A[p * NM + p], aqq = A[q * NM + q], apq = A[p * NM + q];
+        const float gpp = fabsf(app), gqq = fabsf(aqq);
+        const float thr = fmaxf(fmaxf(1.0e-7f * sqrtf(gpp * gqq), 4.0f * 5.9604645e-8f * fmaxf(gpp, gqq)), floor_abs);
+        float c = 1.0f, s = 0.0f, t = 0.0f;
+        if (fabsf(apq) > thr && apq != 0.0f) {
+          const float theta = (aqq - app) / (2.0f * apq);
+          if (fabsf(theta) > 1e18f) t = 0.5f / theta;
+          else t = (theta >= 0.0f ? 1.0f : -1.0f) / (fabsf(theta) + sqrtf(1.0f + theta * theta));
+          c = 1.0f / sqrtf(1.0f + t * t);
+          s = t * c;
+          act = 1;
+        }
+        J.p[tid] = p; J.q[tid] = q; J.act[tid] = act;
+        J.c[tid] = c; J.s[tid] = s; J.t[tid] = t;
+        J.app[tid] = app; J.aqq[tid] = aqq; J.apq[tid] = apq;
+      }
+      if (!__syncthreads_or(act)) continue;
+      any = 1;
+      // rows p and q of every active pair
+      for (int it = tid; it < h * NM; it += NT) {
+        const int k = it / NM, j = it - k * NM;
+        if (J.act[k] && j < n) {
+          const int p = J.p[k], q = J.q[k];
+          const float c = J.c[k], s = J.s[k];
+          const float x = A[p * NM + j], y = A[q * NM + j];
+          A[p * NM + j] = c * x - s * y;
+          A[q * NM + j] = s * x + c * y;
+        }
+      }
+      __syncthreads();
+      // columns p and q of every active pair, of A (exact 2x2 block) and of V
+      for (int it = tid; it < 2 * h * NM; it += NT) {
+        const bool isv = it >= h * NM;
+        const int it2 = isv ? it - h * NM : it;
+        const int i = it2 / h, k = it2 - i * h;
+        if (J.act[k] && i < n) {
+          const int p = J.p[k], q = J.q[k];
+          const float c = J.c[k], s = J.s[k];
+          float* Mx = isv ? V : A;
+          const float x = Mx[i * NM + p], y = Mx[i * NM + q];
+          float nx = c * x - s * y, ny = s * x + c * y;
+          if (!isv) {
+            const float t = J.t[k], apq = J.apq[k];
+            if (i == p) { nx = J.app[k] - t * apq; ny = 0.0f; }
+            else if (i == q) { nx = 0.0f; ny = J.aqq[k] + t * apq; }
+          }
+          Mx[i * NM + p] = nx;
+          Mx[i * NM + q] = ny;
+        }
+      }
+      __syncthreads();
+    }
+    if (!any) break;
+  }
+  if (tid < n) lam[tid] = (double)A[tid * NM + tid];
+  __syncthreads();
+}
+
 }  // namespace dls
