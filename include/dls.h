@@ -50,9 +50,12 @@ enum { DLS_EB_ABS = 0, DLS_EB_REL_RANGE = 1, DLS_EB_NRMSE = 2 };
  *   FP32:   FP32 products on the CUDA cores with FP32 accumulation; FP32
  *           Jacobi refined to FP64 accuracy; every stored decision (quantized
  *           coefficient, rank test, correction, escape) keeps FP64 semantics.
- *   TF32X3 / BF16X3: as FP32 with the Gram and projection products on the
- *           tensor cores as 3-term split products (reserved: rejected with
- *           DLS_ERR_INVALID_ARG by builds without those kernels).
+ *   TF32X3: as FP32, with the block Gram on the tensor cores (tcgen05) as a
+ *           3-term TF32 split product (hi hi + hi lo + lo hi, FP32
+ *           accumulation) for 16 x 16 x bz x 16 blocks of a field whose x
+ *           extent is a multiple of 4; other blocks use the FP32 Gram.  The
+ *           projection stays on the CUDA cores.
+ *   BF16X3: reserved (rejected with DLS_ERR_INVALID_ARG).
  * Non-FP64 modes apply to float32 fields with a Gram order <= 16; other
  * fields take the FP64 form whatever the mode. */
 enum { DLS_PREC_FP64 = 0, DLS_PREC_TF32X3 = 1, DLS_PREC_BF16X3 = 2, DLS_PREC_FP32 = 3 };
@@ -259,7 +262,8 @@ int dls_mlp_train(float* d_params, float* d_adam, const float* d_feat, const flo
  * accepted, blocks that fell back to the bisection, and FP64 re-evaluations
  * of E(r) taken because the FP32 estimate could not decide; then the cycles
  * spent waiting for staged tiles (included in the phases above; 0 for blocks
- * the row-loading kernel serves).  count >= 13.  Synchronous copy. */
+ * the row-loading kernel serves); then the number of blocks whose Gram ran on
+ * the tensor cores (DLS_PREC_TF32X3).  count >= 14.  Synchronous copy. */
 int dls_phase_cycles(const dls_params* p, const void* d_workspace, unsigned long long* h_cycles, int32_t count);
 
 /* Stream header as a host struct (reads the header with one synchronous copy). */

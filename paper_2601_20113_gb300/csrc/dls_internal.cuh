@@ -214,7 +214,7 @@ struct MixedWork {
   unsigned long long* phase;   // ctas x kMixedPhases cycle counters
 };
 constexpr int kMaxMixedN = 16;
-constexpr int kMixedPhases = 13;
+constexpr int kMixedPhases = 14;
 
 // Block-rank MLP: 32 features -> 64 -> 64 -> 1 (ReLU).  Parameter vector layout
 // (floats): [mu 32][sigma 32][W1 64x32][b1 64][W2 64x64][b2 64][W3 64][b3 1].

@@ -48,7 +48,7 @@ struct MxArgs {
 };
 // Phases timed by the per-CTA cycle counters.
 enum { kPhGram = 0, kPhJacobi, kPhRefine, kPhRR, kPhPredict, kPhEncode, kPhDecide, kPhSearch, kPhPack,
-       kCntAccepted, kCntSearched, kCntExact, kPhTileWait, kPhases };
+       kCntAccepted, kCntSearched, kCntExact, kPhTileWait, kCntTcGram, kPhases };
 
 struct MxSmem {
   float G32[NM * NM];

@@ -38,7 +38,7 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 enum { kPhGram = 0, kPhJacobi, kPhRefine, kPhRR, kPhPredict, kPhEncode, kPhDecide, kPhSearch, kPhPack,
-       kCntAccepted, kCntSearched, kCntExact, kPhTileWait, kPhases };
+       kCntAccepted, kCntSearched, kCntExact, kPhTileWait, kCntTcGram, kPhases };
 static_assert(kPhases == kMixedPhases, "phase counter layout");
 
 struct TileArgs {
@@ -61,6 +61,7 @@ struct TileArgs {
   int bxb, yc, zc, bt;     // chunk box (x, y, z, t)
   int rc;                  // rows per chunk = bxb * yc * zc
   uint32_t mbx, myc;       // ceil(2^32 / bxb), ceil(2^32 / yc) (0 for a divisor of 1)
+  int tc_gram;             // 1: Gram pass on the tensor cores (3xTF32), chunk box 16 x 16 x 1 x 16
   double jfloor;           // Jacobi skip floor as a fraction of the per-mode budget
 };
 
@@ -90,6 +91,10 @@ struct __align__(128) TileSmem {
   int64_t colbase[NM + 1];
   unsigned long long ph[kPhases];   // cycle counters of this CTA (thread 0)
   JacPairs jp;
+  unsigned long long mma_bar;     // tcgen05.commit target
+  uint32_t mma_phase;             // commits waited for so far (thread 0)
+  int mma_pending;                // a wait for products timed out
+  uint32_t tmem_base;             // TMEM columns of this CTA (tensor-core Gram)
   BlockMeta m;
   RecLayout lay;
 };
@@ -134,6 +139,37 @@ __device__ __forceinline__ void cp_async_arrive(unsigned long long* b) {
   asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(b)) : "memory");
 }
 
+// ---------------------------------------------------------------- tcgen05
+// Shared-memory matrix descriptor, no swizzle: start, leading byte offset (the
+// K-direction stride between 8x16-byte core matrices), stride byte offset
+// (between 8-row groups), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+__device__ __forceinline__ void tc_mma_tf32(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+               "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+               : "memory");
+}
+__device__ __forceinline__ void tc_commit(unsigned long long* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+// 8 consecutive FP32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tc_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+constexpr uint32_t kTmemCols = 128;
+
 // ---------------------------------------------------------------- chunk geometry
 // A block is cut into chunks of zc z-planes x yc y-lines (all x, all t); the
 // chunk's tile in shared memory is [t][z][y][x] with bxb x-values per line,
@@ -173,14 +209,31 @@ __device__ __forceinline__ int64_t gidx_row(const TileArgs& a, const Geom& g, in
          (g.x0 + x);
 }
 
-__device__ void issue_chunk(const TileArgs& a, const CUtensorMap* tm, TileSmem& S, const Geom& g, const Chunks& ch,
-                            int c, uint32_t& iss) {
+// The two tensor maps of a launch: row tiles [t][z][y][x] for the row-wise
+// passes, and the core-matrix tiles of the tensor-core Gram (see pass_gram_tc).
+struct Maps {
+  const CUtensorMap* row;
+  const CUtensorMap* gram;
+};
+constexpr int kLayoutRow = 0, kLayoutGram = 1;
+
+__device__ void issue_chunk(const TileArgs& a, const Maps& tm, TileSmem& S, const Geom& g, const Chunks& ch,
+                            int c, uint32_t& iss, int layout) {
   const int stage = (int)(iss % kStages);
   const int yb = (c % ch.ncy) * a.yc, zb = (c / ch.ncy) * a.zc;
-  if (a.use_tma) {
+  if (layout == kLayoutGram) {
+    // two boxes {4 x, 8 t, 4 x-groups, 16 y, 1 z}: t 0-7 and t 8-15
     if (threadIdx.x == 0) {
       mbar_expect_tx(&S.full[stage], (unsigned)(a.rc * a.bt * 4));
-      tma_load_5d(&S.ring[stage][0], tm, &S.full[stage], (int)g.x0, (int)(g.y0 + yb), (int)(g.z0 + zb), (int)g.t0,
+      const int tv = g.v * (int)a.P.dims[3] + (int)g.t0;
+      for (int h = 0; h < 2; ++h)
+        tma_load_5d(&S.ring[stage][h * 2048], tm.gram, &S.full[stage], 0, tv + 8 * h, (int)(g.x0 / 4),
+                    (int)(g.y0 + yb), (int)(g.z0 + zb));
+    }
+  } else if (a.use_tma) {
+    if (threadIdx.x == 0) {
+      mbar_expect_tx(&S.full[stage], (unsigned)(a.rc * a.bt * 4));
+      tma_load_5d(&S.ring[stage][0], tm.row, &S.full[stage], (int)g.x0, (int)(g.y0 + yb), (int)(g.z0 + zb), (int)g.t0,
                   g.v);
     }
   } else {
@@ -210,19 +263,21 @@ __device__ __forceinline__ bool wait_chunk(TileSmem& S, uint32_t con) {
   return ok;
 }
 
-// Ring cursor: chunks [0, pf_cnt) of block pf_blk are in flight.
+// Ring cursor: chunks [0, pf_cnt) of block pf_blk, in layout pf_layout, are in flight.
 struct Cursor {
   uint32_t iss, con;
   int64_t pf_blk;
-  int pf_cnt;
+  int pf_cnt, pf_layout;
 };
 
-__device__ void prefetch(const TileArgs& a, const CUtensorMap* tm, TileSmem& S, Cursor& cu, int64_t bi, const Geom& g) {
+__device__ void prefetch(const TileArgs& a, const Maps& tm, TileSmem& S, Cursor& cu, int64_t bi, const Geom& g,
+                         int layout) {
   const Chunks ch = chunks_of(a, g);
   const int k = ch.n < kStages ? ch.n : kStages;
-  for (int c = 0; c < k; ++c) issue_chunk(a, tm, S, g, ch, c, cu.iss);
+  for (int c = 0; c < k; ++c) issue_chunk(a, tm, S, g, ch, c, cu.iss, layout);
   cu.pf_blk = bi;
   cu.pf_cnt = k;
+  cu.pf_layout = layout;
 }
 
 // Drops chunks in flight that belong to another block.
@@ -239,13 +294,14 @@ __device__ void drain(TileSmem& S, Cursor& cu) {
 // Streams every chunk of block bi through the ring, calling body(c, tile) for
 // each; all threads call.  Returns false if a wait timed out.
 template <class F>
-__device__ bool stream_block(const TileArgs& a, const CUtensorMap* tm, TileSmem& S, Cursor& cu, int64_t bi,
-                             const Geom& g, F&& body) {
+__device__ bool stream_block(const TileArgs& a, const Maps& tm, TileSmem& S, Cursor& cu, int64_t bi,
+                             const Geom& g, int layout, F&& body) {
   const Chunks ch = chunks_of(a, g);
-  if (cu.pf_blk != bi && cu.pf_cnt > 0) drain(S, cu);
-  const int have = cu.pf_blk == bi ? cu.pf_cnt : 0;
+  const bool match = cu.pf_blk == bi && cu.pf_layout == layout;
+  if (!match && cu.pf_cnt > 0) drain(S, cu);
+  const int have = match ? cu.pf_cnt : 0;
   const int k = ch.n < kStages ? ch.n : kStages;
-  for (int c = have; c < k; ++c) issue_chunk(a, tm, S, g, ch, c, cu.iss);
+  for (int c = have; c < k; ++c) issue_chunk(a, tm, S, g, ch, c, cu.iss, layout);
   cu.pf_cnt = 0;
   cu.pf_blk = -1;
   for (int c = 0; c < ch.n; ++c) {
@@ -255,7 +311,7 @@ __device__ bool stream_block(const TileArgs& a, const CUtensorMap* tm, TileSmem&
     body(c, ch, &S.ring[cu.con % kStages][0]);
     __syncthreads();
     ++cu.con;
-    if (c + kStages < ch.n) issue_chunk(a, tm, S, g, ch, c + kStages, cu.iss);
+    if (c + kStages < ch.n) issue_chunk(a, tm, S, g, ch, c + kStages, cu.iss, layout);
   }
   return true;
 }
@@ -280,6 +336,39 @@ __device__ void cta_reduce(TileSmem& S, const float* v, int cnt) {
   __syncthreads();
 }
 
+// After the Gram pass: time-gradient energy sum_rows sum_j (x_{j+1} - x_j)^2
+// from the Gram, the row-norm bound n max|x|^2 from the range, and the
+// non-finite screen on the diagonal with an exact rescan when it trips (a
+// finite block whose squares overflow is not an input error).  All threads.
+__device__ void derived_stats(const TileArgs& a, TileSmem& S, const Geom& g, int n) {
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    float tg = 0.0f;
+    bool screen = false;
+    for (int j = 0; j < n; ++j) {
+      if (!isfinite(S.G32[j * NM + j])) screen = true;
+      if (j + 1 < n) tg += S.G32[(j + 1) * NM + j + 1] + S.G32[j * NM + j] - 2.0f * S.G32[j * NM + j + 1];
+    }
+    float mnn = S.st_min[0], mxx = S.st_max[0];
+    for (int w = 1; w < kWarps; ++w) { mnn = fminf(mnn, S.st_min[w]); mxx = fmaxf(mxx, S.st_max[w]); }
+    const float am = fmaxf(fabsf(mnn), fabsf(mxx));
+    S.st_tg[0] = fmaxf(tg, 0.0f);
+    S.st_rowmax[0] = (float)n * am * am;
+    S.nonfinite = screen ? 2 : 0;
+  }
+  __syncthreads();
+  if (S.nonfinite == 2) {
+    int bad = 0;
+    for (int64_t e = tid; e < g.N; e += kTT) {
+      const int64_t lt = e / g.M, ls = e - lt * g.M;
+      if (!isfinite(__ldg(a.in + gidx_row(a, g, ls, (int)lt)))) bad = 1;
+    }
+    bad = __syncthreads_or(bad);
+    if (tid == 0) S.nonfinite = bad;
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------- Gram pass
 // Group g (2 warps) accumulates packed pairs [68 g, 68 g + 68) over every row;
 // each group gathers the statistics of every other row.  With `project`, rows
@@ -287,7 +376,7 @@ __device__ void cta_reduce(TileSmem& S, const float* v, int cnt) {
 // NF = 16: the Gram order is 16 and known at compile time (no per-column
 // predicates); NF = 0: any order n <= 16.
 template <bool PROJECT, int NF>
-__device__ __noinline__ bool pass_gram(const TileArgs& a, const CUtensorMap* tm, TileSmem& S, Cursor& cu, int64_t bi,
+__device__ __noinline__ bool pass_gram(const TileArgs& a, const Maps& tm, TileSmem& S, Cursor& cu, int64_t bi,
                           const Geom& g) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int grp = tid / kGT, gt = tid % kGT;
@@ -296,7 +385,7 @@ __device__ __noinline__ bool pass_gram(const TileArgs& a, const CUtensorMap* tm,
 #pragma unroll
   for (int p = 0; p < kHalf; ++p) acc[p] = 0.0f;
   float mn = INFINITY, mx = -INFINITY, xg = 0.0f;
-  const bool ok = stream_block(a, tm, S, cu, bi, g, [&](int c, const Chunks& ch, const float* tile) {
+  const bool ok = stream_block(a, tm, S, cu, bi, g, kLayoutRow, [&](int c, const Chunks& ch, const float* tile) {
     int ii = 0;
     for (int r = gt; r < a.rc; r += kGT, ++ii) {
       int xx;
@@ -386,35 +475,162 @@ __device__ __noinline__ bool pass_gram(const TileArgs& a, const CUtensorMap* tm,
     }
   }
   __syncthreads();
-  if (!PROJECT && tid == 0) {
-    // time-gradient energy sum_rows sum_j (x_{j+1} - x_j)^2 from the Gram;
-    // row-norm bound n max|x|^2; non-finite screen on the diagonal
-    float tg = 0.0f;
-    bool screen = false;
-    for (int j = 0; j < n; ++j) {
-      if (!isfinite(S.G32[j * NM + j])) screen = true;
-      if (j + 1 < n) tg += S.G32[(j + 1) * NM + j + 1] + S.G32[j * NM + j] - 2.0f * S.G32[j * NM + j + 1];
+  if (!PROJECT) derived_stats(a, S, g, n);
+  return true;
+}
+
+// ---------------------------------------------------------------- tensor-core Gram
+// Gram pass on the tensor cores (3xTF32), for chunk boxes of 16 x 16 x 1 x 16.
+// The Gram map stages a chunk as [t / 8][y][x / 4][t % 8][x % 4]: each y-pair
+// is a subset s of 32 spatial rows, and the tile is the K-major operand of a
+// 128-row matrix A whose row m = (t / 8, s, t % 8) holds time step t over the
+// 32 rows of subset s (8-row groups 1024 B apart, 4-row K steps 128 B apart,
+// no swizzle).  D = A A^T accumulates in TMEM over the chunks of the block;
+// the Gram is the sum of its eight diagonal 16 x 16 blocks (one per subset).
+// Split precision: the staged x is replaced by hi = x with its 13 low mantissa
+// bits cleared and lo = x - hi, also truncated to TF32, goes to a second
+// buffer; D += hi hi^T + hi lo^T + lo hi^T.  Both operands are exact TF32
+// values, so the products do not depend on how the tensor cores read FP32;
+// the split keeps about 21 bits of each x (relative error 2^-21).
+__device__ __forceinline__ float tf32_trunc(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
+
+__device__ __noinline__ bool pass_gram_tc(const TileArgs& a, const Maps& tm, TileSmem& S, Cursor& cu, int64_t bi,
+                                          const Geom& g, float* lo) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = g.n;
+  float mn = INFINITY, mx = -INFINITY, xg = 0.0f;
+  // D FP32; A, B TF32, K-major; N = 128 (bits 17-22: N/8), M = 128 (bits 24-28: M/16)
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+  uint32_t accum = 0;
+  const bool ok = stream_block(a, tm, S, cu, bi, g, kLayoutGram, [&](int c, const Chunks& ch, const float* tile_c) {
+    float* tile = const_cast<float*>(tile_c);
+    // statistics of the valid elements (read-only pass: neighbours are read)
+    for (int gi = tid; gi < 1024; gi += kTT) {
+      const int t = (gi >> 9) * 8 + (gi & 7), xc = (gi >> 3) & 3, y = (gi >> 5) & 15;
+      if (t < n && y < g.sy) {
+        const float4 v = reinterpret_cast<const float4*>(tile)[gi];
+        const float xv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int x = xc * 4 + i;
+          if (x < g.sx) {
+            mn = fminf(mn, xv[i]);
+            mx = fmaxf(mx, xv[i]);
+            if (x + 1 < g.sx) {
+              const float nb = i < 3 ? xv[i + 1] : tile[(gi + 8) * 4];
+              const float d = nb - xv[i];
+              xg = __fmaf_rn(d, d, xg);
+            }
+          }
+        }
+      }
     }
-    float mnn = S.st_min[0], mxx = S.st_max[0];
-    for (int w = 1; w < kWarps; ++w) { mnn = fminf(mnn, S.st_min[w]); mxx = fmaxf(mxx, S.st_max[w]); }
-    const float am = fmaxf(fabsf(mnn), fabsf(mxx));
-    S.st_tg[0] = fmaxf(tg, 0.0f);
-    S.st_rowmax[0] = (float)n * am * am;
-    S.nonfinite = screen ? 2 : 0;
-  }
-  __syncthreads();
-  if (!PROJECT && S.nonfinite == 2) {
-    // a non-finite diagonal: look for a non-finite input value exactly (a
-    // finite block whose squares overflow is not an input error)
-    int bad = 0;
-    for (int64_t e = tid; e < g.N; e += kTT) {
-      const int64_t lt = e / g.M, ls = e - lt * g.M;
-      if (!isfinite(__ldg(a.in + gidx_row(a, g, ls, (int)lt)))) bad = 1;
+    __syncthreads();
+    // split into hi (in place) and lo
+    for (int gi = tid; gi < 1024; gi += kTT) {
+      const float4 v = reinterpret_cast<const float4*>(tile)[gi];
+      float4 h, l;
+      h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u); l.x = tf32_trunc(__fsub_rn(v.x, h.x));
+      h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u); l.y = tf32_trunc(__fsub_rn(v.y, h.y));
+      h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u); l.z = tf32_trunc(__fsub_rn(v.z, h.z));
+      h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u); l.w = tf32_trunc(__fsub_rn(v.w, h.w));
+      reinterpret_cast<float4*>(tile)[gi] = h;
+      reinterpret_cast<float4*>(lo)[gi] = l;
     }
-    bad = __syncthreads_or(bad);
-    if (tid == 0) S.nonfinite = bad;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor core reads
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t ha = smem_u32(tile), la = smem_u32(lo);
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        const uint64_t dh = sdesc(ha + ks * 256, 128, 1024), dl = sdesc(la + ks * 256, 128, 1024);
+        tc_mma_tf32(S.tmem_base, dh, dh, idesc, accum);
+        accum = 1;
+        tc_mma_tf32(S.tmem_base, dh, dl, idesc, 1);
+        tc_mma_tf32(S.tmem_base, dl, dh, idesc, 1);
+      }
+      tc_commit(&S.mma_bar);
+      // the stage and the lo buffer are reused next: wait for the products
+      if (mbar_wait(&S.mma_bar, S.mma_phase & 1u)) {
+        ++S.mma_phase;
+      } else {
+        S.abort_flag = 1;
+        S.mma_pending = 1;
+      }
+    }
+    (void)c; (void)ch;
+  });
+  if (!ok) return false;
+  tc_fence_after();
+  // read D: warp w holds rows m = 32 w + lane = (t / 8 = w / 2, s = 4 (w % 2) + lane / 8, t % 8 = lane % 8)
+  {
+    const int half = warp & 1, sl = lane >> 3, tl = lane & 7, h = warp >> 1;
+    float v0[8], v1[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) { v0[i] = 0.0f; v1[i] = 0.0f; }
+    const uint32_t tw = S.tmem_base + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float r0[8], r1[8];
+      tc_ld8(tw + (uint32_t)((4 * half + q) * 8), r0);
+      tc_ld8(tw + (uint32_t)(64 + (4 * half + q) * 8), r1);
+      if (sl == q) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) { v0[i] = r0[i]; v1[i] = r1[i]; }
+      }
+    }
+    // sum the warp's four subsets: lanes tl, tl + 8, tl + 16, tl + 24
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      v0[i] = __fadd_rn(v0[i], __shfl_xor_sync(FULL, v0[i], 8));
+      v1[i] = __fadd_rn(v1[i], __shfl_xor_sync(FULL, v1[i], 8));
+      v0[i] = __fadd_rn(v0[i], __shfl_xor_sync(FULL, v0[i], 16));
+      v1[i] = __fadd_rn(v1[i], __shfl_xor_sync(FULL, v1[i], 16));
+    }
+    float* part = &S.red[0][0];                 // [h][t % 8][16]
+    if (half == 1 && sl == 0) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) { part[(h * 8 + tl) * 16 + i] = v0[i]; part[(h * 8 + tl) * 16 + 8 + i] = v1[i]; }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (half == 0 && sl == 0) {
+      const int t = h * 8 + tl;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        S.G32[t * NM + i] = __fadd_rn(v0[i], part[(h * 8 + tl) * 16 + i]);
+        S.G32[t * NM + 8 + i] = __fadd_rn(v1[i], part[(h * 8 + tl) * 16 + 8 + i]);
+      }
+    }
     __syncthreads();
   }
+  // symmetric from the upper triangle; FP64 copy; statistics
+  for (int e = tid; e < NM * NM; e += kTT) {
+    const int i = e / NM, j = e % NM;
+    if (i < n && j < n) {
+      const float v = i <= j ? S.G32[i * NM + j] : S.G32[j * NM + i];
+      S.G64[e] = (double)v;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < NM * NM; e += kTT) {
+    const int i = e / NM, j = e % NM;
+    if (i < n && j < n) S.G32[e] = (float)S.G64[e];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = fminf(mn, __shfl_xor_sync(FULL, mn, o));
+    mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, o));
+    xg += __shfl_xor_sync(FULL, xg, o);
+  }
+  if (lane == 0) {
+    S.st_min[warp] = mn; S.st_max[warp] = mx; S.st_xg[warp] = xg;
+    S.st_tg[warp] = 0.0f; S.st_rowmax[warp] = 0.0f;
+  }
+  if (tid == 0) S.ph[kCntTcGram] += 1;
+  __syncthreads();
+  derived_stats(a, S, g, n);
   return true;
 }
 
@@ -618,7 +834,7 @@ __device__ __forceinline__ void row_decode_step(const TileSmem& S, int k, float 
 // the projection and the decode step.  Column widths: OR of zigzag(q) over
 // the warp (same bit width as the maximum) into S.qor.
 template <int NF>
-__device__ __noinline__ bool pass_encode(const TileArgs& a, const CUtensorMap* tm, TileSmem& S, Cursor& cu, int64_t bi,
+__device__ __noinline__ bool pass_encode(const TileArgs& a, const Maps& tm, TileSmem& S, Cursor& cu, int64_t bi,
                             const Geom& g, int r, bool check, const RowConst& rcst, const CorrConst& cc, bool pointwise,
                             int32_t* qs, int8_t* k8, int32_t* k32) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -630,7 +846,7 @@ __device__ __noinline__ bool pass_encode(const TileArgs& a, const CUtensorMap* t
   int nc = 0, ne = 0, ovf = 0;
   uint32_t kmx = 0;
   const int M = (int)g.M, Lq = (int)align_up(g.L, 4), rc = a.rc;
-  const bool ok = stream_block(a, tm, S, cu, bi, g, [&](int c, const Chunks& ch, const float* tile) {
+  const bool ok = stream_block(a, tm, S, cu, bi, g, kLayoutRow, [&](int c, const Chunks& ch, const float* tile) {
     for (int rb = 0; rb < rc; rb += kTT) {          // same trip count in every lane
       const int rr = rb + tid;
       int xx = 0;
@@ -720,13 +936,13 @@ __device__ __noinline__ bool pass_encode(const TileArgs& a, const CUtensorMap* t
 
 // E(r) for every r in [0, rcap] (FP32 estimates into S.Ered).
 template <int NF>
-__device__ __noinline__ bool pass_all_errors(const TileArgs& a, const CUtensorMap* tm, TileSmem& S, Cursor& cu, int64_t bi,
+__device__ __noinline__ bool pass_all_errors(const TileArgs& a, const Maps& tm, TileSmem& S, Cursor& cu, int64_t bi,
                                 const Geom& g, int rcap, const RowConst& rcst, int& ovf) {
   const int tid = threadIdx.x, n = NF ? NF : g.n;
   float E[NM + 1];
 #pragma unroll
   for (int r = 0; r <= NM; ++r) E[r] = 0.0f;
-  const bool ok = stream_block(a, tm, S, cu, bi, g, [&](int c, const Chunks& ch, const float* tile) {
+  const bool ok = stream_block(a, tm, S, cu, bi, g, kLayoutRow, [&](int c, const Chunks& ch, const float* tile) {
     for (int rr = tid; rr < a.rc; rr += kTT) {
       int xx;
       const int l = row_index(a, g, ch, c, rr, &xx);
@@ -1170,26 +1386,48 @@ __device__ __noinline__ void write_record(const TileArgs& a, TileSmem& S, const 
 }
 
 // ---------------------------------------------------------------- the kernel
-template <int MINB>
-__global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUtensorMap tmap, const TileArgs a) {
+// TC: the tensor-core Gram (its instantiation alone contains tcgen05 code).
+template <int MINB, bool TC>
+__global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUtensorMap tmap,
+                                                    const __grid_constant__ CUtensorMap tmapg, const TileArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // TMA destinations: align the tile ring to 1024 bytes explicitly
   const uint32_t sbase = smem_u32(smem_raw);
   TileSmem& S = *reinterpret_cast<TileSmem*>(smem_raw + (((sbase + 1023u) & ~1023u) - sbase));
-  const CUtensorMap* tm = &tmap;
+  const Maps tm{&tmap, &tmapg};
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int32_t* qs = a.q_scr + (int64_t)blockIdx.x * NM * a.lmax;
   int8_t* k8 = a.k8_scr + (int64_t)blockIdx.x * a.nptmax;
   int32_t* k32 = a.k32_scr + (int64_t)blockIdx.x * a.nptmax;
   const Plan& P = a.P;
+  // tensor-core Gram: the lo buffer follows the shared struct (1024-aligned)
+  float* lobuf = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(&S) +
+                                          align_up((int64_t)sizeof(TileSmem), 1024));
+  (void)lobuf;
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) mbar_init(&S.full[s], a.use_tma ? 1u : (unsigned)kTT);
+    mbar_init(&S.mma_bar, 1u);
+    S.mma_phase = 0;
+    S.mma_pending = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     S.nexact = 0;
     S.abort_flag = 0;
   }
-  __syncthreads();
+  if (TC) {
+    if (warp == 0) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
+                   "r"(kTmemCols)
+                   : "memory");
+      // give up the allocation permit at once, so further CTAs can become resident
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  } else {
+    __syncthreads();
+  }
   if (tid < kPhases) S.ph[tid] = 0;
   long long tck = clock64();
   auto mark = [&](int p) {
@@ -1208,7 +1446,7 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
     }
   };
   Cursor cu;
-  cu.iss = 0; cu.con = 0; cu.pf_blk = -1; cu.pf_cnt = 0;
+  cu.iss = 0; cu.con = 0; cu.pf_blk = -1; cu.pf_cnt = 0; cu.pf_layout = kLayoutRow;
   if (tid == 0) S.bnext = grab();
   __syncthreads();
   for (;;) {
@@ -1233,7 +1471,11 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
 
     if (tid == 0) tck = clock64();
     const bool full = n == NM;   // Gram order 16: the passes without per-column predicates
-    if (!(full ? pass_gram<false, NM>(a, tm, S, cu, bi, g) : pass_gram<false, 0>(a, tm, S, cu, bi, g))) break;
+    if (TC) {
+      if (!pass_gram_tc(a, tm, S, cu, bi, g, lobuf)) break;
+    } else if (!(full ? pass_gram<false, NM>(a, tm, S, cu, bi, g) : pass_gram<false, 0>(a, tm, S, cu, bi, g))) {
+      break;
+    }
     mark(kPhGram);
     if (S.nonfinite) {
       if (tid == 0) atomicOr(&a.status->nonfinite, 1u);
@@ -1241,7 +1483,7 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
       continue;
     }
     // the encode pass reads the same block again: start its first chunks now
-    prefetch(a, tm, S, cu, bi, g);
+    prefetch(a, tm, S, cu, bi, g, kLayoutRow);
     // rotations below 1% of the per-mode budget eb^2 L change no decision
     // worth a sweep; the decisions themselves stay exact
     const float jfloor = (float)(a.jfloor * (P.eb_type == DLS_EB_NRMSE ? el2 / n : vi.eb * vi.eb * (double)g.L));
@@ -1260,7 +1502,7 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
       const double noise = (P.eb_type == DLS_EB_NRMSE ? el2 / n : budget);
       if (n > 1 && 4.0 * 5.9604644775390625e-8 * tr > 0.1 * noise) {
         if (!(full ? pass_gram<true, NM>(a, tm, S, cu, bi, g) : pass_gram<true, 0>(a, tm, S, cu, bi, g))) break;
-        prefetch(a, tm, S, cu, bi, g);
+        prefetch(a, tm, S, cu, bi, g, kLayoutRow);
         jacobi_cta<kTT>(S.G32, S.Vj, S.lam_t, n, jfloor, S.jp);
         // V = Vst W in FP64; eigenvalues from the Rayleigh-Ritz diagonal
         for (int e = tid; e < NM * NM; e += kTT) {
@@ -1373,7 +1615,7 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
     // the next block's first chunks load while this record is packed
     {
       const int64_t bn = S.bnext;
-      if (bn < P.nb) prefetch(a, tm, S, cu, bn, block_geom(P, P.b0 + bn));
+      if (bn < P.nb) prefetch(a, tm, S, cu, bn, block_geom(P, P.b0 + bn), TC ? kLayoutGram : kLayoutRow);
     }
     write_record(a, S, g, bi, raw, r, qs, k8, k32);
     mark(kPhPack);
@@ -1382,10 +1624,20 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
   if (S.abort_flag) {
     if (tid == 0) atomicOr(&a.status->timeout, 1u);
   }
-  // leave no copy in flight
+  // leave no copy and no product in flight, then give back the TMEM
   while (cu.con < cu.iss) {
     mbar_wait(&S.full[cu.con % kStages], (cu.con / kStages) & 1u);
     ++cu.con;
+  }
+  if (TC) {
+    if (tid == 0 && S.mma_pending) mbar_wait(&S.mma_bar, S.mma_phase & 1u);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+      tc_fence_after();
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem_base), "r"(kTmemCols)
+                   : "memory");
+    }
   }
   if (tid == 0) {
     S.ph[kCntExact] = S.nexact;
@@ -1428,22 +1680,46 @@ bool tile_chunk_box(const Plan& p, int* bxb, int* yc, int* zc, int* bt) {
   return true;
 }
 
-size_t tile_smem_bytes() { return sizeof(TileSmem) + 1024; }
+// Dynamic shared memory: alignment slack, the shared struct, and with the
+// tensor-core Gram the 16 KiB lo buffer.
+size_t tile_smem_bytes(bool tc) {
+  return 1024 + (size_t)align_up((int64_t)sizeof(TileSmem), 1024) + (tc ? (size_t)kStageFloats * 4 : 0);
+}
 
-int tile_ctas_per_sm(int variant) {
-  int nb = 0;
-  const size_t smem = tile_smem_bytes();
-  if (variant == 1) {
-    if (cudaFuncSetAttribute(k_tile<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tile<2>, kTT, smem) != cudaSuccess)
-      nb = 0;
-  } else {
-    if (cudaFuncSetAttribute(k_tile<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tile<4>, kTT, smem) != cudaSuccess)
-      nb = 0;
-  }
+// Resident CTAs per SM from the kernel's registers and shared memory and the
+// device's per-SM limits (and, with the tensor-core Gram, the TMEM columns).
+// Computed here because the occupancy query treats a kernel that contains
+// tcgen05.alloc as one CTA per SM.
+template <int MINB, bool TC>
+int ctas_per_sm_of() {
+  const bool tc = TC;
+  const size_t smem = tile_smem_bytes(tc);
+  if (cudaFuncSetAttribute(k_tile<MINB, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  cudaFuncAttributes fa;
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaFuncGetAttributes(&fa, k_tile<MINB, TC>) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+    return 0;
+  // registers are allocated per warp in units of 256
+  const int regs_warp = (int)align_up((int64_t)fa.numRegs * 32, 256);
+  const int by_regs = prop.regsPerMultiprocessor / (regs_warp * (kTT / 32));
+  const int by_smem = (int)(prop.sharedMemPerMultiprocessor /
+                            (smem + (size_t)fa.sharedSizeBytes + prop.reservedSharedMemPerBlock));
+  const int by_threads = prop.maxThreadsPerMultiProcessor / kTT;
+  int n = by_regs < by_smem ? by_regs : by_smem;
+  n = n < by_threads ? n : by_threads;
+  n = n < prop.maxBlocksPerMultiProcessor ? n : prop.maxBlocksPerMultiProcessor;
+  if (tc) n = n < (int)(512 / kTmemCols) ? n : (int)(512 / kTmemCols);
+  return n;
+}
+
+int tile_ctas_per_sm(int variant, bool tc) {
+  const int n = tc ? (variant == 1 ? ctas_per_sm_of<2, true>() : ctas_per_sm_of<4, true>())
+                  : (variant == 1 ? ctas_per_sm_of<2, false>() : ctas_per_sm_of<4, false>());
   cudaGetLastError();
-  return nb;
+  return n;
 }
 
 int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, int learned, int variant,
@@ -1492,17 +1768,40 @@ int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, in
       a.use_tma = rc == CUDA_SUCCESS ? 1 : 0;
     }
   }
+  // tensor-core Gram (3xTF32): 16 x 16 x bz x 16 blocks on a TMA-aligned field;
+  // the second map stages chunks as [t / 8][y][x / 4][t % 8][x % 4]
+  CUtensorMap tmapg;
+  memset(&tmapg, 0, sizeof(tmapg));
+  a.tc_gram = 0;
+  if (p.precision == DLS_PREC_TF32X3 && a.use_tma && a.bxb == 16 && a.yc == 16 && a.zc == 1 && a.bt == 16) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    const cuuint64_t dims[5] = {4, (cuuint64_t)(p.dims[3] * p.nvars), (cuuint64_t)(p.dims[0] / 4), (cuuint64_t)p.dims[1],
+                                (cuuint64_t)p.dims[2]};
+    const cuuint64_t strides[4] = {(cuuint64_t)p.P * 4, 16, (cuuint64_t)p.dims[0] * 4,
+                                   (cuuint64_t)(p.dims[0] * p.dims[1]) * 4};
+    const cuuint32_t box[5] = {4, 8, 4, 16, 1};
+    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    if (enc && enc(&tmapg, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void*>(d_in), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+      a.tc_gram = 1;
+  }
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return DLS_ERR_CUDA;
-  const int per_sm = tile_ctas_per_sm(variant);
+  const int per_sm = tile_ctas_per_sm(variant, a.tc_gram != 0);
   if (per_sm < 1) return DLS_ERR_CUDA;
   int ctas = sms * per_sm;
   if (ctas > w.ctas) ctas = w.ctas;
   if ((int64_t)ctas > p.nb) ctas = (int)p.nb;
-  const size_t smem = tile_smem_bytes();
-  if (variant == 1) k_tile<2><<<ctas, kTT, smem, s>>>(tmap, a);
-  else k_tile<4><<<ctas, kTT, smem, s>>>(tmap, a);
+  const size_t smem = tile_smem_bytes(a.tc_gram != 0);
+  if (a.tc_gram) {
+    if (variant == 1) k_tile<2, true><<<ctas, kTT, smem, s>>>(tmap, tmapg, a);
+    else k_tile<4, true><<<ctas, kTT, smem, s>>>(tmap, tmapg, a);
+  } else {
+    if (variant == 1) k_tile<2, false><<<ctas, kTT, smem, s>>>(tmap, tmapg, a);
+    else k_tile<4, false><<<ctas, kTT, smem, s>>>(tmap, tmapg, a);
+  }
   return cudaGetLastError() == cudaSuccess ? DLS_OK : DLS_ERR_CUDA;
 }
 

@@ -389,7 +389,7 @@ class CompressPlan:
 
 
 PHASES = ("gram", "jacobi", "refine", "rayleigh_ritz", "predict", "encode", "decide", "search", "pack",
-          "n_accepted", "n_searched", "n_exact_fallback", "tile_wait")
+          "n_accepted", "n_searched", "n_exact_fallback", "tile_wait", "n_tensor_core_gram")
 
 
 def phase_cycles(p: Params, workspace: torch.Tensor) -> dict:

@@ -169,9 +169,32 @@ def test_mixed_mode_on_f64_field_takes_fp64_form():
     assert got.size == ref.size and np.array_equal(got[128:], ref[128:])   # header differs in the precision byte
 
 
-def test_tensor_core_modes_are_reserved():
-    p = dls.make_params((1, 16, 16, 16, 16), dls.F32, (16, 16, 16, 16), 1e-3, precision=dls.PREC_TF32X3)
+def test_bf16x3_mode_is_reserved():
+    p = dls.make_params((1, 16, 16, 16, 16), dls.F32, (16, 16, 16, 16), 1e-3, precision=dls.PREC_BF16X3)
     assert dls.workspace_size(p) == 0
+
+
+@pytest.mark.parametrize("rel", [1e-2, 1e-3, 1e-4])
+def test_tf32x3_tensor_core_gram(rel):
+    """3xTF32 Gram on the tensor cores: every block's Gram runs there (counter),
+    the bound holds at every point and the ratio stays within 1% of the oracle's."""
+    dims = (64, 48, 32, 40)                     # edge blocks in z (0) and t (8 steps)
+    f = synth.modes3d(*dims, seed=21, count=32).numpy()
+    eb = rel * float(f.max() - f.min())
+    cfg = oracle.Config(dims, (16, 16, 16, 16), oracle.F32, eb=eb, rank_cap=16)
+    st, ref, _ = oracle.compress(cfg, f)
+    fd = torch.from_numpy(f).cuda()
+    p = dls.make_params(tuple(f.shape), torch.float32, (16, 16, 16, 16), eb, dls.EB_ABS, 16,
+                        precision=dls.PREC_TF32X3, rank_mode=dls.RANK_TAIL)
+    out = torch.empty(dls.compress_bound(p), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(dls.workspace_size(p), dtype=torch.uint8, device="cuda")
+    st, nb = dls.compress_into(p, fd, out, ws)
+    assert st == 0
+    ph = dls.phase_cycles(p, ws)
+    assert ph["n_tensor_core_gram"] == oracle.num_blocks(cfg)
+    rec = dls.decompress(out[:nb])
+    assert (rec.double() - fd.double()).abs().max().item() <= eb
+    assert abs((f.nbytes / nb) / (f.nbytes / ref.size) - 1) <= 0.01
 
 
 def test_mixed_both_block_sides():
