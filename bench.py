@@ -258,8 +258,13 @@ def _roofline(form, in_bytes, out_bytes, kernel_ms, hbm, peak_kind, dims):
 
 
 def _config(form="learned"):
-    return {"workload": "modes3d 256^3 x 64 float32 (4 GiB), 64 modes |k|<=8, k^-5/3, N(0,1e-3^2) noise, "
-                        "blocks 16^3x16 (16384), abs bound 1e-3 x range, rank cap 16",
+    nb = 1
+    for d, b in zip(DIMS, BLOCK):
+        nb *= -(-d // b)
+    gib = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] * 4 / 2 ** 30
+    return {"workload": f"modes3d {DIMS[0]}x{DIMS[1]}x{DIMS[2]} x {DIMS[3]} float32 ({gib:g} GiB), 64 modes "
+                        f"|k|<=8, k^-5/3, N(0,1e-3^2) noise, blocks 16^3x16 ({nb}), abs bound 1e-3 x range, "
+                        "rank cap 16",
             "form": FORM_TEXT[form],
             "l2": "inputs 4 GiB > 129 MB L2 (no flush)"}
 

@@ -87,3 +87,50 @@ def test_learned_mode_changes_no_stored_byte():
     assert a.size == b.size and np.array_equal(a, b)
     r = rank.cpu().numpy()
     assert r.min() >= -1 and r.max() <= 16
+
+
+def _run_mode(f, eb, mode):
+    p = dls.make_params(tuple(f.shape), torch.float32, (16, 16, 16, 16), eb, dls.EB_ABS, 16,
+                        precision=dls.PREC_FP32, rank_mode=mode)
+    out = torch.empty(dls.compress_bound(p), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(dls.workspace_size(p), dtype=torch.uint8, device="cuda")
+    st, nb = dls.compress_into(p, f, out, ws)
+    assert st == 0
+    ph = dls.phase_cycles(p, ws)
+    s = out[:nb].cpu().numpy().copy()
+    s[67] = 0                                    # header byte: rank mode used
+    return s, ph
+
+
+def test_trained_model_skips_the_search():
+    """What the trained network gains over the method without it.  On a field
+    of the training kind but a seed outside the training set, the trained model
+    predicts the rank the bisection of Algorithm 1 would choose for nearly every
+    block, so those blocks take one encode pass instead of the search; an
+    untrained network of the same shape gets far fewer; the stored bytes equal
+    the bisection's in both cases, and the device cycles drop."""
+    from paper_2601_20113_gb300 import train_rank
+    f = synth.modes3d(64, 64, 64, 32, seed=48_211, count=40, noise=10 ** -2.7, device="cuda")
+    eb = 10 ** -3.3 * float(f.max() - f.min())
+    ref, ph_search = _run_mode(f, eb, dls.RANK_SEARCH)
+    nb = ph_search["n_searched"]
+    assert nb == 128 and ph_search["n_accepted"] == 0
+
+    dls.set_rank_model(train_rank.load_model())
+    got, ph_learned = _run_mode(f, eb, dls.RANK_LEARNED)
+    assert np.array_equal(got, ref)
+    acc_trained = ph_learned["n_accepted"] / nb
+    assert acc_trained >= 0.9, acc_trained
+
+    feat, _ = dls.block_features(f, (16, 16, 16, 16), eb)
+    fe = feat.cpu().numpy()
+    dls.set_rank_model(mlp.init_params(11, fe.mean(0), fe.std(0) + 1e-3))
+    got_u, ph_untrained = _run_mode(f, eb, dls.RANK_LEARNED)
+    assert np.array_equal(got_u, ref)
+    assert ph_untrained["n_accepted"] / nb < acc_trained - 0.3
+
+    work = ("gram", "jacobi", "refine", "rayleigh_ritz", "predict", "encode", "decide", "search", "pack")
+    cyc = {k: sum(ph[x] for x in work) for k, ph in (("search", ph_search), ("learned", ph_learned))}
+    print(f"accepted trained {acc_trained:.3f} untrained {ph_untrained['n_accepted'] / nb:.3f}; "
+          f"cycles learned / search = {cyc['learned'] / cyc['search']:.3f}")
+    assert cyc["learned"] < 0.9 * cyc["search"]
