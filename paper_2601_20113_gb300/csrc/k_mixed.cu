@@ -886,7 +886,7 @@ __device__ __forceinline__ void mixed_body(const MxArgs& a) {
       for (int i = 0; i < n; ++i) tr += S.lam[i];
       const double budget = (vi.eb * vi.eb) * (double)g.L;   // per-mode share of eps_l^2
       const double noise = (P.eb_type == DLS_EB_NRMSE ? el2 / n : budget);
-      if (n > 1 && 4.0 * 5.9604644775390625e-8 * tr > 0.1 * noise) {
+      if (n > 1 && 4.0 * 5.9604644775390625e-8 * tr > 0.5 * noise) {
         pass_gram(a, S, g, true);
         jacobi_cta<kMT>(S.G32, S.Vj, S.lam_t, n, 0.0f, S.jp);
         // V = Vst W in FP64, eigenvalues from the rotated diagonal

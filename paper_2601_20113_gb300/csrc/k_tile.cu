@@ -788,21 +788,33 @@ struct RowConst {
 // + x_0 sum_j Vst[j][k], the differences exact when the row carries a large
 // common part), quantized with FP64 semantics and dequantized in float.
 // The encode, search and exact passes all call this, so all see the same numbers.
+// Shifted projection sum_j d_j v_j + a0 vsum in four interleaved partial
+// sums (j mod 4), combined as (s0 + s1) + (s2 + s3): the one order every pass
+// uses for the coefficients.
+__device__ __forceinline__ float project(const float* d, const float* v, float a0, float vsum, int n) {
+  float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+#pragma unroll
+  for (int j4 = 0; j4 < NM / 4; ++j4) {
+    if (4 * j4 + 0 < n) s0 = __fmaf_rn(d[4 * j4 + 0], v[4 * j4 + 0], s0);
+    if (4 * j4 + 1 < n) s1 = __fmaf_rn(d[4 * j4 + 1], v[4 * j4 + 1], s1);
+    if (4 * j4 + 2 < n) s2 = __fmaf_rn(d[4 * j4 + 2], v[4 * j4 + 2], s2);
+    if (4 * j4 + 3 < n) s3 = __fmaf_rn(d[4 * j4 + 3], v[4 * j4 + 3], s3);
+  }
+  return __fmaf_rn(a0, vsum, __fadd_rn(__fadd_rn(s0, s1), __fadd_rn(s2, s3)));
+}
+
 template <int NF>
 __device__ __forceinline__ float coeff_q(const TileSmem& S, const float* d, float a0, int n_, int k,
                                          const RowConst& rc, int32_t& q, int& ovf) {
   const int n = NF ? NF : n_;
   const float4* vp = reinterpret_cast<const float4*>(&S.VstT[k * NM]);
-  float c = 0.0f;
+  float v[NM];
 #pragma unroll
   for (int j4 = 0; j4 < NM / 4; ++j4) {
-    const float4 v = vp[j4];
-    if (4 * j4 + 0 < n) c = __fmaf_rn(d[4 * j4 + 0], v.x, c);
-    if (4 * j4 + 1 < n) c = __fmaf_rn(d[4 * j4 + 1], v.y, c);
-    if (4 * j4 + 2 < n) c = __fmaf_rn(d[4 * j4 + 2], v.z, c);
-    if (4 * j4 + 3 < n) c = __fmaf_rn(d[4 * j4 + 3], v.w, c);
+    const float4 t = vp[j4];
+    v[4 * j4 + 0] = t.x; v[4 * j4 + 1] = t.y; v[4 * j4 + 2] = t.z; v[4 * j4 + 3] = t.w;
   }
-  c = __fmaf_rn(a0, S.vsum[k], c);
+  const float c = project(d, v, a0, S.vsum[k], n);
   q = quant_exact(c, rc.delta, rc.inv_delta, ovf);
   return __fmul_rn(__int2float_rn(q), rc.delta_f);
 }
@@ -869,11 +881,7 @@ __device__ __noinline__ bool pass_encode(const TileArgs& a, const Maps& tm, Tile
           const float4 t = vp[j4];
           v[4 * j4 + 0] = t.x; v[4 * j4 + 1] = t.y; v[4 * j4 + 2] = t.z; v[4 * j4 + 3] = t.w;
         }
-        float cf = 0.0f;
-#pragma unroll
-        for (int j = 0; j < NM; ++j)
-          if (j < n) cf = __fmaf_rn(d[j], v[j], cf);
-        cf = __fmaf_rn(a0, S.vsum[k], cf);
+        const float cf = project(d, v, a0, S.vsum[k], n);
         const int32_t q = quant_exact(cf, rcst.delta, rcst.inv_delta, ovf);
         if (valid) qs[k * Lq + l] = q;
         const uint32_t wor = __reduce_or_sync(FULL, valid ? zigzag(q) : 0u);
@@ -1484,7 +1492,7 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
     }
     // the encode pass reads the same block again: start its first chunks now
     prefetch(a, tm, S, cu, bi, g, kLayoutRow);
-    // rotations below 1% of the per-mode budget eb^2 L change no decision
+    // rotations below 5% of the per-mode budget eb^2 L change no decision
     // worth a sweep; the decisions themselves stay exact
     const float jfloor = (float)(a.jfloor * (P.eb_type == DLS_EB_NRMSE ? el2 / n : vi.eb * vi.eb * (double)g.L));
     jacobi_cta<kTT>(S.G32, S.Vj, S.lam_t, n, jfloor, S.jp);
@@ -1494,13 +1502,14 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
     __syncthreads();
     mark(kPhRefine);
     // Tight bounds need the modes an FP32 Gram cannot resolve (eigenvalues near
-    // 2^-24 trace G): one Rayleigh-Ritz step on the projected data fixes them.
+    // 2^-24 trace G): one Rayleigh-Ritz step on the projected data fixes them,
+    // when that resolution reaches half the per-mode budget eb^2 L.
     {
       double tr = 0.0;
       for (int i = 0; i < n; ++i) tr += S.lam[i];
       const double budget = (vi.eb * vi.eb) * (double)g.L;
       const double noise = (P.eb_type == DLS_EB_NRMSE ? el2 / n : budget);
-      if (n > 1 && 4.0 * 5.9604644775390625e-8 * tr > 0.1 * noise) {
+      if (n > 1 && 4.0 * 5.9604644775390625e-8 * tr > 0.5 * noise) {
         if (!(full ? pass_gram<true, NM>(a, tm, S, cu, bi, g) : pass_gram<true, 0>(a, tm, S, cu, bi, g))) break;
         prefetch(a, tm, S, cu, bi, g, kLayoutRow);
         jacobi_cta<kTT>(S.G32, S.Vj, S.lam_t, n, jfloor, S.jp);
@@ -1748,7 +1757,7 @@ int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, in
   auto magic = [](int d) -> uint32_t { return d <= 1 ? 0u : (uint32_t)((0x100000000ull + (uint64_t)d - 1) / (uint64_t)d); };
   a.mbx = magic(a.bxb);
   a.myc = magic(a.yc);
-  a.jfloor = 1e-2;
+  a.jfloor = 5e-2;
   CUtensorMap tmap;
   memset(&tmap, 0, sizeof(tmap));
   const bool aligned = (p.dims[0] % 4 == 0) && (p.block[0] % 4 == 0) && (((uintptr_t)d_in & 15) == 0);

@@ -295,8 +295,9 @@ __device__ __forceinline__ void circle_pair(int round, int i, int m, int& p, int
 // receives the eigenvectors as columns and lam the eigenvalues (diagonal),
 // both by index.  Each round rotates m/2 disjoint pairs of the round-robin
 // circle (m = n rounded up to even): rotation parameters by m/2 threads, then
-// the two rows of every pair, then the two columns of every pair of A and V,
-// with the exact 2x2 result written for the rotated pairs.  Thresholds as in
+// in one step every 2x2 block of A (rows of pair k, columns of pair l) becomes
+// J_k^T A_kl J_l, with the exact 2x2 result on the rotated diagonal blocks, and
+// the columns of V rotate.  Thresholds as in
 // jacobi_reg (relative, with floor_abs).  Stops after a sweep without rotation
 // or 30 sweeps.  All threads call.
 template <int NT>
@@ -335,36 +336,39 @@ __device__ void jacobi_cta(float* A, float* V, double* lam, int n, float floor_a
       }
       if (!__syncthreads_or(act)) continue;
       any = 1;
-      // rows p and q of every active pair
-      for (int it = tid; it < h * NM; it += NT) {
-        const int k = it / NM, j = it - k * NM;
-        if (J.act[k] && j < n) {
-          const int p = J.p[k], q = J.q[k];
-          const float c = J.c[k], s = J.s[k];
-          const float x = A[p * NM + j], y = A[q * NM + j];
-          A[p * NM + j] = c * x - s * y;
-          A[q * NM + j] = s * x + c * y;
-        }
-      }
-      __syncthreads();
-      // columns p and q of every active pair, of A (exact 2x2 block) and of V
-      for (int it = tid; it < 2 * h * NM; it += NT) {
-        const bool isv = it >= h * NM;
-        const int it2 = isv ? it - h * NM : it;
-        const int i = it2 / h, k = it2 - i * h;
-        if (J.act[k] && i < n) {
-          const int p = J.p[k], q = J.q[k];
-          const float c = J.c[k], s = J.s[k];
-          float* Mx = isv ? V : A;
-          const float x = Mx[i * NM + p], y = Mx[i * NM + q];
-          float nx = c * x - s * y, ny = s * x + c * y;
-          if (!isv) {
+      // one step: every 2x2 block (pair k rows, pair l columns) of A becomes
+      // J_k^T A_kl J_l (the exact 2x2 result on the rotated diagonal blocks),
+      // and the two columns of every active pair of V rotate
+      const int nblk = h * h;
+      for (int it = tid; it < nblk + n * h; it += NT) {
+        if (it < nblk) {
+          const int k = it / h, l = it - k * h;
+          if (!J.act[k] && !J.act[l]) continue;
+          const int p = J.p[k], q = J.q[k], pp = J.p[l], qq = J.q[l];
+          const float ck = J.c[k], sk = J.s[k], cl = J.c[l], sl = J.s[l];
+          const float a = A[p * NM + pp], b = A[p * NM + qq], c = A[q * NM + pp], d = A[q * NM + qq];
+          const float r1 = ck * a - sk * c, r2 = ck * b - sk * d, r3 = sk * a + ck * c, r4 = sk * b + ck * d;
+          float na = cl * r1 - sl * r2, nb = sl * r1 + cl * r2, nc = cl * r3 - sl * r4, nd = sl * r3 + cl * r4;
+          if (k == l) {
             const float t = J.t[k], apq = J.apq[k];
-            if (i == p) { nx = J.app[k] - t * apq; ny = 0.0f; }
-            else if (i == q) { nx = 0.0f; ny = J.aqq[k] + t * apq; }
+            na = J.app[k] - t * apq;
+            nb = 0.0f;
+            nc = 0.0f;
+            nd = J.aqq[k] + t * apq;
           }
-          Mx[i * NM + p] = nx;
-          Mx[i * NM + q] = ny;
+          A[p * NM + pp] = na;
+          A[p * NM + qq] = nb;
+          A[q * NM + pp] = nc;
+          A[q * NM + qq] = nd;
+        } else {
+          const int it2 = it - nblk;
+          const int i = it2 / h, l = it2 - i * h;
+          if (!J.act[l]) continue;
+          const int p = J.p[l], q = J.q[l];
+          const float c = J.c[l], sv = J.s[l];
+          const float x = V[i * NM + p], y = V[i * NM + q];
+          V[i * NM + p] = c * x - sv * y;
+          V[i * NM + q] = sv * x + c * y;
         }
       }
       __syncthreads();
