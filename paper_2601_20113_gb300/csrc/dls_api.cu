@@ -70,7 +70,7 @@ int make_plan(const dls_params* p, Plan* out) {
 struct Layout {
   size_t meta, vst, q, kc, offsets, vars, status, partial, total;
   // mixed-precision form
-  size_t staging, q_scr, k8_scr, k32_scr, feat, ranks, phase;
+  size_t staging, q_scr, k8_scr, k32_scr, bit_scr, feat, ranks, phase;
   int ctas;
   bool mixed;
 };
@@ -155,6 +155,7 @@ static Layout work_layout(const Plan& P) {
     L.q_scr = take(sizeof(int32_t) * (size_t)L.ctas * kMaxMixedN * (size_t)align_up(P.lmax, 4));
     L.k8_scr = take((size_t)L.ctas * (size_t)npt);
     L.k32_scr = take(sizeof(int32_t) * (size_t)L.ctas * (size_t)npt);
+    L.bit_scr = take(sizeof(uint32_t) * (size_t)L.ctas * (size_t)(align_up(npt, 32) / 32));
     L.feat = take(sizeof(float) * 32 * (size_t)nb1);
     L.ranks = take(sizeof(int32_t) * (size_t)nb1);
     L.phase = take(sizeof(unsigned long long) * (size_t)L.ctas * kMixedPhases);
@@ -274,6 +275,7 @@ static MixedWork mixed_work(const Plan& P, const Layout& L, void* ws) {
   mw.q_scr = (int32_t*)(b + L.q_scr);
   mw.k8_scr = (int8_t*)(b + L.k8_scr);
   mw.k32_scr = (int32_t*)(b + L.k32_scr);
+  mw.bit_scr = (uint32_t*)(b + L.bit_scr);
   mw.feat = (float*)(b + L.feat);
   mw.ranks = (int32_t*)(b + L.ranks);
   mw.lmax = align_up(P.lmax, 4);
@@ -510,6 +512,7 @@ int dls_block_features(const dls_params* p, const void* d_in, float* d_feat, int
   mw.meta = w.meta; mw.offsets = w.offsets; mw.vars = w.vars; mw.status = w.status;
   mw.staging = b + L.staging; mw.q_scr = (int32_t*)(b + L.q_scr); mw.k8_scr = (int8_t*)(b + L.k8_scr);
   mw.k32_scr = (int32_t*)(b + L.k32_scr); mw.feat = d_feat; mw.ranks = d_rank;
+  mw.bit_scr = (uint32_t*)(b + L.bit_scr);
   mw.lmax = align_up(P.lmax, 4); mw.nptmax = align_up((int64_t)P.nmax * P.lmax, 16); mw.ctas = L.ctas;
   mw.phase = (unsigned long long*)(b + L.phase);
   if ((st = launch_mixed_all(P, d_in, mw, kRankSearch, 2, s)) != DLS_OK) return st;

@@ -207,6 +207,7 @@ struct MixedWork {
   int32_t* q_scr;       // ctas x kMaxMixedN x lmax
   int8_t* k8_scr;       // ctas x nptmax
   int32_t* k32_scr;     // ctas x nptmax
+  uint32_t* bit_scr;    // ctas x nptmax / 32: nonzero-correction bitmap (full blocks)
   float* feat;          // nb x 32
   int32_t* ranks;       // nb
   int64_t lmax, nptmax;

@@ -51,6 +51,7 @@ struct TileArgs {
   int32_t* q_scr;
   int8_t* k8_scr;
   int32_t* k32_scr;
+  uint32_t* bit_scr;       // per CTA: nptmax / 32 words
   float* feat;
   int32_t* ranks;
   int64_t lmax, nptmax;
@@ -88,6 +89,7 @@ struct __align__(128) TileSmem {
   int r_pred;
   unsigned nexact;
   int warp_cnt[kWarps];
+  int sh32[32];
   int64_t colbase[NM + 1];
   unsigned long long ph[kPhases];   // cycle counters of this CTA (thread 0)
   JacPairs jp;
@@ -216,6 +218,13 @@ struct Maps {
   const CUtensorMap* gram;
 };
 constexpr int kLayoutRow = 0, kLayoutGram = 1;
+
+// True when the block is full and its chunk rows are its rows in order (row l of
+// chunk c is l = c rc + r), with rc and M multiples of 32: then every warp step
+// of the row-wise passes covers 32 consecutive rows from a multiple of 32.
+__device__ __forceinline__ bool bitmap_rows(const TileArgs& a, const Geom& g) {
+  return g.sx == a.bxb && g.sy == a.yc && g.sz % a.zc == 0 && (a.rc & 31) == 0 && (g.M & 31) == 0;
+}
 
 __device__ void issue_chunk(const TileArgs& a, const Maps& tm, TileSmem& S, const Geom& g, const Chunks& ch,
                             int c, uint32_t& iss, int layout) {
@@ -848,9 +857,13 @@ __device__ __forceinline__ void row_decode_step(const TileSmem& S, int k, float 
 template <int NF>
 __device__ __noinline__ bool pass_encode(const TileArgs& a, const Maps& tm, TileSmem& S, Cursor& cu, int64_t bi,
                             const Geom& g, int r, bool check, const RowConst& rcst, const CorrConst& cc, bool pointwise,
-                            int32_t* qs, int8_t* k8, int32_t* k32) {
+                            int32_t* qs, int8_t* k8, int32_t* k32, uint32_t* bits) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = NF ? NF : g.n;
+  // full blocks whose chunk rows are the block rows in order: each warp step
+  // covers 32 consecutive rows starting at a multiple of 32, so a ballot per
+  // column is one word of the nonzero-correction bitmap (element e -> bit e)
+  const bool use_bits = bitmap_rows(a, g);
   for (int i = tid; i < kWarps * NM; i += kTT) (&S.qor[0][0])[i] = 0u;
   if (tid == 0) { S.kmax = 0; S.ncorr = 0; S.nesc = 0; }
   __syncthreads();
@@ -896,38 +909,71 @@ __device__ __noinline__ bool pass_encode(const TileArgs& a, const Maps& tm, Tile
         for (int j = 0; j < NM; ++j) acc[j] = __fmaf_rn(chk, v[j], acc[j]);
       }
       if (valid) {
+        // corrections: every element decided first without branches (so they
+        // interleave); the few the FP32 evaluation leaves open take the FP64 path
+        int32_t kv[NM];
+        uint32_t unsure = 0;
 #pragma unroll
         for (int j = 0; j < NM; ++j) {
+          kv[j] = 0;
           if (j < n) {
             const float xj = xr[j * rc];
             if (check) { const float dd = __fsub_rn(xj, acc[j]); e2 = __fmaf_rn(dd, dd, e2); }
-            const int32_t kv = pointwise ? corr_exact(xj, acc[j], cc) : 0;
+            if (pointwise) {
+              bool u;
+              kv[j] = corr_fast(xj, acc[j], cc, &u);
+              unsure |= (u ? 1u : 0u) << j;
+            }
+          }
+        }
+        while (unsure) {
+          const int jj = __ffs(unsure) - 1;
+          unsure &= unsure - 1;
+          float aj = acc[0];
+#pragma unroll
+          for (int j = 1; j < NM; ++j) aj = (j == jj) ? acc[j] : aj;
+          const int32_t v = corr_slow(xr[jj * rc], aj, cc);
+#pragma unroll
+          for (int j = 0; j < NM; ++j) kv[j] = (j == jj) ? v : kv[j];
+        }
+#pragma unroll
+        for (int j = 0; j < NM; ++j) {
+          if (j < n) {
             const int e = j * M + l;
-            const bool big = kv < -127 || kv > 127;          // includes escapes
-            k8[e] = big ? (int8_t)-128 : (int8_t)kv;
-            if (big) k32[e] = kv;
-            const bool esc = kv == kEscape, corr = kv != 0 && !esc;
-            ne += esc ? 1 : 0;
-            nc += corr ? 1 : 0;
-            const uint32_t z = corr ? zigzag(kv) : 0u;
-            kmx = z > kmx ? z : kmx;
+            const int32_t k = kv[j];
+            const bool big = k < -127 || k > 127;            // includes escapes
+            k8[e] = big ? (int8_t)-128 : (int8_t)k;
+            if (big) k32[e] = k;
+            ne += k == kEscape ? 1 : 0;
+            nc += k != 0 ? 1 : 0;                             // escapes taken out below
+            kmx |= k == kEscape ? 0u : zigzag(k);             // OR: same bit width as the maximum
+          }
+        }
+        if (use_bits) {
+#pragma unroll
+          for (int j = 0; j < NM; ++j) {
+            if (j < n) {
+              const unsigned mk = __ballot_sync(FULL, kv[j] != 0 && kv[j] != kEscape);
+              if (lane == 0) bits[(j * M + l) >> 5] = mk;
+            }
           }
         }
       }
     }
   });
   if (!ok) return false;
+  nc -= ne;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     nc += __shfl_xor_sync(FULL, nc, o);
     ne += __shfl_xor_sync(FULL, ne, o);
-    kmx = max(kmx, __shfl_xor_sync(FULL, kmx, o));
+    kmx |= __shfl_xor_sync(FULL, kmx, o);
     ovf |= __shfl_xor_sync(FULL, ovf, o);
   }
   if (lane == 0) {
     if (nc) atomicAdd(&S.ncorr, nc);
     if (ne) atomicAdd(&S.nesc, ne);
-    if (kmx) atomicMax(&S.kmax, (int)kmx);
+    if (kmx) atomicOr(reinterpret_cast<unsigned int*>(&S.kmax), kmx);
     if (ovf) S.ovf = 1;
   }
   __syncthreads();
@@ -1161,7 +1207,7 @@ __device__ __forceinline__ void flush32(uint64_t& acc, int& nbits, uint32_t* dst
 }
 
 __device__ __noinline__ void write_record(const TileArgs& a, TileSmem& S, const Geom& g, int64_t bi, bool raw, int r,
-                             int32_t* qs, const int8_t* k8, const int32_t* k32) {
+                             int32_t* qs, const int8_t* k8, const int32_t* k32, const uint32_t* bits) {
   const int tid = threadIdx.x;
   const int n = g.n;
   const int64_t L = g.L, N = g.N, M = g.M;
@@ -1333,11 +1379,33 @@ __device__ __noinline__ void write_record(const TileArgs& a, TileSmem& S, const 
       // entry list (element indices) into the q scratch, then 32 entries of
       // ib + wk bits per task -> exactly ib + wk words
       uint32_t* list = reinterpret_cast<uint32_t*>(qs);
-      compact16(
-          S, k8, (int)N, [&](int8_t b, int e) { return b != 0 && (b != (int8_t)-128 || k32[e] != kEscape); },
-          [&](int e, int idx) {
-            if (idx < m.ncorr) list[idx] = (uint32_t)e;   // the count and the bytes agree by construction
-          });
+      if (bitmap_rows(a, g)) {
+        // entry list from the bitmap the encode pass wrote: contiguous word
+        // ranges per thread, an exclusive scan of their counts, then the bits
+        const int nw = (int)(N / 32);
+        const int per = (nw + kTT - 1) / kTT;
+        const int w0 = tid * per, w1 = (w0 + per) < nw ? (w0 + per) : nw;
+        int cnt = 0;
+        for (int w = w0; w < w1; ++w) cnt += __popc(bits[w]);
+        int tot;
+        int idx = block_excl_scan(cnt, S.sh32, &tot);
+        for (int w = w0; w < w1; ++w) {
+          uint32_t mk = bits[w];
+          while (mk) {
+            const int b = __ffs(mk) - 1;
+            mk &= mk - 1;
+            if (idx < m.ncorr) list[idx] = (uint32_t)(w * 32 + b);   // the count and the bits agree
+            ++idx;
+          }
+        }
+        __syncthreads();
+      } else {
+        compact16(
+            S, k8, (int)N, [&](int8_t b, int e) { return b != 0 && (b != (int8_t)-128 || k32[e] != kEscape); },
+            [&](int e, int idx) {
+              if (idx < m.ncorr) list[idx] = (uint32_t)e;   // the count and the bytes agree by construction
+            });
+      }
       const int ib = m.ib, wk = m.wk, W = ib + wk;
       const int64_t nc = m.ncorr;
       for (int64_t task = tid; task < cdiv(nc, 32); task += kTT) {
@@ -1407,6 +1475,7 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
   int32_t* qs = a.q_scr + (int64_t)blockIdx.x * NM * a.lmax;
   int8_t* k8 = a.k8_scr + (int64_t)blockIdx.x * a.nptmax;
   int32_t* k32 = a.k32_scr + (int64_t)blockIdx.x * a.nptmax;
+  uint32_t* bits = a.bit_scr + (int64_t)blockIdx.x * (align_up(a.nptmax, 32) / 32);
   const Plan& P = a.P;
   // tensor-core Gram: the lo buffer follows the shared struct (1024-aligned)
   float* lobuf = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(&S) +
@@ -1578,8 +1647,8 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
     int r = 0;
     if (a.learned != kRankSearch && !may_overflow) {
       const int rp = S.r_pred;
-      if (!(full ? pass_encode<NM>(a, tm, S, cu, bi, g, rp, true, rcst, cc, pointwise, qs, k8, k32)
-                 : pass_encode<0>(a, tm, S, cu, bi, g, rp, true, rcst, cc, pointwise, qs, k8, k32)))
+      if (!(full ? pass_encode<NM>(a, tm, S, cu, bi, g, rp, true, rcst, cc, pointwise, qs, k8, k32, bits)
+                 : pass_encode<0>(a, tm, S, cu, bi, g, rp, true, rcst, cc, pointwise, qs, k8, k32, bits)))
         break;
       mark(kPhEncode);
       const double E_rm1 = S.Ered[0], E_r = S.Ered[1];
@@ -1615,8 +1684,8 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
         }
         r = lo;
         if (!pointwise && !decide_pass(a, S, g, r, Eall[r], bnd, el2, rcst)) raw = true;
-        if (!raw && !(full ? pass_encode<NM>(a, tm, S, cu, bi, g, r, false, rcst, cc, pointwise, qs, k8, k32)
-                           : pass_encode<0>(a, tm, S, cu, bi, g, r, false, rcst, cc, pointwise, qs, k8, k32)))
+        if (!raw && !(full ? pass_encode<NM>(a, tm, S, cu, bi, g, r, false, rcst, cc, pointwise, qs, k8, k32, bits)
+                           : pass_encode<0>(a, tm, S, cu, bi, g, r, false, rcst, cc, pointwise, qs, k8, k32, bits)))
           break;
       }
       mark(kPhSearch);
@@ -1626,7 +1695,7 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
       const int64_t bn = S.bnext;
       if (bn < P.nb) prefetch(a, tm, S, cu, bn, block_geom(P, P.b0 + bn), TC ? kLayoutGram : kLayoutRow);
     }
-    write_record(a, S, g, bi, raw, r, qs, k8, k32);
+    write_record(a, S, g, bi, raw, r, qs, k8, k32, bits);
     mark(kPhPack);
     if (tid == 0) S.ph[accepted ? kCntAccepted : kCntSearched] += 1;
   }
@@ -1745,6 +1814,7 @@ int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, in
   a.q_scr = w.q_scr;
   a.k8_scr = w.k8_scr;
   a.k32_scr = w.k32_scr;
+  a.bit_scr = w.bit_scr;
   a.feat = w.feat;
   a.ranks = w.ranks;
   a.lmax = w.lmax;

@@ -63,6 +63,8 @@ __host__ __device__ inline CorrConst make_corr_const(double eb, double step, boo
 static __device__ __noinline__ int32_t corr_slow(float x, float xh, const CorrConst& cc);
 __device__ __forceinline__ int32_t corr_exact(float x, float xh, const CorrConst& cc) {
   const float R = __fsub_rn(x, xh);
+  // |fl(x - xhat)| < eb (1 - 1e-6), rounded down, proves |x - xhat| < eb: k = 0, in bound
+  if (fabsf(R) < cc.eb_lo_f) return 0;
   const float y = __fmul_rn(R, cc.inv_step_f);
   const float ay = fabsf(y);
   const float m = __fmul_rn(ay, 5.0e-7f) + 1.0e-30f;
@@ -78,6 +80,21 @@ __device__ __forceinline__ int32_t corr_exact(float x, float xh, const CorrConst
   if (d <= cc.eb_lo_f) return (int32_t)r;
   if (d >= cc.eb_hi_f) return kEscape;
   return corr_slow(x, xh, cc);
+}
+// The same decision without branches, for loops that decide many elements:
+// returns k when the FP32 evaluation settles it, and sets *unsure otherwise
+// (the caller then takes corr_slow, which decides with the FP64 definition).
+__device__ __forceinline__ int32_t corr_fast(float x, float xh, const CorrConst& cc, bool* unsure) {
+  const float R = __fsub_rn(x, xh);
+  const bool zero = fabsf(R) < cc.eb_lo_f;           // |x - xhat| < eb certainly
+  const float y = __fmul_rn(R, cc.inv_step_f);
+  const float m = __fmul_rn(fabsf(y), 5.0e-7f) + 1.0e-30f;
+  const float r = rintf(y);
+  const bool clear = fabsf(__fsub_rn(y, r)) < 0.5f - m && fabsf(r) <= 1048576.0f;
+  const float d = fabsf(__fsub_rn(x, __fmaf_rn(r, cc.step_f, xh)));
+  const bool in = d <= cc.eb_lo_f, out = d >= cc.eb_hi_f;
+  *unsure = !zero && !(clear && (in || out));
+  return zero ? 0 : (out ? kEscape : (int32_t)r);
 }
 static __device__ __noinline__ int32_t corr_slow(float x, float xh, const CorrConst& cc) {
   const float R = __fsub_rn(x, xh);
