@@ -89,6 +89,7 @@ struct __align__(128) TileSmem {
   int r_pred;
   unsigned nexact;
   int warp_cnt[kWarps];
+  int prev_n;                     // order of the basis left in VstT by the previous block (0: none)
   int sh32[32];
   int64_t colbase[NM + 1];
   unsigned long long ph[kPhases];   // cycle counters of this CTA (thread 0)
@@ -641,6 +642,51 @@ __device__ __noinline__ bool pass_gram_tc(const TileArgs& a, const Maps& tm, Til
   __syncthreads();
   derived_stats(a, S, g, n);
   return true;
+}
+
+// ---------------------------------------------------------------- warm start
+// G32 <- P^T G32 P with P = the previous block's stored basis (P[j][k] =
+// VstT[k][j], orthonormal to FP32 accuracy), in FP32.  All threads.
+__device__ void warm_rotate(TileSmem& S, int n) {
+  float* T = &S.red[0][0];                  // 256 floats of scratch
+  const int tid = threadIdx.x;
+  for (int e = tid; e < NM * NM; e += kTT) {
+    const int i = e / NM, j = e % NM;
+    float v = 0.0f;
+    if (i < n && j < n)
+      for (int k = 0; k < n; ++k) v = __fmaf_rn(S.G32[i * NM + k], S.VstT[j * NM + k], v);
+    T[e] = v;                                // (G P)[i][j]
+  }
+  __syncthreads();
+  for (int e = tid; e < NM * NM; e += kTT) {
+    const int i = e / NM, j = e % NM;
+    if (i < n && j < n && i <= j) {
+      float v = 0.0f;
+      for (int k = 0; k < n; ++k) v = __fmaf_rn(S.VstT[i * NM + k], T[k * NM + j], v);
+      S.G32[i * NM + j] = v;
+      S.G32[j * NM + i] = v;
+    }
+  }
+  __syncthreads();
+}
+
+// Vj <- P Vj (the eigenvectors of P^T G P back in the block's coordinates).
+__device__ void warm_back(TileSmem& S, int n) {
+  float* T = &S.red[0][0];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < NM * NM; e += kTT) {
+    const int i = e / NM, j = e % NM;
+    float v = 0.0f;
+    if (i < n && j < n)
+      for (int k = 0; k < n; ++k) v = __fmaf_rn(S.VstT[k * NM + i], S.Vj[k * NM + j], v);
+    T[e] = v;
+  }
+  __syncthreads();
+  for (int e = tid; e < NM * NM; e += kTT) {
+    const int i = e / NM, j = e % NM;
+    if (i < n && j < n) S.Vj[e] = T[e];
+  }
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------- FP64 refinement
@@ -1489,6 +1535,7 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     S.nexact = 0;
+    S.prev_n = 0;
     S.abort_flag = 0;
   }
   if (TC) {
@@ -1564,10 +1611,17 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
     // rotations below 5% of the per-mode budget eb^2 L change no decision
     // worth a sweep; the decisions themselves stay exact
     const float jfloor = (float)(a.jfloor * (P.eb_type == DLS_EB_NRMSE ? el2 / n : vi.eb * vi.eb * (double)g.L));
+    // warm start from the CTA's previous basis P (same order n): Jacobi on
+    // P^T G P, then V = P W; blocks of one field share much of their temporal
+    // structure, so few sweeps remain
+    const bool warm = S.prev_n == n && n > 1;
+    if (warm) warm_rotate(S, n);
     jacobi_cta<kTT>(S.G32, S.Vj, S.lam_t, n, jfloor, S.jp);
+    if (warm) warm_back(S, n);
     mark(kPhJacobi);
     refine64(S, n);
     if (warp == 0) order_basis(S, n, lane);
+    if (tid == 0) S.prev_n = n;
     __syncthreads();
     mark(kPhRefine);
     // Tight bounds need the modes an FP32 Gram cannot resolve (eigenvalues near
