@@ -221,10 +221,13 @@ struct Maps {
 constexpr int kLayoutRow = 0, kLayoutGram = 1;
 
 // True when the block is full and its chunk rows are its rows in order (row l of
-// chunk c is l = c rc + r), with rc and M multiples of 32: then every warp step
-// of the row-wise passes covers 32 consecutive rows from a multiple of 32.
+// chunk c is l = c rc + r: whole x lines, y chunks that tile the block's y
+// extent, whole planes when a chunk holds several), with rc and M multiples of
+// 32: then every warp step of the row-wise passes covers 32 consecutive rows
+// from a multiple of 32.
 __device__ __forceinline__ bool bitmap_rows(const TileArgs& a, const Geom& g) {
-  return g.sx == a.bxb && g.sy == a.yc && g.sz % a.zc == 0 && (a.rc & 31) == 0 && (g.M & 31) == 0;
+  const bool ylines = a.zc == 1 ? g.sy % a.yc == 0 : g.sy == a.yc;
+  return g.sx == a.bxb && ylines && g.sz % a.zc == 0 && (a.rc & 31) == 0 && (g.M & 31) == 0;
 }
 
 __device__ void issue_chunk(const TileArgs& a, const Maps& tm, TileSmem& S, const Geom& g, const Chunks& ch,
