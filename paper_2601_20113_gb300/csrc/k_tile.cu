@@ -89,7 +89,6 @@ struct __align__(128) TileSmem {
   int r_pred;
   unsigned nexact;
   int warp_cnt[kWarps];
-  int prev_n;                     // order of the basis left in VstT by the previous block (0: none)
   int sh32[32];
   int64_t colbase[NM + 1];
   unsigned long long ph[kPhases];   // cycle counters of this CTA (thread 0)
@@ -398,15 +397,23 @@ __device__ __noinline__ bool pass_gram(const TileArgs& a, const Maps& tm, TileSm
 #pragma unroll
   for (int p = 0; p < kHalf; ++p) acc[p] = 0.0f;
   float mn = INFINITY, mx = -INFINITY, xg = 0.0f;
+  // full blocks whose chunk rows are the block rows: every row is valid and
+  // its x is r mod the block width
+  const bool lin = bitmap_rows(a, g);
+  const int rc = a.rc, bxb = a.bxb, sx = g.sx;
+  const uint32_t mbx = a.mbx;
   const bool ok = stream_block(a, tm, S, cu, bi, g, kLayoutRow, [&](int c, const Chunks& ch, const float* tile) {
     int ii = 0;
-    for (int r = gt; r < a.rc; r += kGT, ++ii) {
+    for (int r = gt; r < rc; r += kGT, ++ii) {
       int xx;
-      const int l = row_index(a, g, ch, c, r, &xx);
-      if (l < 0) continue;
+      if (lin) {
+        xx = r - fdiv(r, mbx) * bxb;
+      } else if (row_index(a, g, ch, c, r, &xx) < 0) {
+        continue;
+      }
       float x[NM];
 #pragma unroll
-      for (int j = 0; j < NM; ++j) x[j] = j < n ? tile[j * a.rc + r] : 0.0f;
+      for (int j = 0; j < NM; ++j) x[j] = j < n ? tile[j * rc + r] : 0.0f;
       if (PROJECT) {
         const float a0 = x[0];
         float cc[NM];
@@ -434,10 +441,10 @@ __device__ __noinline__ bool pass_gram(const TileArgs& a, const Maps& tm, TileSm
             mx = fmaxf(mx, x[j]);
           }
         }
-        if (xx + 1 < g.sx) {
+        if (xx + 1 < sx) {
 #pragma unroll
           for (int j = 0; j < NM; ++j)
-            if (j < n) { const float d = tile[j * a.rc + r + 1] - x[j]; xg = __fmaf_rn(d, d, xg); }
+            if (j < n) { const float d = tile[j * rc + r + 1] - x[j]; xg = __fmaf_rn(d, d, xg); }
         }
       }
       if (grp == 0) {
@@ -645,51 +652,6 @@ __device__ __noinline__ bool pass_gram_tc(const TileArgs& a, const Maps& tm, Til
   __syncthreads();
   derived_stats(a, S, g, n);
   return true;
-}
-
-// ---------------------------------------------------------------- warm start
-// G32 <- P^T G32 P with P = the previous block's stored basis (P[j][k] =
-// VstT[k][j], orthonormal to FP32 accuracy), in FP32.  All threads.
-__device__ void warm_rotate(TileSmem& S, int n) {
-  float* T = &S.red[0][0];                  // 256 floats of scratch
-  const int tid = threadIdx.x;
-  for (int e = tid; e < NM * NM; e += kTT) {
-    const int i = e / NM, j = e % NM;
-    float v = 0.0f;
-    if (i < n && j < n)
-      for (int k = 0; k < n; ++k) v = __fmaf_rn(S.G32[i * NM + k], S.VstT[j * NM + k], v);
-    T[e] = v;                                // (G P)[i][j]
-  }
-  __syncthreads();
-  for (int e = tid; e < NM * NM; e += kTT) {
-    const int i = e / NM, j = e % NM;
-    if (i < n && j < n && i <= j) {
-      float v = 0.0f;
-      for (int k = 0; k < n; ++k) v = __fmaf_rn(S.VstT[i * NM + k], T[k * NM + j], v);
-      S.G32[i * NM + j] = v;
-      S.G32[j * NM + i] = v;
-    }
-  }
-  __syncthreads();
-}
-
-// Vj <- P Vj (the eigenvectors of P^T G P back in the block's coordinates).
-__device__ void warm_back(TileSmem& S, int n) {
-  float* T = &S.red[0][0];
-  const int tid = threadIdx.x;
-  for (int e = tid; e < NM * NM; e += kTT) {
-    const int i = e / NM, j = e % NM;
-    float v = 0.0f;
-    if (i < n && j < n)
-      for (int k = 0; k < n; ++k) v = __fmaf_rn(S.VstT[k * NM + i], S.Vj[k * NM + j], v);
-    T[e] = v;
-  }
-  __syncthreads();
-  for (int e = tid; e < NM * NM; e += kTT) {
-    const int i = e / NM, j = e % NM;
-    if (i < n && j < n) S.Vj[e] = T[e];
-  }
-  __syncthreads();
 }
 
 // ---------------------------------------------------------------- FP64 refinement
@@ -903,7 +865,11 @@ __device__ __forceinline__ void row_decode_step(const TileSmem& S, int k, float 
 // unrolled (r is small), and each basis row is read once per column for both
 // the projection and the decode step.  Column widths: OR of zigzag(q) over
 // the warp (same bit width as the maximum) into S.qor.
-template <int NF>
+// SPARSE (pointwise bound, bitmap rows): k8 is written only for the elements
+// whose correction may be nonzero, and the record reads k8 through the
+// nonzero-correction bitmap; escapes cannot be listed from such a k8, so a
+// block that has any is encoded again without SPARSE.
+template <int NF, bool SPARSE>
 __device__ __noinline__ bool pass_encode(const TileArgs& a, const Maps& tm, TileSmem& S, Cursor& cu, int64_t bi,
                             const Geom& g, int r, bool check, const RowConst& rcst, const CorrConst& cc, bool pointwise,
                             int32_t* qs, int8_t* k8, int32_t* k32, uint32_t* bits) {
@@ -913,6 +879,9 @@ __device__ __noinline__ bool pass_encode(const TileArgs& a, const Maps& tm, Tile
   // covers 32 consecutive rows starting at a multiple of 32, so a ballot per
   // column is one word of the nonzero-correction bitmap (element e -> bit e)
   const bool use_bits = bitmap_rows(a, g);
+  // the constants by value: the loop's stores cannot be assumed not to alias them
+  const RowConst rq = rcst;
+  const CorrConst cq = cc;
   for (int i = tid; i < kWarps * NM; i += kTT) (&S.qor[0][0])[i] = 0u;
   if (tid == 0) { S.kmax = 0; S.ncorr = 0; S.nesc = 0; }
   __syncthreads();
@@ -924,7 +893,7 @@ __device__ __noinline__ bool pass_encode(const TileArgs& a, const Maps& tm, Tile
     for (int rb = 0; rb < rc; rb += kTT) {          // same trip count in every lane
       const int rr = rb + tid;
       int xx = 0;
-      const int l = rr < rc ? row_index(a, g, ch, c, rr, &xx) : -1;
+      const int l = rr < rc ? (use_bits ? c * rc + rr : row_index(a, g, ch, c, rr, &xx)) : -1;
       const bool valid = l >= 0;
       const float* xr = tile + (valid ? rr : 0);
       const float a0 = valid ? xr[0] : 0.0f;
@@ -944,11 +913,11 @@ __device__ __noinline__ bool pass_encode(const TileArgs& a, const Maps& tm, Tile
           v[4 * j4 + 0] = t.x; v[4 * j4 + 1] = t.y; v[4 * j4 + 2] = t.z; v[4 * j4 + 3] = t.w;
         }
         const float cf = project(d, v, a0, S.vsum[k], n);
-        const int32_t q = quant_exact(cf, rcst.delta, rcst.inv_delta, ovf);
+        const int32_t q = quant_exact(cf, rq.delta, rq.inv_delta, ovf);
         if (valid) qs[k * Lq + l] = q;
         const uint32_t wor = __reduce_or_sync(FULL, valid ? zigzag(q) : 0u);
         if (lane == 0) S.qor[warp][k] |= wor;
-        const float chk = __fmul_rn(__int2float_rn(q), rcst.delta_f);
+        const float chk = __fmul_rn(__int2float_rn(q), rq.delta_f);
         if (check && k == r - 1 && valid) {
 #pragma unroll
           for (int j = 0; j < NM; ++j)
@@ -957,7 +926,46 @@ __device__ __noinline__ bool pass_encode(const TileArgs& a, const Maps& tm, Tile
 #pragma unroll
         for (int j = 0; j < NM; ++j) acc[j] = __fmaf_rn(chk, v[j], acc[j]);
       }
-      if (valid) {
+      if (SPARSE && valid) {
+        // elements with |fl(x - xhat)| < eb (rounded down) need no correction
+        // (the first test of the decision); the others are decided one by one
+        uint32_t cand = 0;
+#pragma unroll
+        for (int j = 0; j < NM; ++j) {
+          if (j < n) {
+            const float R = __fsub_rn(xr[j * rc], acc[j]);
+            if (check) e2 = __fmaf_rn(R, R, e2);
+            cand |= (fabsf(R) < cq.eb_lo_f ? 0u : 1u) << j;
+          }
+        }
+        uint32_t nzb = 0;
+        while (cand) {
+          const int jj = __ffs(cand) - 1;
+          cand &= cand - 1;
+          float aj = acc[0];
+#pragma unroll
+          for (int j = 1; j < NM; ++j) aj = (j == jj) ? acc[j] : aj;
+          const float xj = xr[jj * rc];
+          bool u;
+          int32_t k = corr_fast(xj, aj, cq, &u);
+          if (u) k = corr_slow(xj, aj, cq);
+          const int e = jj * M + l;
+          const bool big = k < -127 || k > 127;            // includes escapes
+          k8[e] = big ? (int8_t)-128 : (int8_t)k;
+          if (big) k32[e] = k;
+          ne += k == kEscape ? 1 : 0;
+          nc += k != 0 ? 1 : 0;
+          kmx |= k == kEscape ? 0u : zigzag(k);
+          nzb |= (k != 0 && k != kEscape ? 1u : 0u) << jj;
+        }
+#pragma unroll
+        for (int j = 0; j < NM; ++j) {
+          if (j < n) {
+            const unsigned mk = __ballot_sync(FULL, (nzb >> j) & 1u);
+            if (lane == 0) bits[(j * M + l) >> 5] = mk;
+          }
+        }
+      } else if (valid) {
         // corrections: every element decided first without branches (so they
         // interleave); the few the FP32 evaluation leaves open take the FP64 path
         int32_t kv[NM];
@@ -970,7 +978,7 @@ __device__ __noinline__ bool pass_encode(const TileArgs& a, const Maps& tm, Tile
             if (check) { const float dd = __fsub_rn(xj, acc[j]); e2 = __fmaf_rn(dd, dd, e2); }
             if (pointwise) {
               bool u;
-              kv[j] = corr_fast(xj, acc[j], cc, &u);
+              kv[j] = corr_fast(xj, acc[j], cq, &u);
               unsure |= (u ? 1u : 0u) << j;
             }
           }
@@ -981,7 +989,7 @@ __device__ __noinline__ bool pass_encode(const TileArgs& a, const Maps& tm, Tile
           float aj = acc[0];
 #pragma unroll
           for (int j = 1; j < NM; ++j) aj = (j == jj) ? acc[j] : aj;
-          const int32_t v = corr_slow(xr[jj * rc], aj, cc);
+          const int32_t v = corr_slow(xr[jj * rc], aj, cq);
 #pragma unroll
           for (int j = 0; j < NM; ++j) kv[j] = (j == jj) ? v : kv[j];
         }
@@ -1395,10 +1403,13 @@ __device__ __noinline__ void write_record(const TileArgs& a, TileSmem& S, const 
     if (lay.dense) {
       const int wk = m.wk;
       const int64_t runs = cdiv(N, 32);
+      // bitmap rows: k8 may hold stale bytes where the bitmap has no bit
+      const bool masked = bitmap_rows(a, g);
       for (int64_t task = tid; task < runs; task += kTT) {
         const int64_t first = task * 32;
         const int cnt = (int)((N - first) < 32 ? (N - first) : 32);
         uint32_t* dst = cw + task * wk;
+        const uint32_t bw = masked ? bits[task] : 0xFFFFFFFFu;
         int8_t kb[32];
         if (cnt == 32) {
           const uint4* kv4 = reinterpret_cast<const uint4*>(k8 + first);
@@ -1415,7 +1426,7 @@ __device__ __noinline__ void write_record(const TileArgs& a, TileSmem& S, const 
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           if (i < cnt) {
-            int32_t kv = kb[i];
+            int32_t kv = (bw >> i) & 1u ? kb[i] : 0;
             if (kv == -128) kv = k32[first + i];
             acc |= (uint64_t)(kv == kEscape ? 0u : zigzag(kv)) << nbits;
             nbits += wk;
@@ -1511,10 +1522,18 @@ __device__ __noinline__ void write_record(const TileArgs& a, TileSmem& S, const 
 }
 
 // ---------------------------------------------------------------- the kernel
+// The eigensolver out of line: inline, it would share the kernel's registers
+// with the block state the body keeps live across it.
+__device__ __noinline__ void jacobi_tile(TileSmem& S, int n, float jfloor) {
+  jacobi_cta<kTT>(S.G32, S.Vj, S.lam_t, n, jfloor, S.jp);
+}
+
 // TC: the tensor-core Gram (its instantiation alone contains tcgen05 code).
+// The arguments stay in parameter space (the passes take their address).
 template <int MINB, bool TC>
 __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUtensorMap tmap,
-                                                    const __grid_constant__ CUtensorMap tmapg, const TileArgs a) {
+                                                    const __grid_constant__ CUtensorMap tmapg,
+                                                    const __grid_constant__ TileArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // TMA destinations: align the tile ring to 1024 bytes explicitly
   const uint32_t sbase = smem_u32(smem_raw);
@@ -1538,7 +1557,6 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     S.nexact = 0;
-    S.prev_n = 0;
     S.abort_flag = 0;
   }
   if (TC) {
@@ -1614,17 +1632,12 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
     // rotations below 5% of the per-mode budget eb^2 L change no decision
     // worth a sweep; the decisions themselves stay exact
     const float jfloor = (float)(a.jfloor * (P.eb_type == DLS_EB_NRMSE ? el2 / n : vi.eb * vi.eb * (double)g.L));
-    // warm start from the CTA's previous basis P (same order n): Jacobi on
-    // P^T G P, then V = P W; blocks of one field share much of their temporal
-    // structure, so few sweeps remain
-    const bool warm = S.prev_n == n && n > 1;
-    if (warm) warm_rotate(S, n);
-    jacobi_cta<kTT>(S.G32, S.Vj, S.lam_t, n, jfloor, S.jp);
-    if (warm) warm_back(S, n);
+    // the eigensolve starts from the identity: its result depends on this
+    // block's Gram alone, whichever blocks the CTA took before
+    jacobi_tile(S, n, jfloor);
     mark(kPhJacobi);
     refine64(S, n);
     if (warp == 0) order_basis(S, n, lane);
-    if (tid == 0) S.prev_n = n;
     __syncthreads();
     mark(kPhRefine);
     // Tight bounds need the modes an FP32 Gram cannot resolve (eigenvalues near
@@ -1638,7 +1651,7 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
       if (n > 1 && 4.0 * 5.9604644775390625e-8 * tr > 0.5 * noise) {
         if (!(full ? pass_gram<true, NM>(a, tm, S, cu, bi, g) : pass_gram<true, 0>(a, tm, S, cu, bi, g))) break;
         prefetch(a, tm, S, cu, bi, g, kLayoutRow);
-        jacobi_cta<kTT>(S.G32, S.Vj, S.lam_t, n, jfloor, S.jp);
+        jacobi_tile(S, n, jfloor);
         // V = Vst W in FP64; eigenvalues from the Rayleigh-Ritz diagonal
         for (int e = tid; e < NM * NM; e += kTT) {
           const int i = e / NM, j = e % NM;
@@ -1697,6 +1710,16 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
     __syncthreads();
     mark(kPhPredict);
 
+    // the encode pass at rank rr; SPARSE where the bitmap carries the corrections
+    const bool sparse = pointwise && bitmap_rows(a, g);
+    auto encode = [&](int rr, bool check, bool sp) -> bool {
+      if (sp) {
+        return full ? pass_encode<NM, true>(a, tm, S, cu, bi, g, rr, check, rcst, cc, pointwise, qs, k8, k32, bits)
+                    : pass_encode<0, true>(a, tm, S, cu, bi, g, rr, check, rcst, cc, pointwise, qs, k8, k32, bits);
+      }
+      return full ? pass_encode<NM, false>(a, tm, S, cu, bi, g, rr, check, rcst, cc, pointwise, qs, k8, k32, bits)
+                  : pass_encode<0, false>(a, tm, S, cu, bi, g, rr, check, rcst, cc, pointwise, qs, k8, k32, bits);
+    };
     const Chunks chk = chunks_of(a, g);
     const int64_t rows_per_thread = cdiv(a.rc, kTT) * chk.n;
     const double bnd = (double)(rows_per_thread * n + 40) * 6.6e-8;
@@ -1704,9 +1727,7 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
     int r = 0;
     if (a.learned != kRankSearch && !may_overflow) {
       const int rp = S.r_pred;
-      if (!(full ? pass_encode<NM>(a, tm, S, cu, bi, g, rp, true, rcst, cc, pointwise, qs, k8, k32, bits)
-                 : pass_encode<0>(a, tm, S, cu, bi, g, rp, true, rcst, cc, pointwise, qs, k8, k32, bits)))
-        break;
+      if (!encode(rp, true, sparse)) break;
       mark(kPhEncode);
       const double E_rm1 = S.Ered[0], E_r = S.Ered[1];
       if (!S.ovf) {
@@ -1741,12 +1762,13 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
         }
         r = lo;
         if (!pointwise && !decide_pass(a, S, g, r, Eall[r], bnd, el2, rcst)) raw = true;
-        if (!raw && !(full ? pass_encode<NM>(a, tm, S, cu, bi, g, r, false, rcst, cc, pointwise, qs, k8, k32, bits)
-                           : pass_encode<0>(a, tm, S, cu, bi, g, r, false, rcst, cc, pointwise, qs, k8, k32, bits)))
-          break;
+        if (!raw && !encode(r, false, sparse)) break;
       }
       mark(kPhSearch);
     }
+    // escapes are listed from k8 itself: a block that has any is encoded
+    // again with every element written
+    if (!raw && sparse && S.nesc > 0 && !encode(r, false, false)) break;
     // the next block's first chunks load while this record is packed
     {
       const int64_t bn = S.bnext;

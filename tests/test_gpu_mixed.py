@@ -218,3 +218,50 @@ def test_mixed_chunk_shapes(dims, block):
     ref, comp, rec, fd, _ = _mixed_vs_oracle(f, dims, block, eb, rank_mode=dls.RANK_TAIL)
     assert (rec.double() - fd.double()).abs().max().item() <= eb
     assert abs((f.nbytes / comp.numel()) / (f.nbytes / ref.size) - 1) <= 0.01
+
+
+def _record_escapes(comp):
+    """Escape count of every record (record header word 2)."""
+    s = comp.cpu().numpy()
+    b0, b1, offp, payp = (int(s[o:o + 8].view(np.uint64)[0]) for o in (72, 80, 104, 112))
+    offs = s[offp:offp + 8 * (b1 - b0 + 1)].view(np.uint64)
+    return [int(s[payp + int(o) + 8:payp + int(o) + 12].view(np.uint32)[0]) for o in offs[:-1]]
+
+
+@pytest.mark.parametrize("rank_mode", [dls.RANK_SEARCH, dls.RANK_TAIL])
+def test_mixed_escapes_on_full_blocks(rank_mode):
+    """A correction beyond 2^20 steps is stored as an escape (raw value).  Full
+    16^3 x 16 blocks write their corrections through the nonzero-correction
+    bitmap; a block with escapes is encoded again with every element written,
+    and its stream must decode within the bound, identically on both decoders."""
+    dims = (32, 32, 16, 16)
+    f = synth.modes3d(*dims, seed=7, count=16)
+    # two spikes in block 0 at different time steps: a rank-1 basis keeps the
+    # larger, and the other one's residual (5e3 / 2e-3 steps) must escape
+    # (at rank 1 every element is corrected, and a few corrected values land
+    # beyond eb by rounding: those escape too, in every block, as in the oracle)
+    f[0, 3, 2, 5, 7] = 1.0e4
+    f[0, 9, 4, 11, 13] = 5.0e3
+    eb = 1e-3
+    fd = f.cuda()
+    comp = dls.compress(fd, block=(16, 16, 16, 16), eb=eb, rank_cap=1, precision=dls.PREC_FP32,
+                        rank_mode=rank_mode)
+    esc = _record_escapes(comp)
+    assert esc[0] >= 1, esc
+    rec = dls.decompress(comp)
+    assert (rec.double() - fd.double()).abs().max().item() <= eb
+    # an escape stores the raw value: the spike comes back exactly
+    assert rec[0, 9, 4, 11, 13].item() == 5.0e3
+    st, rref = oracle.decompress(comp.cpu().numpy())
+    assert st == oracle.OK
+    assert np.array_equal(rref.astype(np.float32), rec.cpu().numpy())
+
+
+def test_mixed_stream_is_deterministic():
+    """More blocks than resident CTAs: each CTA takes several blocks in an order
+    that changes from run to run; every stored byte depends on the block alone."""
+    f = synth.modes3d(128, 128, 128, 32, seed=9, count=48, device="cuda")
+    eb = 1e-3 * float(f.max() - f.min())
+    runs = [dls.compress(f, block=(16, 16, 16, 16), eb=eb, rank_cap=16, precision=dls.PREC_FP32,
+                         rank_mode=dls.RANK_TAIL).cpu().numpy() for _ in range(3)]
+    assert all(r.size == runs[0].size and np.array_equal(r, runs[0]) for r in runs[1:])
