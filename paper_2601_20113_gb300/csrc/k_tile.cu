@@ -33,6 +33,7 @@ constexpr int kStages = 2;
 constexpr int kStageFloats = 4096;        // 16 KiB per stage
 constexpr int kNP = NM * (NM + 1) / 2;    // packed Gram pairs (136)
 constexpr int kHalf = kNP / 2;            // pairs per thread group (68)
+constexpr int kBitsSmem = 8 * NM * NM;    // bitmap words kept in shared memory (2048)
 constexpr int kGT = kTT / 2;              // threads per Gram group
 constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t kWaitLimit = 1u << 22;
@@ -73,7 +74,14 @@ struct __align__(128) TileSmem {
   float Vj[NM * NM];
   __align__(16) float VstT[NM * NM];     // VstT[k * NM + j] = Vst[j][k]
   float vsum[NM];
-  double G64[NM * NM], X64[NM * NM], R64[NM * NM], T64[NM * NM];
+  // FP64 eigen scratch; from the encode pass through the record it holds the
+  // nonzero-correction bitmap of blocks of up to kBitsSmem * 32 points
+  union {
+    struct {
+      double G64[NM * NM], X64[NM * NM], R64[NM * NM], T64[NM * NM];
+    };
+    uint32_t bitsm[8 * NM * NM];
+  };
   double lam_t[NM], lam[NM];
   float red[kWarps][kNP + 8];
   float ered[kWarps][NM + 2];
@@ -1096,8 +1104,9 @@ __device__ __noinline__ bool pass_all_errors(const TileArgs& a, const Maps& tm, 
 __device__ __noinline__ double exact_error(const TileArgs& a, TileSmem& S, const Geom& g, int r, const RowConst& rcst) {
   const int tid = threadIdx.x, n = g.n;
   const int64_t nch = cdiv(g.L, 32);
-  double* part = S.T64;                       // kTT doubles of scratch
-  static_assert(NM * NM >= kTT, "scratch");
+  // kTT doubles of scratch (T64 may hold the bitmap of the encode pass)
+  double* part = reinterpret_cast<double*>(&S.red[0][0]);
+  static_assert(sizeof(S.red) >= kTT * sizeof(double), "scratch");
   double colsum = 0.0;
   for (int j = 0; j < n; ++j) {
     for (int64_t c0 = 0; c0 < nch; c0 += kTT) {
@@ -1394,10 +1403,6 @@ __device__ __noinline__ void write_record(const TileArgs& a, TileSmem& S, const 
     }
   }
   __syncthreads();   // q scratch is free from here on
-  auto kval = [&](int64_t e) -> int32_t {
-    const int8_t v = k8[e];
-    return v == (int8_t)-128 ? k32[e] : (int32_t)v;
-  };
   uint32_t* cw = reinterpret_cast<uint32_t*>(rec + lay.off_c);
   if (m.wk > 0) {
     if (lay.dense) {
@@ -1446,6 +1451,7 @@ __device__ __noinline__ void write_record(const TileArgs& a, TileSmem& S, const 
         const int per = (nw + kTT - 1) / kTT;
         const int w0 = tid * per, w1 = (w0 + per) < nw ? (w0 + per) : nw;
         int cnt = 0;
+#pragma unroll 4
         for (int w = w0; w < w1; ++w) cnt += __popc(bits[w]);
         int tot;
         int idx = block_excl_scan(cnt, S.sh32, &tot);
@@ -1710,15 +1716,17 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
     __syncthreads();
     mark(kPhPredict);
 
-    // the encode pass at rank rr; SPARSE where the bitmap carries the corrections
+    // the encode pass at rank rr; SPARSE where the bitmap carries the corrections,
+    // kept in shared memory when the block has at most kBitsSmem * 32 points
     const bool sparse = pointwise && bitmap_rows(a, g);
+    uint32_t* const bitp = g.N <= (int64_t)kBitsSmem * 32 ? S.bitsm : bits;
     auto encode = [&](int rr, bool check, bool sp) -> bool {
       if (sp) {
-        return full ? pass_encode<NM, true>(a, tm, S, cu, bi, g, rr, check, rcst, cc, pointwise, qs, k8, k32, bits)
-                    : pass_encode<0, true>(a, tm, S, cu, bi, g, rr, check, rcst, cc, pointwise, qs, k8, k32, bits);
+        return full ? pass_encode<NM, true>(a, tm, S, cu, bi, g, rr, check, rcst, cc, pointwise, qs, k8, k32, bitp)
+                    : pass_encode<0, true>(a, tm, S, cu, bi, g, rr, check, rcst, cc, pointwise, qs, k8, k32, bitp);
       }
-      return full ? pass_encode<NM, false>(a, tm, S, cu, bi, g, rr, check, rcst, cc, pointwise, qs, k8, k32, bits)
-                  : pass_encode<0, false>(a, tm, S, cu, bi, g, rr, check, rcst, cc, pointwise, qs, k8, k32, bits);
+      return full ? pass_encode<NM, false>(a, tm, S, cu, bi, g, rr, check, rcst, cc, pointwise, qs, k8, k32, bitp)
+                  : pass_encode<0, false>(a, tm, S, cu, bi, g, rr, check, rcst, cc, pointwise, qs, k8, k32, bitp);
     };
     const Chunks chk = chunks_of(a, g);
     const int64_t rows_per_thread = cdiv(a.rc, kTT) * chk.n;
@@ -1774,7 +1782,7 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
       const int64_t bn = S.bnext;
       if (bn < P.nb) prefetch(a, tm, S, cu, bn, block_geom(P, P.b0 + bn), TC ? kLayoutGram : kLayoutRow);
     }
-    write_record(a, S, g, bi, raw, r, qs, k8, k32, bits);
+    write_record(a, S, g, bi, raw, r, qs, k8, k32, bitp);
     mark(kPhPack);
     if (tid == 0) S.ph[accepted ? kCntAccepted : kCntSearched] += 1;
   }

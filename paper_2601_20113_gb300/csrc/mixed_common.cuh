@@ -340,10 +340,13 @@ __device__ void jacobi_cta(float* A, float* V, double* lam, int n, float floor_a
         const float thr = fmaxf(fmaxf(1.0e-7f * sqrtf(gpp * gqq), 4.0f * 5.9604645e-8f * fmaxf(gpp, gqq)), floor_abs);
         float c = 1.0f, s = 0.0f, t = 0.0f;
         if (fabsf(apq) > thr && apq != 0.0f) {
-          const float theta = (aqq - app) / (2.0f * apq);
-          if (fabsf(theta) > 1e18f) t = 0.5f / theta;
-          else t = (theta >= 0.0f ? 1.0f : -1.0f) / (fabsf(theta) + sqrtf(1.0f + theta * theta));
-          c = 1.0f / sqrtf(1.0f + t * t);
+          // approximate division and reciprocal square root: any rotation
+          // within a few ulps of orthogonal will do, as the FP64 refinement
+          // restores orthonormality
+          const float theta = __fdividef(aqq - app, 2.0f * apq);
+          if (fabsf(theta) > 1e18f) t = __fdividef(0.5f, theta);
+          else t = __fdividef(theta >= 0.0f ? 1.0f : -1.0f, fabsf(theta) + __fsqrt_rn(1.0f + theta * theta));
+          c = rsqrtf(1.0f + t * t);
           s = t * c;
           act = 1;
         }
