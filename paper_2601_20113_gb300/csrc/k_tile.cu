@@ -1531,7 +1531,8 @@ __device__ __noinline__ void write_record(const TileArgs& a, TileSmem& S, const 
 // The eigensolver out of line: inline, it would share the kernel's registers
 // with the block state the body keeps live across it.
 __device__ __noinline__ void jacobi_tile(TileSmem& S, int n, float jfloor) {
-  jacobi_cta<kTT>(S.G32, S.Vj, S.lam_t, n, jfloor, S.jp);
+  if (n == NM) jacobi_cta<kTT, NM / 2>(S.G32, S.Vj, S.lam_t, n, jfloor, S.jp);
+  else jacobi_cta<kTT>(S.G32, S.Vj, S.lam_t, n, jfloor, S.jp);
 }
 
 // TC: the tensor-core Gram (its instantiation alone contains tcgen05 code).

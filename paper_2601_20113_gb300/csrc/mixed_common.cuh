@@ -294,8 +294,9 @@ __device__ void jacobi_reg(const float* G, int ldg, int n, bool relative, float 
 // ---------------------------------------------------------------- CTA Jacobi
 // Scratch of the CTA Jacobi (shared).
 struct JacPairs {
-  int p[NM / 2], q[NM / 2], act[NM / 2];
-  float c[NM / 2], s[NM / 2], t[NM / 2], app[NM / 2], aqq[NM / 2], apq[NM / 2];
+  int pq[NM / 2];                  // p | q << 8 | active << 16
+  float2 cs[NM / 2];               // (c, s)
+  float4 dg[NM / 2];               // (t, a_pp, a_qq, a_pq) for the exact 2x2 result
 };
 
 // Pair i of round `round` of the round-robin circle over m positions (m even).
@@ -317,11 +318,11 @@ __device__ __forceinline__ void circle_pair(int round, int i, int m, int& p, int
 // the columns of V rotate.  Thresholds as in
 // jacobi_reg (relative, with floor_abs).  Stops after a sweep without rotation
 // or 30 sweeps.  All threads call.
-template <int NT>
+template <int NT, int HF = 0>
 __device__ void jacobi_cta(float* A, float* V, double* lam, int n, float floor_abs, JacPairs& J) {
   const int tid = threadIdx.x;
-  const int m = n + (n & 1);
-  const int h = m / 2;
+  const int m = HF ? 2 * HF : n + (n & 1);
+  const int h = HF ? HF : m / 2;         // HF: the pair count at compile time (order 2 HF)
   for (int e = tid; e < NM * NM; e += NT) {
     const int i = e / NM, j = e % NM;
     V[e] = (i == j) ? 1.0f : 0.0f;
@@ -350,9 +351,9 @@ __device__ void jacobi_cta(float* A, float* V, double* lam, int n, float floor_a
           s = t * c;
           act = 1;
         }
-        J.p[tid] = p; J.q[tid] = q; J.act[tid] = act;
-        J.c[tid] = c; J.s[tid] = s; J.t[tid] = t;
-        J.app[tid] = app; J.aqq[tid] = aqq; J.apq[tid] = apq;
+        J.pq[tid] = p | q << 8 | act << 16;
+        J.cs[tid] = make_float2(c, s);
+        J.dg[tid] = make_float4(t, app, aqq, apq);
       }
       if (!__syncthreads_or(act)) continue;
       any = 1;
@@ -363,18 +364,20 @@ __device__ void jacobi_cta(float* A, float* V, double* lam, int n, float floor_a
       for (int it = tid; it < nblk + n * h; it += NT) {
         if (it < nblk) {
           const int k = it / h, l = it - k * h;
-          if (!J.act[k] && !J.act[l]) continue;
-          const int p = J.p[k], q = J.q[k], pp = J.p[l], qq = J.q[l];
-          const float ck = J.c[k], sk = J.s[k], cl = J.c[l], sl = J.s[l];
+          const int jk = J.pq[k], jl = J.pq[l];
+          if (!((jk | jl) >> 16)) continue;
+          const int p = jk & 255, q = (jk >> 8) & 255, pp = jl & 255, qq = (jl >> 8) & 255;
+          const float2 csk = J.cs[k], csl = J.cs[l];
+          const float ck = csk.x, sk = csk.y, cl = csl.x, sl = csl.y;
           const float a = A[p * NM + pp], b = A[p * NM + qq], c = A[q * NM + pp], d = A[q * NM + qq];
           const float r1 = ck * a - sk * c, r2 = ck * b - sk * d, r3 = sk * a + ck * c, r4 = sk * b + ck * d;
           float na = cl * r1 - sl * r2, nb = sl * r1 + cl * r2, nc = cl * r3 - sl * r4, nd = sl * r3 + cl * r4;
           if (k == l) {
-            const float t = J.t[k], apq = J.apq[k];
-            na = J.app[k] - t * apq;
+            const float4 dg = J.dg[k];      // (t, a_pp, a_qq, a_pq)
+            na = dg.y - dg.x * dg.w;
             nb = 0.0f;
             nc = 0.0f;
-            nd = J.aqq[k] + t * apq;
+            nd = dg.z + dg.x * dg.w;
           }
           A[p * NM + pp] = na;
           A[p * NM + qq] = nb;
@@ -383,9 +386,11 @@ __device__ void jacobi_cta(float* A, float* V, double* lam, int n, float floor_a
         } else {
           const int it2 = it - nblk;
           const int i = it2 / h, l = it2 - i * h;
-          if (!J.act[l]) continue;
-          const int p = J.p[l], q = J.q[l];
-          const float c = J.c[l], sv = J.s[l];
+          const int jl = J.pq[l];
+          if (!(jl >> 16)) continue;
+          const int p = jl & 255, q = (jl >> 8) & 255;
+          const float2 csl = J.cs[l];
+          const float c = csl.x, sv = csl.y;
           const float x = V[i * NM + p], y = V[i * NM + q];
           V[i * NM + p] = c * x - sv * y;
           V[i * NM + q] = sv * x + c * y;
