@@ -1445,18 +1445,33 @@ __device__ __noinline__ void write_record(const TileArgs& a, TileSmem& S, const 
       // ib + wk bits per task -> exactly ib + wk words
       uint32_t* list = reinterpret_cast<uint32_t*>(qs);
       if (bitmap_rows(a, g)) {
-        // entry list from the bitmap the encode pass wrote: contiguous word
-        // ranges per thread, an exclusive scan of their counts, then the bits
+        // entry list from the bitmap the encode pass wrote: warp w takes a
+        // contiguous range of words, 32 at a step (one per lane, so the
+        // lanes' counts are alike); a warp scan places each word's entries
+        const int lane = tid & 31, warp = tid >> 5;
         const int nw = (int)(N / 32);
-        const int per = (nw + kTT - 1) / kTT;
-        const int w0 = tid * per, w1 = (w0 + per) < nw ? (w0 + per) : nw;
+        const int per_w = (int)cdiv(nw, kWarps * 32) * 32;
+        const int wb = warp * per_w, we = (wb + per_w) < nw ? (wb + per_w) : nw;
         int cnt = 0;
-#pragma unroll 4
-        for (int w = w0; w < w1; ++w) cnt += __popc(bits[w]);
-        int tot;
-        int idx = block_excl_scan(cnt, S.sh32, &tot);
-        for (int w = w0; w < w1; ++w) {
-          uint32_t mk = bits[w];
+        for (int w = wb + lane; w < we; w += 32) cnt += __popc(bits[w]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
+        if (lane == 0) S.warp_cnt[warp] = cnt;
+        __syncthreads();
+        int base = 0;
+        for (int i = 0; i < warp; ++i) base += S.warp_cnt[i];
+        for (int w0 = wb; w0 < we; w0 += 32) {
+          const int w = w0 + lane;
+          uint32_t mk = w < we ? bits[w] : 0u;
+          const int c = __popc(mk);
+          int incl = c;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+          }
+          int idx = base + incl - c;
+          base += __shfl_sync(FULL, incl, 31);
           while (mk) {
             const int b = __ffs(mk) - 1;
             mk &= mk - 1;
