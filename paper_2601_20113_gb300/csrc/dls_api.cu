@@ -305,6 +305,7 @@ static int enqueue_compress(const Plan& P, const Layout& L, const void* d_in, vo
     if (ev1) CK(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
     if ((st = launch_scan(P, w, out_cap, d_out, s)) != DLS_OK) return st;
     if ((st = launch_compact(P, mw, d_out, s)) != DLS_OK) return st;
+    if ((st = launch_pack_tile(P, mw, d_out, s)) != DLS_OK) return st;
   } else {
     if (ev0) CK(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
     if ((st = launch_plain_compress(P, d_in, w, s)) != DLS_OK) return st;
@@ -438,7 +439,7 @@ int dls_compress(const dls_params* p, const void* d_in, void* d_out, size_t out_
   if (hs.nonfinite) return DLS_ERR_NONFINITE;
   *out_bytes = (size_t)hs.total_bytes;
   if (hs.capacity) return DLS_ERR_CAPACITY;
-  return DLS_OK;
+  return hs.corrupt ? DLS_ERR_CORRUPT : DLS_OK;
 }
 
 size_t dls_host_staging_size(const dls_params* p) {
@@ -676,7 +677,7 @@ int dls_plan_execute(dls_plan* pl, size_t* out_bytes, dls_stream_t stream) {
   if (hs.nonfinite) return DLS_ERR_NONFINITE;
   *out_bytes = (size_t)hs.total_bytes;
   if (hs.capacity) return DLS_ERR_CAPACITY;
-  return DLS_OK;
+  return hs.corrupt ? DLS_ERR_CORRUPT : DLS_OK;
 }
 
 int dls_plan_info(const dls_plan* pl, int32_t* variant, float* tune_ms) {

@@ -19,6 +19,9 @@ constexpr uint32_t kVersion = 1u;
 constexpr int kHdr = 128;
 constexpr int kVarRec = 32;
 constexpr uint32_t kFlagRaw = 1u, kFlagSpatial = 2u, kFlagDense = 4u;
+// Block metadata only (never in a record): the record waits in its staging
+// slot for the deferred packer, which writes it at its stream offset.
+constexpr uint32_t kFlagDeferred = 1u << 8;
 constexpr double kQmaxF32 = 16777216.0;    // |c/delta| must stay below 2^24 (f32 fields)
 constexpr double kQmaxF64 = 1073741824.0;  // 2^30 (f64 fields)
 constexpr double kKmax = 1048576.0;        // corrections beyond 2^20 steps become escapes
@@ -237,6 +240,7 @@ int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, in
                          cudaStream_t s);
 bool tile_chunk_box(const Plan& p, int* bxb, int* yc, int* zc, int* bt);
 int launch_compact(const Plan& p, const MixedWork& w, void* d_out, cudaStream_t s);
+int launch_pack_tile(const Plan& p, const MixedWork& w, void* d_out, cudaStream_t s);
 size_t mixed_smem_bytes();
 int launch_mlp_train(float* params, float* adam, const float* feat, const float* target, const int32_t* order,
                      int64_t n_order, int steps, int B, float lr, int step0, float* loss, cudaStream_t s);

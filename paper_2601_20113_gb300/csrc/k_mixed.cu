@@ -1001,11 +1001,13 @@ __global__ void __launch_bounds__(kMT, MINB) k_mixed(MxArgs a) {
   mixed_body(a);
 }
 
-// Copies the staged records to their stream positions.
+// Copies the staged records to their stream positions (deferred records are
+// written there by the deferred packer instead).
 __global__ void __launch_bounds__(256) k_compact(Plan P, const uint8_t* staging, const BlockMeta* meta,
                                                  const unsigned long long* offsets, Status* st, uint8_t* out) {
   if (st->capacity || st->nonfinite) return;
   for (int64_t bi = blockIdx.x; bi < P.nb; bi += gridDim.x) {
+    if (meta[bi].flags & kFlagDeferred) continue;
     const Geom g = block_geom(P, P.b0 + bi);
     const uint4* src = reinterpret_cast<const uint4*>(staging + align_up((g.pt_off - P.pt_base) * 4, 16) + 48 * bi);
     uint4* dst = reinterpret_cast<uint4*>(out + P.payload_pos + offsets[bi]);

@@ -1272,15 +1272,220 @@ __device__ __forceinline__ void flush32(uint64_t& acc, int& nbits, uint32_t* dst
   if (nbits >= 32) { dst[wo++] = (uint32_t)acc; acc >>= 32; nbits -= 32; }
 }
 
-__device__ __noinline__ void write_record(const TileArgs& a, TileSmem& S, const Geom& g, int64_t bi, bool raw, int r,
-                             int32_t* qs, const int8_t* k8, const int32_t* k32, const uint32_t* bits) {
-  const int tid = threadIdx.x;
+// ---------------------------------------------------------------- record packing
+// The packing steps after the stored basis, shared by the record writer of the
+// tile kernel and the deferred packer (k_pack_tile).  All threads of a
+// kTT-thread CTA call them.
+
+// q columns: 32 consecutive values of one column per task -> exactly w words.
+// qs holds column c at qs + c * align_up(L, 4).
+__device__ __forceinline__ void pack_q(uint32_t* qw, const int32_t* qs, const uint8_t* wq, const int64_t* colbase,
+                                       int rr, int64_t L) {
+  const int runs = (int)cdiv(L, 32);
+  const int64_t Lq = align_up(L, 4);
+  for (int task = threadIdx.x; task < runs * rr; task += kTT) {
+    const int c = task / runs;
+    const int first = (task - c * runs) * 32;
+    const int wdt = wq[c];
+    if (wdt == 0) continue;
+    const int32_t* col = qs + (int64_t)c * Lq + first;
+    const int cnt = (int)((L - first) < 32 ? (L - first) : 32);
+    uint32_t* dst = qw + colbase[c] + (first / 32) * wdt;
+    uint32_t z[32];
+    if (cnt == 32) {
+      const uint4* cv = reinterpret_cast<const uint4*>(col);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const uint4 v = cv[i];
+        z[4 * i + 0] = zigzag((int32_t)v.x);
+        z[4 * i + 1] = zigzag((int32_t)v.y);
+        z[4 * i + 2] = zigzag((int32_t)v.z);
+        z[4 * i + 3] = zigzag((int32_t)v.w);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) z[i] = i < cnt ? zigzag(col[i]) : 0u;
+    }
+    uint64_t acc = 0;
+    int nbits = 0, wo = 0;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      if (i < cnt) {
+        acc |= (uint64_t)z[i] << nbits;
+        nbits += wdt;
+        flush32(acc, nbits, dst, wo);
+      }
+    }
+    if (nbits > 0) dst[wo] = (uint32_t)acc;
+  }
+}
+
+// Dense corrections: 32 elements of wk bits per task -> exactly wk words.
+// With the bitmap (bits != nullptr) k8 counts only where a bit is set.
+__device__ __forceinline__ void pack_dense(uint32_t* cw, const int8_t* k8, const int32_t* k32, const uint32_t* bits,
+                                           int wk, int64_t N) {
+  const int64_t runs = cdiv(N, 32);
+  for (int64_t task = threadIdx.x; task < runs; task += kTT) {
+    const int64_t first = task * 32;
+    const int cnt = (int)((N - first) < 32 ? (N - first) : 32);
+    uint32_t* dst = cw + task * wk;
+    const uint32_t bw = bits ? bits[task] : 0xFFFFFFFFu;
+    int8_t kb[32];
+    if (cnt == 32) {
+      const uint4* kv4 = reinterpret_cast<const uint4*>(k8 + first);
+      const uint4 w0 = kv4[0], w1 = kv4[1];
+      const uint32_t wd[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+      for (int i = 0; i < 32; ++i) kb[i] = (int8_t)(wd[i >> 2] >> (8 * (i & 3)));
+    } else {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) kb[i] = i < cnt ? k8[first + i] : (int8_t)0;
+    }
+    uint64_t acc = 0;
+    int nbits = 0, wo = 0;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      if (i < cnt) {
+        int32_t kv = (bw >> i) & 1u ? kb[i] : 0;
+        if (kv == -128) kv = k32[first + i];
+        acc |= (uint64_t)(kv == kEscape ? 0u : zigzag(kv)) << nbits;
+        nbits += wk;
+        flush32(acc, nbits, dst, wo);
+      }
+    }
+    if (nbits > 0) dst[wo] = (uint32_t)acc;
+  }
+}
+
+// Entry list (element indices, in element order) from the nonzero-correction
+// bitmap: warp w takes a contiguous range of words, 32 at a step (one per lane,
+// so the lanes' counts are alike); a warp scan places each word's entries.
+// warp_cnt: kWarps ints of shared scratch.
+__device__ __forceinline__ void bitmap_list(uint32_t* list, const uint32_t* bits, int64_t N, int64_t ncorr,
+                                            int* warp_cnt) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nw = (int)(N / 32);
+  const int per_w = (int)cdiv(nw, kWarps * 32) * 32;
+  const int wb = warp * per_w, we = (wb + per_w) < nw ? (wb + per_w) : nw;
+  int cnt = 0;
+  for (int w = wb + lane; w < we; w += 32) cnt += __popc(bits[w]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
+  if (lane == 0) warp_cnt[warp] = cnt;
+  __syncthreads();
+  int base = 0;
+  for (int i = 0; i < warp; ++i) base += warp_cnt[i];
+  for (int w0 = wb; w0 < we; w0 += 32) {
+    const int w = w0 + lane;
+    uint32_t mk = w < we ? bits[w] : 0u;
+    const int c = __popc(mk);
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += y;
+    }
+    int idx = base + incl - c;
+    base += __shfl_sync(FULL, incl, 31);
+    while (mk) {
+      const int b = __ffs(mk) - 1;
+      mk &= mk - 1;
+      if (idx < ncorr) list[idx] = (uint32_t)(w * 32 + b);   // the count and the bits agree
+      ++idx;
+    }
+  }
+  __syncthreads();
+}
+
+// Sparse corrections: 32 entries of ib + wk bits per task -> exactly ib + wk words.
+__device__ __forceinline__ void pack_sparse(uint32_t* cw, const uint32_t* list, const int8_t* k8, const int32_t* k32,
+                                            int ib, int wk, int64_t nc) {
+  const int W = ib + wk;
+  for (int64_t task = threadIdx.x; task < cdiv(nc, 32); task += kTT) {
+    const int64_t first = task * 32;
+    const int cnt = (int)((nc - first) < 32 ? (nc - first) : 32);
+    uint32_t* dst = cw + task * W;
+    // all 32 entries, then all 32 correction bytes, before the bit packing
+    uint32_t ee[32];
+    if (cnt == 32) {
+      const uint4* lv = reinterpret_cast<const uint4*>(list + first);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const uint4 v = lv[i];
+        ee[4 * i + 0] = v.x; ee[4 * i + 1] = v.y; ee[4 * i + 2] = v.z; ee[4 * i + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) ee[i] = i < cnt ? list[first + i] : 0u;
+    }
+    int8_t kb[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) kb[i] = i < cnt ? k8[ee[i]] : (int8_t)0;
+    uint64_t acc = 0;
+    int nbits = 0, wo = 0;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      if (i < cnt) {
+        const int32_t kv = kb[i] == (int8_t)-128 ? k32[ee[i]] : (int32_t)kb[i];
+        acc |= (uint64_t)ee[i] << nbits;
+        nbits += ib;
+        flush32(acc, nbits, dst, wo);
+        acc |= (uint64_t)zigzag(kv) << nbits;
+        nbits += wk;
+        flush32(acc, nbits, dst, wo);
+      }
+    }
+    if (nbits > 0) dst[wo] = (uint32_t)acc;
+  }
+}
+
+// Zeroes the 16-byte words of rec that hold padding between sections (below
+// `limit`), to be written over by the sections themselves after a barrier.
+__device__ __forceinline__ void zero_padding(uint8_t* rec, const RecLayout& lay, const BlockMeta& m, int n,
+                                             int64_t qwords, int64_t limit) {
+  const int rr = m.r;
+  const int64_t ends[6] = {lay.off_wq + rr, lay.off_v + (int64_t)n * rr * 4, lay.off_q + qwords * 4,
+                           lay.off_c + lay.corr_words * 4, lay.off_ei + (int64_t)m.nesc * 4,
+                           lay.off_ev + (int64_t)m.nesc * 4};
+  for (int i = 0; i < 6; ++i) {
+    const int64_t w = ends[i] / 16 * 16;
+    if (w < m.nbytes && w < limit) *reinterpret_cast<uint4*>(rec + w) = make_uint4(0, 0, 0, 0);
+  }
+}
+
+// Deferred packing: a record whose q columns, nonzero-correction bitmap and
+// correction bytes stay in its own staging slot (after the record prefix)
+// until k_pack_tile writes it at its stream offset.  The slot holds a raw
+// record (16 + 4 N bytes), which leaves room for all three when the rank is
+// small next to n, and for the sparse entry list after them (list_cap
+// entries).
+struct SlotScratch {
+  int64_t off_q, off_bits, off_k8, end, off_list, list_cap;
+  bool fits;
+};
+__host__ __device__ inline SlotScratch slot_scratch(int r, int n, int64_t L, int64_t N) {
+  SlotScratch o;
+  const int64_t off_pre = 16 + align_up(r, 8) + align_up((int64_t)n * r * 4, 8);   // the record's q offset
+  o.off_q = align_up(off_pre, 16);
+  o.off_bits = o.off_q + (int64_t)r * align_up(L, 4) * 4;
+  o.off_k8 = o.off_bits + align_up(N / 8, 16);
+  o.end = o.off_k8 + align_up(N, 16);
+  o.off_list = o.end;
+  o.list_cap = o.end <= raw_record_bytes(N, 4) ? (raw_record_bytes(N, 4) - o.end) / 4 : 0;
+  o.fits = r > 0 && N % 32 == 0 && N <= (int64_t)kBitsSmem * 32 && o.end <= raw_record_bytes(N, 4);
+  return o;
+}
+constexpr int kDeferMaxWk = 7;                // deferred records have |k| < 64: no k32 values
+
+// Record of block bi, part 1 (all threads): thread 0 works out the layout
+// (raw when it is not smaller than the raw record), the block metadata and
+// the column offsets.  `defer` marks a non-raw record as deferred.
+__device__ void record_meta(const TileArgs& a, TileSmem& S, const Geom& g, int64_t bi, bool raw, int r, bool defer) {
   const int n = g.n;
-  const int64_t L = g.L, N = g.N, M = g.M;
-  uint8_t* rec = a.staging + align_up((g.pt_off - a.P.pt_base) * 4, 16) + 48 * bi;
+  const int64_t L = g.L, N = g.N;
   BlockMeta& m = S.m;
   RecLayout& lay = S.lay;
-  if (tid == 0) {
+  if (threadIdx.x == 0) {
     const int64_t rawsz = raw_record_bytes(N, 4);
     m.rcap = a.P.rank_cap < n ? a.P.rank_cap : n;
     m.nprobes = 0;
@@ -1298,6 +1503,7 @@ __device__ __noinline__ void write_record(const TileArgs& a, TileSmem& S, const 
       } else {
         m.r = r; m.wk = wk; m.ib = ib; m.ncorr = S.ncorr; m.nesc = S.nesc;
         m.flags |= lay.dense ? (int)kFlagDense : 0;
+        m.flags |= defer ? (int)kFlagDeferred : 0;
         m.nbytes = lay.size;
       }
     }
@@ -1314,38 +1520,39 @@ __device__ __noinline__ void write_record(const TileArgs& a, TileSmem& S, const 
     S.colbase[m.r] = wb;
   }
   __syncthreads();
-  if (m.flags & kFlagRaw) {
-    if (tid == 0) {
-      reinterpret_cast<uint32_t*>(rec)[0] = (uint32_t)m.flags << 8;
-      reinterpret_cast<uint32_t*>(rec)[1] = 0;
-      reinterpret_cast<uint32_t*>(rec)[2] = 0;
-      reinterpret_cast<uint32_t*>(rec)[3] = (uint32_t)m.nbytes;
-    }
-    float* vals = reinterpret_cast<float*>(rec + 16);
-    for (int64_t e = tid; e < N; e += kTT) {
-      const int64_t lt = e / M, ls = e - lt * M;
-      vals[e] = a.in[gidx_row(a, g, ls, (int)lt)];
-    }
-    if (tid == 0 && (16 + N * 4) % 16) {
-      // zero the padding after the last value
-      for (int64_t b = 16 + N * 4; b < m.nbytes; ++b) rec[b] = 0;
-    }
-    __syncthreads();
-    return;
-  }
-  const int rr = m.r;
-  // zero the 16-byte words that hold padding between sections (written over
-  // by the sections themselves after the barrier)
+}
+
+// A raw record: header and the block's values in order.
+__device__ void record_raw(const TileArgs& a, TileSmem& S, const Geom& g, uint8_t* rec) {
+  const int tid = threadIdx.x;
+  const BlockMeta& m = S.m;
+  const int64_t N = g.N, M = g.M;
   if (tid == 0) {
-    const int64_t qwords = S.colbase[rr];
-    const int64_t ends[6] = {lay.off_wq + rr, lay.off_v + (int64_t)n * rr * 4, lay.off_q + qwords * 4,
-                             lay.off_c + lay.corr_words * 4, lay.off_ei + (int64_t)m.nesc * 4,
-                             lay.off_ev + (int64_t)m.nesc * 4};
-    for (int i = 0; i < 6; ++i) {
-      const int64_t w = ends[i] / 16 * 16;
-      if (w < m.nbytes) *reinterpret_cast<uint4*>(rec + w) = make_uint4(0, 0, 0, 0);
-    }
+    reinterpret_cast<uint32_t*>(rec)[0] = (uint32_t)m.flags << 8;
+    reinterpret_cast<uint32_t*>(rec)[1] = 0;
+    reinterpret_cast<uint32_t*>(rec)[2] = 0;
+    reinterpret_cast<uint32_t*>(rec)[3] = (uint32_t)m.nbytes;
   }
+  float* vals = reinterpret_cast<float*>(rec + 16);
+  for (int64_t e = tid; e < N; e += kTT) {
+    const int64_t lt = e / M, ls = e - lt * M;
+    vals[e] = a.in[gidx_row(a, g, ls, (int)lt)];
+  }
+  if (tid == 0 && (16 + N * 4) % 16) {
+    // zero the padding after the last value
+    for (int64_t b = 16 + N * 4; b < m.nbytes; ++b) rec[b] = 0;
+  }
+  __syncthreads();
+}
+
+// Record prefix: padding words below `limit` zeroed, then the header, the
+// column widths and the stored basis.
+__device__ void record_prefix(TileSmem& S, const Geom& g, uint8_t* rec, int64_t limit) {
+  const int tid = threadIdx.x, n = g.n;
+  const BlockMeta& m = S.m;
+  const RecLayout& lay = S.lay;
+  const int rr = m.r;
+  if (tid == 0) zero_padding(rec, lay, m, n, S.colbase[rr], limit);
   __syncthreads();
   if (tid == 0) {
     rec[0] = (uint8_t)m.r;
@@ -1362,124 +1569,33 @@ __device__ __noinline__ void write_record(const TileArgs& a, TileSmem& S, const 
     const int c = i / n, j = i - c * n;
     vout[i] = S.VstT[c * NM + j];
   }
-  // q: 32 consecutive values of one column per task -> exactly w words
-  uint32_t* qw = reinterpret_cast<uint32_t*>(rec + lay.off_q);
-  {
-    const int64_t runs = cdiv(L, 32);
-    for (int64_t task = tid; task < runs * rr; task += kTT) {
-      const int c = (int)(task / runs);
-      const int64_t first = (task - (int64_t)c * runs) * 32;
-      const int wdt = m.wq[c];
-      if (wdt == 0) continue;
-      const int32_t* col = qs + (int64_t)c * align_up(L, 4) + first;
-      const int cnt = (int)((L - first) < 32 ? (L - first) : 32);
-      uint32_t* dst = qw + S.colbase[c] + (first / 32) * wdt;
-      uint32_t z[32];
-      if (cnt == 32) {
-        const uint4* cv = reinterpret_cast<const uint4*>(col);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const uint4 v = cv[i];
-          z[4 * i + 0] = zigzag((int32_t)v.x);
-          z[4 * i + 1] = zigzag((int32_t)v.y);
-          z[4 * i + 2] = zigzag((int32_t)v.z);
-          z[4 * i + 3] = zigzag((int32_t)v.w);
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < 32; ++i) z[i] = i < cnt ? zigzag(col[i]) : 0u;
-      }
-      uint64_t acc = 0;
-      int nbits = 0, wo = 0;
-#pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        if (i < cnt) {
-          acc |= (uint64_t)z[i] << nbits;
-          nbits += wdt;
-          flush32(acc, nbits, dst, wo);
-        }
-      }
-      if (nbits > 0) dst[wo] = (uint32_t)acc;
-    }
+}
+
+// The whole record of block bi in its staging slot (k_compact moves it).
+__device__ __noinline__ void write_record(const TileArgs& a, TileSmem& S, const Geom& g, int64_t bi, bool raw, int r,
+                             int32_t* qs, const int8_t* k8, const int32_t* k32, const uint32_t* bits) {
+  const int64_t L = g.L, N = g.N, M = g.M;
+  uint8_t* rec = a.staging + align_up((g.pt_off - a.P.pt_base) * 4, 16) + 48 * bi;
+  record_meta(a, S, g, bi, raw, r, false);
+  const BlockMeta& m = S.m;
+  const RecLayout& lay = S.lay;
+  if (m.flags & kFlagRaw) {
+    record_raw(a, S, g, rec);
+    return;
   }
+  record_prefix(S, g, rec, m.nbytes);
+  pack_q(reinterpret_cast<uint32_t*>(rec + lay.off_q), qs, m.wq, S.colbase, m.r, L);
   __syncthreads();   // q scratch is free from here on
   uint32_t* cw = reinterpret_cast<uint32_t*>(rec + lay.off_c);
   if (m.wk > 0) {
     if (lay.dense) {
-      const int wk = m.wk;
-      const int64_t runs = cdiv(N, 32);
       // bitmap rows: k8 may hold stale bytes where the bitmap has no bit
-      const bool masked = bitmap_rows(a, g);
-      for (int64_t task = tid; task < runs; task += kTT) {
-        const int64_t first = task * 32;
-        const int cnt = (int)((N - first) < 32 ? (N - first) : 32);
-        uint32_t* dst = cw + task * wk;
-        const uint32_t bw = masked ? bits[task] : 0xFFFFFFFFu;
-        int8_t kb[32];
-        if (cnt == 32) {
-          const uint4* kv4 = reinterpret_cast<const uint4*>(k8 + first);
-          const uint4 w0 = kv4[0], w1 = kv4[1];
-          const uint32_t wd[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-#pragma unroll
-          for (int i = 0; i < 32; ++i) kb[i] = (int8_t)(wd[i >> 2] >> (8 * (i & 3)));
-        } else {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) kb[i] = i < cnt ? k8[first + i] : (int8_t)0;
-        }
-        uint64_t acc = 0;
-        int nbits = 0, wo = 0;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          if (i < cnt) {
-            int32_t kv = (bw >> i) & 1u ? kb[i] : 0;
-            if (kv == -128) kv = k32[first + i];
-            acc |= (uint64_t)(kv == kEscape ? 0u : zigzag(kv)) << nbits;
-            nbits += wk;
-            flush32(acc, nbits, dst, wo);
-          }
-        }
-        if (nbits > 0) dst[wo] = (uint32_t)acc;
-      }
+      pack_dense(cw, k8, k32, bitmap_rows(a, g) ? bits : nullptr, m.wk, N);
     } else {
-      // entry list (element indices) into the q scratch, then 32 entries of
-      // ib + wk bits per task -> exactly ib + wk words
+      // entry list (element indices) into the q scratch
       uint32_t* list = reinterpret_cast<uint32_t*>(qs);
       if (bitmap_rows(a, g)) {
-        // entry list from the bitmap the encode pass wrote: warp w takes a
-        // contiguous range of words, 32 at a step (one per lane, so the
-        // lanes' counts are alike); a warp scan places each word's entries
-        const int lane = tid & 31, warp = tid >> 5;
-        const int nw = (int)(N / 32);
-        const int per_w = (int)cdiv(nw, kWarps * 32) * 32;
-        const int wb = warp * per_w, we = (wb + per_w) < nw ? (wb + per_w) : nw;
-        int cnt = 0;
-        for (int w = wb + lane; w < we; w += 32) cnt += __popc(bits[w]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL, cnt, o);
-        if (lane == 0) S.warp_cnt[warp] = cnt;
-        __syncthreads();
-        int base = 0;
-        for (int i = 0; i < warp; ++i) base += S.warp_cnt[i];
-        for (int w0 = wb; w0 < we; w0 += 32) {
-          const int w = w0 + lane;
-          uint32_t mk = w < we ? bits[w] : 0u;
-          const int c = __popc(mk);
-          int incl = c;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += y;
-          }
-          int idx = base + incl - c;
-          base += __shfl_sync(FULL, incl, 31);
-          while (mk) {
-            const int b = __ffs(mk) - 1;
-            mk &= mk - 1;
-            if (idx < m.ncorr) list[idx] = (uint32_t)(w * 32 + b);   // the count and the bits agree
-            ++idx;
-          }
-        }
-        __syncthreads();
+        bitmap_list(list, bits, N, m.ncorr, S.warp_cnt);
       } else {
         compact16(
             S, k8, (int)N, [&](int8_t b, int e) { return b != 0 && (b != (int8_t)-128 || k32[e] != kEscape); },
@@ -1487,44 +1603,7 @@ __device__ __noinline__ void write_record(const TileArgs& a, TileSmem& S, const 
               if (idx < m.ncorr) list[idx] = (uint32_t)e;   // the count and the bytes agree by construction
             });
       }
-      const int ib = m.ib, wk = m.wk, W = ib + wk;
-      const int64_t nc = m.ncorr;
-      for (int64_t task = tid; task < cdiv(nc, 32); task += kTT) {
-        const int64_t first = task * 32;
-        const int cnt = (int)((nc - first) < 32 ? (nc - first) : 32);
-        uint32_t* dst = cw + task * W;
-        // all 32 entries, then all 32 correction bytes, before the bit packing
-        uint32_t ee[32];
-        if (cnt == 32) {
-          const uint4* lv = reinterpret_cast<const uint4*>(list + first);
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const uint4 v = lv[i];
-            ee[4 * i + 0] = v.x; ee[4 * i + 1] = v.y; ee[4 * i + 2] = v.z; ee[4 * i + 3] = v.w;
-          }
-        } else {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) ee[i] = i < cnt ? list[first + i] : 0u;
-        }
-        int8_t kb[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) kb[i] = i < cnt ? k8[ee[i]] : (int8_t)0;
-        uint64_t acc = 0;
-        int nbits = 0, wo = 0;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          if (i < cnt) {
-            const int32_t kv = kb[i] == (int8_t)-128 ? k32[ee[i]] : (int32_t)kb[i];
-            acc |= (uint64_t)ee[i] << nbits;
-            nbits += ib;
-            flush32(acc, nbits, dst, wo);
-            acc |= (uint64_t)zigzag(kv) << nbits;
-            nbits += wk;
-            flush32(acc, nbits, dst, wo);
-          }
-        }
-        if (nbits > 0) dst[wo] = (uint32_t)acc;
-      }
+      pack_sparse(cw, list, k8, k32, m.ib, m.wk, m.ncorr);
     }
   }
   if (m.nesc > 0) {
@@ -1539,6 +1618,24 @@ __device__ __noinline__ void write_record(const TileArgs& a, TileSmem& S, const 
           ev[idx] = a.in[gidx_row(a, g, ls, (int)lt)];
         });
   }
+  __syncthreads();
+}
+
+// A deferred record: metadata, then the prefix into the slot and the bitmap
+// after the q columns; k_pack_tile does the rest once the offsets are known.
+// Falls back to a raw record when the layout says so.
+__device__ __noinline__ void defer_record(const TileArgs& a, TileSmem& S, const Geom& g, int64_t bi, int r,
+                                          const uint32_t* bits) {
+  uint8_t* slot = a.staging + align_up((g.pt_off - a.P.pt_base) * 4, 16) + 48 * bi;
+  record_meta(a, S, g, bi, false, r, true);
+  if (S.m.flags & kFlagRaw) {
+    record_raw(a, S, g, slot);
+    return;
+  }
+  const SlotScratch sc = slot_scratch(r, g.n, g.L, g.N);
+  record_prefix(S, g, slot, sc.off_q);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(slot + sc.off_bits);
+  for (int64_t i = threadIdx.x; i < g.N / 32; i += kTT) dst[i] = bits[i];
   __syncthreads();
 }
 
@@ -1736,10 +1833,23 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
     // kept in shared memory when the block has at most kBitsSmem * 32 points
     const bool sparse = pointwise && bitmap_rows(a, g);
     uint32_t* const bitp = g.N <= (int64_t)kBitsSmem * 32 ? S.bitsm : bits;
-    auto encode = [&](int rr, bool check, bool sp) -> bool {
+    // SPARSE passes whose rank leaves room write q and k8 into the block's
+    // staging slot (deferred packing); the others use the CTA's scratch
+    uint8_t* const slot = a.staging + align_up((g.pt_off - P.pt_base) * 4, 16) + 48 * bi;
+    bool in_slot = false;
+    auto encode = [&](int rr, bool check, bool sp, bool cta_scratch) -> bool {
+      in_slot = false;
       if (sp) {
-        return full ? pass_encode<NM, true>(a, tm, S, cu, bi, g, rr, check, rcst, cc, pointwise, qs, k8, k32, bitp)
-                    : pass_encode<0, true>(a, tm, S, cu, bi, g, rr, check, rcst, cc, pointwise, qs, k8, k32, bitp);
+        int32_t* q = qs;
+        int8_t* k = k8;
+        const SlotScratch sc = slot_scratch(rr, g.n, g.L, g.N);
+        if (!cta_scratch && sc.fits) {
+          q = reinterpret_cast<int32_t*>(slot + sc.off_q);
+          k = reinterpret_cast<int8_t*>(slot + sc.off_k8);
+          in_slot = true;
+        }
+        return full ? pass_encode<NM, true>(a, tm, S, cu, bi, g, rr, check, rcst, cc, pointwise, q, k, k32, bitp)
+                    : pass_encode<0, true>(a, tm, S, cu, bi, g, rr, check, rcst, cc, pointwise, q, k, k32, bitp);
       }
       return full ? pass_encode<NM, false>(a, tm, S, cu, bi, g, rr, check, rcst, cc, pointwise, qs, k8, k32, bitp)
                   : pass_encode<0, false>(a, tm, S, cu, bi, g, rr, check, rcst, cc, pointwise, qs, k8, k32, bitp);
@@ -1751,7 +1861,7 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
     int r = 0;
     if (a.learned != kRankSearch && !may_overflow) {
       const int rp = S.r_pred;
-      if (!encode(rp, true, sparse)) break;
+      if (!encode(rp, true, sparse, false)) break;
       mark(kPhEncode);
       const double E_rm1 = S.Ered[0], E_r = S.Ered[1];
       if (!S.ovf) {
@@ -1786,19 +1896,28 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
         }
         r = lo;
         if (!pointwise && !decide_pass(a, S, g, r, Eall[r], bnd, el2, rcst)) raw = true;
-        if (!raw && !encode(r, false, sparse)) break;
+        if (!raw && !encode(r, false, sparse, false)) break;
       }
       mark(kPhSearch);
     }
     // escapes are listed from k8 itself: a block that has any is encoded
-    // again with every element written
-    if (!raw && sparse && S.nesc > 0 && !encode(r, false, false)) break;
+    // again with every element written; a deferred record has no correction
+    // beyond kDeferMaxWk bits and an entry list that fits its slot, else the
+    // block is encoded again into the CTA's scratch for the record writer here
+    if (!raw && sparse && S.nesc > 0) {
+      if (!encode(r, false, false, true)) break;
+    } else if (!raw && in_slot &&
+               (bit_width((uint32_t)S.kmax) > kDeferMaxWk || S.ncorr > slot_scratch(r, g.n, g.L, g.N).list_cap)) {
+      if (!encode(r, false, true, true)) break;
+    }
+    const bool deferred = !raw && in_slot;
     // the next block's first chunks load while this record is packed
     {
       const int64_t bn = S.bnext;
       if (bn < P.nb) prefetch(a, tm, S, cu, bn, block_geom(P, P.b0 + bn), TC ? kLayoutGram : kLayoutRow);
     }
-    write_record(a, S, g, bi, raw, r, qs, k8, k32, bitp);
+    if (deferred) defer_record(a, S, g, bi, r, bitp);
+    else write_record(a, S, g, bi, raw, r, qs, k8, k32, bitp);
     mark(kPhPack);
     if (tid == 0) S.ph[accepted ? kCntAccepted : kCntSearched] += 1;
   }
@@ -1824,6 +1943,74 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
     S.ph[kCntExact] = S.nexact;
     if (a.phase)
       for (int i = 0; i < kPhases; ++i) a.phase[(int64_t)blockIdx.x * kPhases + i] += S.ph[i];
+  }
+}
+
+// ---------------------------------------------------------------- deferred packing
+// Packs the records the tile kernel left in their staging slots, straight to
+// their stream offsets (after the scan).  One CTA per block at a time, many
+// CTAs per SM: the bit packing is short dependent chains, which a full SM of
+// warps overlaps.
+__global__ void __launch_bounds__(kTT, 6) k_pack_tile(Plan P, const BlockMeta* meta, uint8_t* staging,
+                                                      const unsigned long long* offsets, Status* st, uint8_t* out) {
+  __shared__ BlockMeta m;
+  __shared__ RecLayout lay;
+  __shared__ int64_t colbase[NM + 1];
+  __shared__ int warp_cnt[kWarps];
+  __shared__ __align__(16) uint32_t bitsm[kBitsSmem];
+  __shared__ int skip;
+  if (st->capacity || st->nonfinite || st->timeout) return;
+  const int tid = threadIdx.x;
+  for (int64_t bi = blockIdx.x; bi < P.nb; bi += gridDim.x) {
+    const Geom g = block_geom(P, P.b0 + bi);
+    if (tid == 0) {
+      m = meta[bi];
+      int sk = !(m.flags & kFlagDeferred);
+      if (!sk) {
+        lay = rec_layout(m.r, g.n, g.L, g.N, 4, m.wq, m.wk, m.ib, m.ncorr, m.nesc);
+        const SlotScratch sc = slot_scratch(m.r, g.n, g.L, g.N);
+        // a deferred record is one the tile kernel could defer: check before use
+        if (!sc.fits || lay.size != m.nbytes || m.nesc != 0 || m.wk > kDeferMaxWk || m.r > g.n ||
+            m.ncorr > sc.list_cap) {
+          atomicOr(&st->corrupt, 1u);
+          sk = 1;
+        }
+        int64_t wb = 0;
+        for (int c = 0; c < m.r && c < NM; ++c) { colbase[c] = wb; wb += (g.L * m.wq[c] + 31) / 32; }
+        colbase[m.r < NM ? m.r : NM] = wb;
+      }
+      skip = sk;
+    }
+    __syncthreads();
+    if (skip) {
+      __syncthreads();
+      continue;
+    }
+    const SlotScratch sc = slot_scratch(m.r, g.n, g.L, g.N);
+    uint8_t* slot = staging + align_up((g.pt_off - P.pt_base) * 4, 16) + 48 * bi;
+    uint8_t* rec = out + P.payload_pos + offsets[bi];
+    if (tid == 0) zero_padding(rec, lay, m, g.n, colbase[m.r], m.nbytes);
+    __syncthreads();
+    // the prefix (header, widths, basis; its padding zeroed) as it is
+    for (int64_t i = tid; i < lay.off_q / 8; i += kTT)
+      reinterpret_cast<uint2*>(rec)[i] = reinterpret_cast<const uint2*>(slot)[i];
+    const int64_t nw = g.N / 32;
+    for (int64_t i = tid; i < nw; i += kTT) bitsm[i] = reinterpret_cast<const uint32_t*>(slot + sc.off_bits)[i];
+    const int32_t* qs = reinterpret_cast<const int32_t*>(slot + sc.off_q);
+    const int8_t* k8 = reinterpret_cast<const int8_t*>(slot + sc.off_k8);
+    pack_q(reinterpret_cast<uint32_t*>(rec + lay.off_q), qs, m.wq, colbase, m.r, g.L);
+    __syncthreads();
+    if (m.wk > 0) {
+      uint32_t* cw = reinterpret_cast<uint32_t*>(rec + lay.off_c);
+      if (lay.dense) {
+        pack_dense(cw, k8, nullptr, bitsm, m.wk, g.N);
+      } else {
+        uint32_t* list = reinterpret_cast<uint32_t*>(slot + sc.off_list);
+        bitmap_list(list, bitsm, g.N, m.ncorr, warp_cnt);
+        pack_sparse(cw, list, k8, nullptr, m.ib, m.wk, m.ncorr);
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -1984,6 +2171,18 @@ int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, in
     if (variant == 1) k_tile<2, false><<<ctas, kTT, smem, s>>>(tmap, tmapg, a);
     else k_tile<4, false><<<ctas, kTT, smem, s>>>(tmap, tmapg, a);
   }
+  return cudaGetLastError() == cudaSuccess ? DLS_OK : DLS_ERR_CUDA;
+}
+
+// The deferred records of a compression (after the scan has placed them).
+int launch_pack_tile(const Plan& p, const MixedWork& w, void* d_out, cudaStream_t s) {
+  if (p.nb == 0) return DLS_OK;
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return DLS_ERR_CUDA;
+  const int64_t cap = (int64_t)sms * 6;
+  const int grid = (int)(p.nb < cap ? p.nb : cap);
+  k_pack_tile<<<grid, kTT, 0, s>>>(p, w.meta, w.staging, w.offsets, w.status, (uint8_t*)d_out);
   return cudaGetLastError() == cudaSuccess ? DLS_OK : DLS_ERR_CUDA;
 }
 
