@@ -108,6 +108,8 @@ size_t dls_workspace_size(const dls_params* p);
  * d_in: nvars * nx*ny*nz*nt values of p->dtype.  d_out: out_cap bytes.
  * d_workspace: ws_bytes >= dls_workspace_size(p).  On success *out_bytes is
  * the stream size.  On DLS_ERR_CAPACITY *out_bytes is the size needed.
+ * DLS_ERR_CORRUPT means a record failed the packer's own consistency check
+ * (an internal fault, not an input error); the stream is then not valid.
  * Synchronizes `stream` once to read the stream size. */
 int dls_compress(const dls_params* p, const void* d_in, void* d_out, size_t out_cap,
                  size_t* out_bytes, void* d_workspace, size_t ws_bytes, dls_stream_t stream);
@@ -119,8 +121,9 @@ int dls_compress(const dls_params* p, const void* d_in, void* d_out, size_t out_
  * the choice is cached as JSON lines in the file named by the environment
  * variable DLS_AUTOTUNE_CACHE when set), then captures the whole compression
  * (status reset, bound resolution, the persistent per-block kernel over every
- * block of every variable, scan + header, record placement, status readback)
- * in one CUDA graph.  Executing replays the graph and synchronizes `stream`.
+ * block of every variable, scan + header, record placement and the deferred
+ * record packer, status readback) in one CUDA graph.  Execution returns what
+ * dls_compress returns.  Executing replays the graph and synchronizes `stream`.
  * The plan owns a small pinned status buffer; buffers stay owned by the
  * caller and must outlive the plan.  Creation writes d_out and d_workspace. */
 typedef struct dls_plan dls_plan;
