@@ -1277,8 +1277,41 @@ __device__ __forceinline__ void flush32(uint64_t& acc, int& nbits, uint32_t* dst
 // tile kernel and the deferred packer (k_pack_tile).  All threads of a
 // kTT-thread CTA call them.
 
+// 32 values below 2^W into exactly W words, W known at compile time: every
+// shift and word boundary is fixed, two instructions a value.
+template <int W>
+__device__ __forceinline__ void pack32_fixed(uint32_t* dst, const uint32_t (&z)[32]) {
+  uint32_t acc = 0;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int bit = i * W, off = bit & 31;
+    acc |= z[i] << off;
+    if (off + W >= 32) {
+      dst[bit >> 5] = acc;
+      acc = off + W > 32 ? z[i] >> (32 - off) : 0u;
+    }
+  }
+}
+// pack32_fixed<w> for w in [W, kMaxFixedW]; false for other widths.
+constexpr int kMaxFixedW = 25;
+template <int W = 1>
+__device__ __forceinline__ bool pack32_width(uint32_t* dst, const uint32_t (&z)[32], int w) {
+  if constexpr (W > kMaxFixedW) {
+    return false;
+  } else {
+    if (w == W) {
+      pack32_fixed<W>(dst, z);
+      return true;
+    }
+    return pack32_width<W + 1>(dst, z, w);
+  }
+}
+
 // q columns: 32 consecutive values of one column per task -> exactly w words.
-// qs holds column c at qs + c * align_up(L, 4).
+// qs holds column c at qs + c * align_up(L, 4).  FIXED: full tasks go through
+// the compile-time-width packers (the deferred packer; the per-block kernel
+// keeps the smaller generic loop).
+template <bool FIXED = false>
 __device__ __forceinline__ void pack_q(uint32_t* qw, const int32_t* qs, const uint8_t* wq, const int64_t* colbase,
                                        int rr, int64_t L) {
   const int runs = (int)cdiv(L, 32);
@@ -1306,6 +1339,7 @@ __device__ __forceinline__ void pack_q(uint32_t* qw, const int32_t* qs, const ui
 #pragma unroll
       for (int i = 0; i < 32; ++i) z[i] = i < cnt ? zigzag(col[i]) : 0u;
     }
+    if (FIXED && cnt == 32 && pack32_width(dst, z, wdt)) continue;
     uint64_t acc = 0;
     int nbits = 0, wo = 0;
 #pragma unroll
@@ -1322,6 +1356,7 @@ __device__ __forceinline__ void pack_q(uint32_t* qw, const int32_t* qs, const ui
 
 // Dense corrections: 32 elements of wk bits per task -> exactly wk words.
 // With the bitmap (bits != nullptr) k8 counts only where a bit is set.
+template <bool FIXED = false>
 __device__ __forceinline__ void pack_dense(uint32_t* cw, const int8_t* k8, const int32_t* k32, const uint32_t* bits,
                                            int wk, int64_t N) {
   const int64_t runs = cdiv(N, 32);
@@ -1330,6 +1365,18 @@ __device__ __forceinline__ void pack_dense(uint32_t* cw, const int8_t* k8, const
     const int cnt = (int)((N - first) < 32 ? (N - first) : 32);
     uint32_t* dst = cw + task * wk;
     const uint32_t bw = bits ? bits[task] : 0xFFFFFFFFu;
+    if (FIXED && cnt == 32 && wk <= kMaxFixedW) {
+      // no k32 values here (corrections below 64)
+      const uint4* kv4 = reinterpret_cast<const uint4*>(k8 + first);
+      const uint4 w0 = kv4[0], w1 = kv4[1];
+      const uint32_t wd[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+      uint32_t z[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i)
+        z[i] = (bw >> i) & 1u ? zigzag((int32_t)(int8_t)(wd[i >> 2] >> (8 * (i & 3)))) : 0u;
+      pack32_width(dst, z, wk);
+      continue;
+    }
     int8_t kb[32];
     if (cnt == 32) {
       const uint4* kv4 = reinterpret_cast<const uint4*>(k8 + first);
@@ -1398,6 +1445,7 @@ __device__ __forceinline__ void bitmap_list(uint32_t* list, const uint32_t* bits
 }
 
 // Sparse corrections: 32 entries of ib + wk bits per task -> exactly ib + wk words.
+template <bool FIXED = false>
 __device__ __forceinline__ void pack_sparse(uint32_t* cw, const uint32_t* list, const int8_t* k8, const int32_t* k32,
                                             int ib, int wk, int64_t nc) {
   const int W = ib + wk;
@@ -1421,6 +1469,14 @@ __device__ __forceinline__ void pack_sparse(uint32_t* cw, const uint32_t* list, 
     int8_t kb[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) kb[i] = i < cnt ? k8[ee[i]] : (int8_t)0;
+    if (FIXED && cnt == 32 && W <= kMaxFixedW) {
+      // no k32 values here (corrections below 64); an entry is its index,
+      // then its correction, in W <= kMaxFixedW bits
+#pragma unroll
+      for (int i = 0; i < 32; ++i) ee[i] |= zigzag((int32_t)kb[i]) << ib;
+      pack32_width(dst, ee, W);
+      continue;
+    }
     uint64_t acc = 0;
     int nbits = 0, wo = 0;
 #pragma unroll
@@ -1998,16 +2054,16 @@ __global__ void __launch_bounds__(kTT, 6) k_pack_tile(Plan P, const BlockMeta* m
     for (int64_t i = tid; i < nw; i += kTT) bitsm[i] = reinterpret_cast<const uint32_t*>(slot + sc.off_bits)[i];
     const int32_t* qs = reinterpret_cast<const int32_t*>(slot + sc.off_q);
     const int8_t* k8 = reinterpret_cast<const int8_t*>(slot + sc.off_k8);
-    pack_q(reinterpret_cast<uint32_t*>(rec + lay.off_q), qs, m.wq, colbase, m.r, g.L);
+    pack_q<true>(reinterpret_cast<uint32_t*>(rec + lay.off_q), qs, m.wq, colbase, m.r, g.L);
     __syncthreads();
     if (m.wk > 0) {
       uint32_t* cw = reinterpret_cast<uint32_t*>(rec + lay.off_c);
       if (lay.dense) {
-        pack_dense(cw, k8, nullptr, bitsm, m.wk, g.N);
+        pack_dense<true>(cw, k8, nullptr, bitsm, m.wk, g.N);
       } else {
         uint32_t* list = reinterpret_cast<uint32_t*>(slot + sc.off_list);
         bitmap_list(list, bitsm, g.N, m.ncorr, warp_cnt);
-        pack_sparse(cw, list, k8, nullptr, m.ib, m.wk, m.ncorr);
+        pack_sparse<true>(cw, list, k8, nullptr, m.ib, m.wk, m.ncorr);
       }
     }
     __syncthreads();
