@@ -866,13 +866,25 @@ __device__ __forceinline__ void row_decode_step(const TileSmem& S, int k, float 
 }
 
 
+// Bit-matrix transpose across a warp (lane i's bit j becomes lane j's bit i):
+// five butterfly stages, each swapping the off-diagonal halves of the blocks.
+__device__ __forceinline__ uint32_t warp_transpose_bits(uint32_t v, int lane) {
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    const uint32_t lo = s == 16 ? 0x0000FFFFu : s == 8 ? 0x00FF00FFu : s == 4 ? 0x0F0F0F0Fu : s == 2 ? 0x33333333u : 0x55555555u;
+    const uint32_t t = __shfl_xor_sync(FULL, v, s);
+    v = (lane & s) ? ((v & ~lo) | ((t >> s) & lo)) : ((v & lo) | ((t << s) & ~lo));
+  }
+  return v;
+}
+
 // ---------------------------------------------------------------- encode pass
 // Projection, quantization and decode at rank r, q into the CTA scratch,
 // corrections into k8/k32; with `check`, FP32 estimates of E(r-1), E(r) land
 // in S.Ered[0], S.Ered[1].  One row per thread; the column loop is not
 // unrolled (r is small), and each basis row is read once per column for both
 // the projection and the decode step.  Column widths: OR of zigzag(q) over
-// the warp (same bit width as the maximum) into S.qor.
+// the warp (same bit width as the maximum), kept by lane k for column k, into S.qor.
 // SPARSE (pointwise bound, bitmap rows): k8 is written only for the elements
 // whose correction may be nonzero, and the record reads k8 through the
 // nonzero-correction bitmap; escapes cannot be listed from such a k8, so a
@@ -890,7 +902,7 @@ __device__ __noinline__ bool pass_encode(const TileArgs& a, const Maps& tm, Tile
   // the constants by value: the loop's stores cannot be assumed not to alias them
   const RowConst rq = rcst;
   const CorrConst cq = cc;
-  for (int i = tid; i < kWarps * NM; i += kTT) (&S.qor[0][0])[i] = 0u;
+  uint32_t qor_lane = 0;   // lane k: OR of zigzag(q) of column k over this warp's rows
   if (tid == 0) { S.kmax = 0; S.ncorr = 0; S.nesc = 0; }
   __syncthreads();
   float e1 = 0.0f, e2 = 0.0f;
@@ -924,7 +936,7 @@ __device__ __noinline__ bool pass_encode(const TileArgs& a, const Maps& tm, Tile
         const int32_t q = quant_exact(cf, rq.delta, rq.inv_delta, ovf);
         if (valid) qs[k * Lq + l] = q;
         const uint32_t wor = __reduce_or_sync(FULL, valid ? zigzag(q) : 0u);
-        if (lane == 0) S.qor[warp][k] |= wor;
+        if (lane == k) qor_lane |= wor;
         const float chk = __fmul_rn(__int2float_rn(q), rq.delta_f);
         if (check && k == r - 1 && valid) {
 #pragma unroll
@@ -966,13 +978,9 @@ __device__ __noinline__ bool pass_encode(const TileArgs& a, const Maps& tm, Tile
           kmx |= k == kEscape ? 0u : zigzag(k);
           nzb |= (k != 0 && k != kEscape ? 1u : 0u) << jj;
         }
-#pragma unroll
-        for (int j = 0; j < NM; ++j) {
-          if (j < n) {
-            const unsigned mk = __ballot_sync(FULL, (nzb >> j) & 1u);
-            if (lane == 0) bits[(j * M + l) >> 5] = mk;
-          }
-        }
+        // lane j gets column j's word of the bitmap (this warp's 32 rows)
+        const uint32_t mk = warp_transpose_bits(nzb, lane);
+        if (lane < n) bits[(lane * M + (l - lane)) >> 5] = mk;
       } else if (valid) {
         // corrections: every element decided first without branches (so they
         // interleave); the few the FP32 evaluation leaves open take the FP64 path
@@ -1041,6 +1049,7 @@ __device__ __noinline__ bool pass_encode(const TileArgs& a, const Maps& tm, Tile
     if (kmx) atomicOr(reinterpret_cast<unsigned int*>(&S.kmax), kmx);
     if (ovf) S.ovf = 1;
   }
+  if (lane < NM) S.qor[warp][lane] = qor_lane;
   __syncthreads();
   if (tid < NM) {
     uint32_t o = 0;
