@@ -819,7 +819,19 @@ struct RowConst {
 // Shifted projection sum_j d_j v_j + a0 vsum in four interleaved partial
 // sums (j mod 4), combined as (s0 + s1) + (s2 + s3): the one order every pass
 // uses for the coefficients.
+// Order 16 (NF = NM): the partial-sum pairs (s0, s1), (s2, s3) as packed
+// FP32 FMAs (each component rounds as __fmaf_rn: the same numbers).
+template <int NF>
 __device__ __forceinline__ float project(const float* d, const float* v, float a0, float vsum, int n) {
+  if (NF == NM) {
+    float2 s01 = make_float2(0.0f, 0.0f), s23 = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int j4 = 0; j4 < NM / 4; ++j4) {
+      s01 = __ffma2_rn(make_float2(d[4 * j4 + 0], d[4 * j4 + 1]), make_float2(v[4 * j4 + 0], v[4 * j4 + 1]), s01);
+      s23 = __ffma2_rn(make_float2(d[4 * j4 + 2], d[4 * j4 + 3]), make_float2(v[4 * j4 + 2], v[4 * j4 + 3]), s23);
+    }
+    return __fmaf_rn(a0, vsum, __fadd_rn(__fadd_rn(s01.x, s01.y), __fadd_rn(s23.x, s23.y)));
+  }
   float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
 #pragma unroll
   for (int j4 = 0; j4 < NM / 4; ++j4) {
@@ -842,7 +854,7 @@ __device__ __forceinline__ float coeff_q(const TileSmem& S, const float* d, floa
     const float4 t = vp[j4];
     v[4 * j4 + 0] = t.x; v[4 * j4 + 1] = t.y; v[4 * j4 + 2] = t.z; v[4 * j4 + 3] = t.w;
   }
-  const float c = project(d, v, a0, S.vsum[k], n);
+  const float c = project<NF>(d, v, a0, S.vsum[k], n);
   q = quant_exact(c, rc.delta, rc.inv_delta, ovf);
   return __fmul_rn(__int2float_rn(q), rc.delta_f);
 }
@@ -855,13 +867,14 @@ __device__ __forceinline__ void shifted(const float* x, float* d) {
 // acc[j] <- fma(ch[k], Vst[j][k], acc[j]) for one k (decode contract order).
 __device__ __forceinline__ void row_decode_step(const TileSmem& S, int k, float chk, float* acc) {
   const float4* vp = reinterpret_cast<const float4*>(&S.VstT[k * NM]);
+  const float2 c2 = make_float2(chk, chk);
 #pragma unroll
   for (int j4 = 0; j4 < NM / 4; ++j4) {
     const float4 v = vp[j4];
-    acc[4 * j4 + 0] = __fmaf_rn(chk, v.x, acc[4 * j4 + 0]);
-    acc[4 * j4 + 1] = __fmaf_rn(chk, v.y, acc[4 * j4 + 1]);
-    acc[4 * j4 + 2] = __fmaf_rn(chk, v.z, acc[4 * j4 + 2]);
-    acc[4 * j4 + 3] = __fmaf_rn(chk, v.w, acc[4 * j4 + 3]);
+    const float2 a = __ffma2_rn(c2, make_float2(v.x, v.y), make_float2(acc[4 * j4 + 0], acc[4 * j4 + 1]));
+    const float2 b = __ffma2_rn(c2, make_float2(v.z, v.w), make_float2(acc[4 * j4 + 2], acc[4 * j4 + 3]));
+    acc[4 * j4 + 0] = a.x; acc[4 * j4 + 1] = a.y;
+    acc[4 * j4 + 2] = b.x; acc[4 * j4 + 3] = b.y;
   }
 }
 
@@ -932,7 +945,7 @@ __device__ __noinline__ bool pass_encode(const TileArgs& a, const Maps& tm, Tile
           const float4 t = vp[j4];
           v[4 * j4 + 0] = t.x; v[4 * j4 + 1] = t.y; v[4 * j4 + 2] = t.z; v[4 * j4 + 3] = t.w;
         }
-        const float cf = project(d, v, a0, S.vsum[k], n);
+        const float cf = project<NF>(d, v, a0, S.vsum[k], n);
         const int32_t q = quant_exact(cf, rq.delta, rq.inv_delta, ovf);
         if (valid) qs[k * Lq + l] = q;
         const uint32_t wor = __reduce_or_sync(FULL, valid ? zigzag(q) : 0u);
@@ -944,7 +957,13 @@ __device__ __noinline__ bool pass_encode(const TileArgs& a, const Maps& tm, Tile
             if (j < n) { const float dd = __fsub_rn(xr[j * rc], acc[j]); e1 = __fmaf_rn(dd, dd, e1); }
         }
 #pragma unroll
-        for (int j = 0; j < NM; ++j) acc[j] = __fmaf_rn(chk, v[j], acc[j]);
+        for (int j2 = 0; j2 < NM / 2; ++j2) {
+          // decode step, two elements per packed FMA (each as __fmaf_rn)
+          const float2 t = __ffma2_rn(make_float2(chk, chk), make_float2(v[2 * j2], v[2 * j2 + 1]),
+                                      make_float2(acc[2 * j2], acc[2 * j2 + 1]));
+          acc[2 * j2] = t.x;
+          acc[2 * j2 + 1] = t.y;
+        }
       }
       if (SPARSE && valid) {
         // elements with |fl(x - xhat)| < eb (rounded down) need no correction
