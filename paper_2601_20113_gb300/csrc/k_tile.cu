@@ -919,6 +919,7 @@ __device__ __noinline__ bool pass_encode(const TileArgs& a, const Maps& tm, Tile
   if (tid == 0) { S.kmax = 0; S.ncorr = 0; S.nesc = 0; }
   __syncthreads();
   float e1 = 0.0f, e2 = 0.0f;
+  float2 e1v = make_float2(0.0f, 0.0f), e2v = make_float2(0.0f, 0.0f);   // order 16: even / odd elements
   int nc = 0, ne = 0, ovf = 0;
   uint32_t kmx = 0;
   const int M = (int)g.M, Lq = (int)align_up(g.L, 4), rc = a.rc;
@@ -931,10 +932,24 @@ __device__ __noinline__ bool pass_encode(const TileArgs& a, const Maps& tm, Tile
       const float* xr = tile + (valid ? rr : 0);
       const float a0 = valid ? xr[0] : 0.0f;
       float d[NM], acc[NM];
+      // order 16: element pairs as packed FMAs; fma(a, -1, x) rounds as x - a
+      const float2 m1 = make_float2(-1.0f, -1.0f);
+      auto x2 = [&](int j2) { return make_float2(xr[2 * j2 * rc], xr[(2 * j2 + 1) * rc]); };
+      if (NF == NM && valid) {
 #pragma unroll
-      for (int j = 0; j < NM; ++j) {
-        d[j] = (valid && j < n) ? __fsub_rn(xr[j * rc], a0) : 0.0f;
-        acc[j] = 0.0f;
+        for (int j2 = 0; j2 < NM / 2; ++j2) {
+          const float2 t = __ffma2_rn(make_float2(a0, a0), m1, x2(j2));
+          d[2 * j2] = t.x;
+          d[2 * j2 + 1] = t.y;
+          acc[2 * j2] = 0.0f;
+          acc[2 * j2 + 1] = 0.0f;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < NM; ++j) {
+          d[j] = (valid && j < n) ? __fsub_rn(xr[j * rc], a0) : 0.0f;
+          acc[j] = 0.0f;
+        }
       }
 #pragma unroll 1
       for (int k = 0; k < r; ++k) {
@@ -952,9 +967,17 @@ __device__ __noinline__ bool pass_encode(const TileArgs& a, const Maps& tm, Tile
         if (lane == k) qor_lane |= wor;
         const float chk = __fmul_rn(__int2float_rn(q), rq.delta_f);
         if (check && k == r - 1 && valid) {
+          if (NF == NM) {
 #pragma unroll
-          for (int j = 0; j < NM; ++j)
-            if (j < n) { const float dd = __fsub_rn(xr[j * rc], acc[j]); e1 = __fmaf_rn(dd, dd, e1); }
+            for (int j2 = 0; j2 < NM / 2; ++j2) {
+              const float2 dd = __ffma2_rn(make_float2(acc[2 * j2], acc[2 * j2 + 1]), m1, x2(j2));
+              e1v = __ffma2_rn(dd, dd, e1v);
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < NM; ++j)
+              if (j < n) { const float dd = __fsub_rn(xr[j * rc], acc[j]); e1 = __fmaf_rn(dd, dd, e1); }
+          }
         }
 #pragma unroll
         for (int j2 = 0; j2 < NM / 2; ++j2) {
@@ -969,12 +992,22 @@ __device__ __noinline__ bool pass_encode(const TileArgs& a, const Maps& tm, Tile
         // elements with |fl(x - xhat)| < eb (rounded down) need no correction
         // (the first test of the decision); the others are decided one by one
         uint32_t cand = 0;
+        if (NF == NM) {
 #pragma unroll
-        for (int j = 0; j < NM; ++j) {
-          if (j < n) {
-            const float R = __fsub_rn(xr[j * rc], acc[j]);
-            if (check) e2 = __fmaf_rn(R, R, e2);
-            cand |= (fabsf(R) < cq.eb_lo_f ? 0u : 1u) << j;
+          for (int j2 = 0; j2 < NM / 2; ++j2) {
+            const float2 R = __ffma2_rn(make_float2(acc[2 * j2], acc[2 * j2 + 1]), m1, x2(j2));
+            if (check) e2v = __ffma2_rn(R, R, e2v);
+            cand |= (fabsf(R.x) < cq.eb_lo_f ? 0u : 1u) << (2 * j2);
+            cand |= (fabsf(R.y) < cq.eb_lo_f ? 0u : 1u) << (2 * j2 + 1);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < NM; ++j) {
+            if (j < n) {
+              const float R = __fsub_rn(xr[j * rc], acc[j]);
+              if (check) e2 = __fmaf_rn(R, R, e2);
+              cand |= (fabsf(R) < cq.eb_lo_f ? 0u : 1u) << j;
+            }
           }
         }
         uint32_t nzb = 0;
@@ -1075,6 +1108,8 @@ __device__ __noinline__ bool pass_encode(const TileArgs& a, const Maps& tm, Tile
     for (int w = 0; w < kWarps; ++w) o |= S.qor[w][tid];
     S.wq[tid] = tid < r ? bit_width(o) : 0;
   }
+  e1 = __fadd_rn(e1, __fadd_rn(e1v.x, e1v.y));
+  e2 = __fadd_rn(e2, __fadd_rn(e2v.x, e2v.y));
   const float ev[2] = {e1, e2};
   if (check) cta_reduce(S, ev, 2);
   else __syncthreads();

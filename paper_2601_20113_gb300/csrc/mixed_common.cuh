@@ -399,6 +399,19 @@ __device__ void jacobi_cta(float* A, float* V, double* lam, int n, float floor_a
       __syncthreads();
     }
     if (!any) break;
+    // after a sweep with rotations: stop if no pair is above its threshold
+    // now (the next sweep would rotate nothing), instead of running it
+    int above = 0;
+    for (int t = tid; t < n * (n - 1) / 2; t += NT) {
+      int i = 0, rem = t;
+      while (rem >= n - 1 - i) { rem -= n - 1 - i; ++i; }
+      const int j = i + 1 + rem;
+      const float app = A[i * NM + i], aqq = A[j * NM + j], apq = A[i * NM + j];
+      const float gpp = fabsf(app), gqq = fabsf(aqq);
+      const float thr = fmaxf(fmaxf(1.0e-7f * sqrtf(gpp * gqq), 4.0f * 5.9604645e-8f * fmaxf(gpp, gqq)), floor_abs);
+      if (fabsf(apq) > thr && apq != 0.0f) above = 1;
+    }
+    if (!__syncthreads_or(above)) break;
   }
   if (tid < n) lam[tid] = (double)A[tid * NM + tid];
   __syncthreads();
