@@ -266,7 +266,7 @@ def _config(form="learned"):
         nb *= -(-d // b)
     gib = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] * 4 / 2 ** 30
     return {"workload": f"modes3d {DIMS[0]}x{DIMS[1]}x{DIMS[2]} x {DIMS[3]} float32 ({gib:g} GiB), 64 modes "
-                        f"|k|<=8, k^-5/3, N(0,1e-3^2) noise, blocks 16^3x16 ({nb}), abs bound 1e-3 x range, "
+                        f"|k|<=8, k^-5/3, N(0,1e-3^2) noise, blocks 16^3x16 ({nb}), abs bound {REL_BOUND:g} x range, "
                         "rank cap 16",
             "form": FORM_TEXT[form],
             "l2": "inputs 4 GiB > 129 MB L2 (no flush)"}
@@ -282,10 +282,13 @@ def main():
     ap.add_argument("--dims", default=None, help="nx,ny,nz,nt override (profiling on a small case)")
     ap.add_argument("--form", default="learned", choices=sorted(FORMS))
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP64 form beside")
+    ap.add_argument("--rel", type=float, default=1e-3,
+                    help="absolute bound as a fraction of the value range (1e-2, 1e-3, 1e-4 in the at-scale config)")
     args = ap.parse_args()
+    global DIMS, REL_BOUND
     if args.dims:
-        global DIMS
         DIMS = tuple(int(v) for v in args.dims.split(","))
+    REL_BOUND = args.rel
     if args.impl == "reference":
         return run_reference(args)
 
