@@ -2025,9 +2025,12 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
     // block is encoded again into the CTA's scratch for the record writer here
     if (!raw && sparse && S.nesc > 0) {
       if (!encode(r, false, false, true)) break;
-    } else if (!raw && in_slot &&
-               (bit_width((uint32_t)S.kmax) > kDeferMaxWk || S.ncorr > slot_scratch(r, g.n, g.L, g.N).list_cap)) {
-      if (!encode(r, false, true, true)) break;
+    } else if (!raw && in_slot) {
+      // the layout's own choice: a dense record needs no entry list
+      const int wk = bit_width((uint32_t)S.kmax), ib = bit_width((uint32_t)(g.N - 1));
+      const bool dense = wk > 0 && (g.N * wk + 31) / 32 < ((int64_t)S.ncorr * (ib + wk) + 31) / 32;
+      if (wk > kDeferMaxWk || (!dense && S.ncorr > slot_scratch(r, g.n, g.L, g.N).list_cap))
+        if (!encode(r, false, true, true)) break;
     }
     const bool deferred = !raw && in_slot;
     // the next block's first chunks load while this record is packed
@@ -2090,7 +2093,7 @@ __global__ void __launch_bounds__(kTT, 6) k_pack_tile(Plan P, const BlockMeta* m
         const SlotScratch sc = slot_scratch(m.r, g.n, g.L, g.N);
         // a deferred record is one the tile kernel could defer: check before use
         if (!sc.fits || lay.size != m.nbytes || m.nesc != 0 || m.wk > kDeferMaxWk || m.r > g.n ||
-            m.ncorr > sc.list_cap) {
+            (!lay.dense && m.ncorr > sc.list_cap)) {
           atomicOr(&st->corrupt, 1u);
           sk = 1;
         }
