@@ -36,7 +36,9 @@ constexpr int kHalf = kNP / 2;            // pairs per thread group (68)
 constexpr int kBitsSmem = 8 * NM * NM;    // bitmap words kept in shared memory (2048)
 constexpr int kGT = kTT / 2;              // threads per Gram group
 constexpr unsigned FULL = 0xffffffffu;
-constexpr uint32_t kWaitLimit = 1u << 22;
+// Bound of every wait on an mbarrier, in SM clock cycles (about a second):
+// a poll can return at once, so a bound in polls would be far shorter.
+constexpr long long kWaitCycles = 1ll << 31;
 
 enum { kPhGram = 0, kPhJacobi, kPhRefine, kPhRR, kPhPredict, kPhEncode, kPhDecide, kPhSearch, kPhPack,
        kCntAccepted, kCntSearched, kCntExact, kPhTileWait, kCntTcGram, kPhases };
@@ -127,11 +129,15 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, unsigned pa
       : "memory");
   return ok != 0;
 }
-// Bounded wait: false after kWaitLimit polls.
+// Bounded wait: false after kWaitCycles (the clock is read every 1024 polls).
 __device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity) {
-  for (uint32_t i = 0; i < kWaitLimit; ++i)
-    if (mbar_try_wait(b, parity)) return true;
-  return false;
+  if (mbar_try_wait(b, parity)) return true;
+  const long long t0 = clock64();
+  for (;;) {
+    for (int i = 0; i < 1024; ++i)
+      if (mbar_try_wait(b, parity)) return true;
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
 }
 __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, unsigned long long* bar, int c0, int c1,
                                             int c2, int c3, int c4) {
