@@ -305,7 +305,7 @@ static int enqueue_compress(const Plan& P, const Layout& L, const void* d_in, vo
     if (ev1) CK(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
     if ((st = launch_scan(P, w, out_cap, d_out, s)) != DLS_OK) return st;
     if ((st = launch_compact(P, mw, d_out, s)) != DLS_OK) return st;
-    if ((st = launch_pack_tile(P, mw, d_out, s)) != DLS_OK) return st;
+    if ((st = launch_pack_tile(P, mw, d_in, d_out, s)) != DLS_OK) return st;
   } else {
     if (ev0) CK(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
     if ((st = launch_plain_compress(P, d_in, w, s)) != DLS_OK) return st;

@@ -240,7 +240,7 @@ int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, in
                          cudaStream_t s);
 bool tile_chunk_box(const Plan& p, int* bxb, int* yc, int* zc, int* bt);
 int launch_compact(const Plan& p, const MixedWork& w, void* d_out, cudaStream_t s);
-int launch_pack_tile(const Plan& p, const MixedWork& w, void* d_out, cudaStream_t s);
+int launch_pack_tile(const Plan& p, const MixedWork& w, const void* d_in, void* d_out, cudaStream_t s);
 size_t mixed_smem_bytes();
 int launch_mlp_train(float* params, float* adam, const float* feat, const float* target, const int32_t* order,
                      int64_t n_order, int steps, int B, float lr, int step0, float* loss, cudaStream_t s);

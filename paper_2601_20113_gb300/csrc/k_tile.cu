@@ -95,6 +95,9 @@ struct __align__(128) TileSmem {
   int wq[NM];
   uint32_t qor[kWarps][NM];
   int kmax, ncorr, nesc, ovf, nonfinite, abort_flag;
+  int nesc_slot;                  // escapes listed in the staging slot by the encode pass
+  uint32_t* esc_list;             // where (null: not listed), and how many fit
+  int esc_cap;
   int64_t bi, bnext;
   int r_pred;
   unsigned nexact;
@@ -218,6 +221,11 @@ __device__ __forceinline__ int row_index(const TileArgs& a, const Geom& g, const
 }
 
 // Global index of block entry (row l, column j) of a side-0 block.
+__device__ __forceinline__ int64_t gidx_plan(const Plan& P, const Geom& g, int64_t l, int j) {
+  const int64_t x = l % g.sx, r = l / g.sx;
+  const int64_t y = r % g.sy, z = r / g.sy;
+  return (int64_t)g.v * P.K + (g.t0 + j) * P.P + ((g.z0 + z) * P.dims[1] + (g.y0 + y)) * P.dims[0] + (g.x0 + x);
+}
 __device__ __forceinline__ int64_t gidx_row(const TileArgs& a, const Geom& g, int64_t l, int j) {
   const int64_t x = l % g.sx, r = l / g.sx;
   const int64_t y = r % g.sy, z = r / g.sy;
@@ -922,7 +930,7 @@ __device__ __noinline__ bool pass_encode(const TileArgs& a, const Maps& tm, Tile
   const RowConst rq = rcst;
   const CorrConst cq = cc;
   uint32_t qor_lane = 0;   // lane k: OR of zigzag(q) of column k over this warp's rows
-  if (tid == 0) { S.kmax = 0; S.ncorr = 0; S.nesc = 0; }
+  if (tid == 0) { S.kmax = 0; S.ncorr = 0; S.nesc = 0; S.nesc_slot = 0; }
   __syncthreads();
   float e1 = 0.0f, e2 = 0.0f;
   float2 e1v = make_float2(0.0f, 0.0f), e2v = make_float2(0.0f, 0.0f);   // order 16: even / odd elements
@@ -1016,7 +1024,7 @@ __device__ __noinline__ bool pass_encode(const TileArgs& a, const Maps& tm, Tile
             }
           }
         }
-        uint32_t nzb = 0;
+        uint32_t nzb = 0, escm = 0;
         while (cand) {
           const int jj = __ffs(cand) - 1;
           cand &= cand - 1;
@@ -1031,10 +1039,22 @@ __device__ __noinline__ bool pass_encode(const TileArgs& a, const Maps& tm, Tile
           const bool big = k < -127 || k > 127;            // includes escapes
           k8[e] = big ? (int8_t)-128 : (int8_t)k;
           if (big) k32[e] = k;
-          ne += k == kEscape ? 1 : 0;
+          escm |= (k == kEscape ? 1u : 0u) << jj;
           nc += k != 0 ? 1 : 0;
           kmx |= k == kEscape ? 0u : zigzag(k);
           nzb |= (k != 0 && k != kEscape ? 1u : 0u) << jj;
+        }
+        if (escm) {
+          // rare: the row's escapes, listed for the deferred packer (in no
+          // particular order)
+          ne += __popc(escm);
+          uint32_t* const el = S.esc_list;
+          if (el) {
+            for (uint32_t em = escm; em; em &= em - 1) {
+              const int i = atomicAdd(&S.nesc_slot, 1);
+              if (i < S.esc_cap) el[i] = (uint32_t)((__ffs(em) - 1) * M + l);
+            }
+          }
         }
         // lane j gets column j's word of the bitmap (this warp's 32 rows)
         const uint32_t mk = warp_transpose_bits(nzb, lane);
@@ -1585,9 +1605,10 @@ __device__ __forceinline__ void zero_padding(uint8_t* rec, const RecLayout& lay,
 // small next to n, and for the sparse entry list after them (list_cap
 // entries).
 struct SlotScratch {
-  int64_t off_q, off_bits, off_k8, end, off_list, list_cap;
+  int64_t off_q, off_bits, off_k8, end, off_esc, esc_cap, off_list, list_cap;
   bool fits;
 };
+constexpr int kMaxSlotEsc = 1024;             // escapes a deferred record can carry
 __host__ __device__ inline SlotScratch slot_scratch(int r, int n, int64_t L, int64_t N) {
   SlotScratch o;
   const int64_t off_pre = 16 + align_up(r, 8) + align_up((int64_t)n * r * 4, 8);   // the record's q offset
@@ -1595,8 +1616,11 @@ __host__ __device__ inline SlotScratch slot_scratch(int r, int n, int64_t L, int
   o.off_bits = o.off_q + (int64_t)r * align_up(L, 4) * 4;
   o.off_k8 = o.off_bits + align_up(N / 8, 16);
   o.end = o.off_k8 + align_up(N, 16);
-  o.off_list = o.end;
-  o.list_cap = o.end <= raw_record_bytes(N, 4) ? (raw_record_bytes(N, 4) - o.end) / 4 : 0;
+  const int64_t room = o.end <= raw_record_bytes(N, 4) ? (raw_record_bytes(N, 4) - o.end) / 4 : 0;
+  o.off_esc = o.end;
+  o.esc_cap = room < kMaxSlotEsc ? room / 4 * 4 : kMaxSlotEsc;
+  o.off_list = o.off_esc + o.esc_cap * 4;
+  o.list_cap = room - o.esc_cap;
   o.fits = r > 0 && N % 32 == 0 && N <= (int64_t)kBitsSmem * 32 && o.end <= raw_record_bytes(N, 4);
   return o;
 }
@@ -1967,15 +1991,19 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
       if (sp) {
         int32_t* q = qs;
         int8_t* k = k8;
+        uint32_t* esc = nullptr;
         const SlotScratch sc = slot_scratch(rr, g.n, g.L, g.N);
         if (!cta_scratch && sc.fits) {
           q = reinterpret_cast<int32_t*>(slot + sc.off_q);
           k = reinterpret_cast<int8_t*>(slot + sc.off_k8);
+          esc = reinterpret_cast<uint32_t*>(slot + sc.off_esc);
           in_slot = true;
         }
+        if (tid == 0) { S.esc_list = esc; S.esc_cap = (int)sc.esc_cap; }   // read after the pass's first barrier
         return full ? pass_encode<NM, true>(a, tm, S, cu, bi, g, rr, check, rcst, cc, pointwise, q, k, k32, bitp)
                     : pass_encode<0, true>(a, tm, S, cu, bi, g, rr, check, rcst, cc, pointwise, q, k, k32, bitp);
       }
+      if (tid == 0) S.esc_list = nullptr;
       return full ? pass_encode<NM, false>(a, tm, S, cu, bi, g, rr, check, rcst, cc, pointwise, qs, k8, k32, bitp)
                   : pass_encode<0, false>(a, tm, S, cu, bi, g, rr, check, rcst, cc, pointwise, qs, k8, k32, bitp);
     };
@@ -2025,18 +2053,20 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
       }
       mark(kPhSearch);
     }
-    // escapes are listed from k8 itself: a block that has any is encoded
-    // again with every element written; a deferred record has no correction
-    // beyond kDeferMaxWk bits and an entry list that fits its slot, else the
-    // block is encoded again into the CTA's scratch for the record writer here
-    if (!raw && sparse && S.nesc > 0) {
-      if (!encode(r, false, false, true)) break;
-    } else if (!raw && in_slot) {
+    // a deferred record has no correction beyond kDeferMaxWk bits, its
+    // escapes fit the slot's list and, when sparse, so does its entry list;
+    // otherwise the block is encoded again into the CTA's scratch for the
+    // record writer here, with every element written when it has escapes
+    // (the writer lists escapes from k8 itself)
+    if (!raw && in_slot) {
       // the layout's own choice: a dense record needs no entry list
       const int wk = bit_width((uint32_t)S.kmax), ib = bit_width((uint32_t)(g.N - 1));
       const bool dense = wk > 0 && (g.N * wk + 31) / 32 < ((int64_t)S.ncorr * (ib + wk) + 31) / 32;
-      if (wk > kDeferMaxWk || (!dense && S.ncorr > slot_scratch(r, g.n, g.L, g.N).list_cap))
-        if (!encode(r, false, true, true)) break;
+      const SlotScratch sc = slot_scratch(r, g.n, g.L, g.N);
+      if (wk > kDeferMaxWk || (!dense && S.ncorr > sc.list_cap) || S.nesc > sc.esc_cap)
+        if (!encode(r, false, S.nesc == 0, true)) break;
+    } else if (!raw && sparse && S.nesc > 0) {
+      if (!encode(r, false, false, true)) break;
     }
     const bool deferred = !raw && in_slot;
     // the next block's first chunks load while this record is packed
@@ -2080,12 +2110,14 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
 // CTAs per SM: the bit packing is short dependent chains, which a full SM of
 // warps overlaps.
 __global__ void __launch_bounds__(kTT, 6) k_pack_tile(Plan P, const BlockMeta* meta, uint8_t* staging,
-                                                      const unsigned long long* offsets, Status* st, uint8_t* out) {
+                                                      const unsigned long long* offsets, Status* st, uint8_t* out,
+                                                      const float* in) {
   __shared__ BlockMeta m;
   __shared__ RecLayout lay;
   __shared__ int64_t colbase[NM + 1];
   __shared__ int warp_cnt[kWarps];
   __shared__ __align__(16) uint32_t bitsm[kBitsSmem];
+  __shared__ uint32_t esc_in[kMaxSlotEsc], esc_sorted[kMaxSlotEsc];
   __shared__ int skip;
   if (st->capacity || st->nonfinite || st->timeout) return;
   const int tid = threadIdx.x;
@@ -2098,7 +2130,7 @@ __global__ void __launch_bounds__(kTT, 6) k_pack_tile(Plan P, const BlockMeta* m
         lay = rec_layout(m.r, g.n, g.L, g.N, 4, m.wq, m.wk, m.ib, m.ncorr, m.nesc);
         const SlotScratch sc = slot_scratch(m.r, g.n, g.L, g.N);
         // a deferred record is one the tile kernel could defer: check before use
-        if (!sc.fits || lay.size != m.nbytes || m.nesc != 0 || m.wk > kDeferMaxWk || m.r > g.n ||
+        if (!sc.fits || lay.size != m.nbytes || m.nesc > sc.esc_cap || m.wk > kDeferMaxWk || m.r > g.n ||
             (!lay.dense && m.ncorr > sc.list_cap)) {
           atomicOr(&st->corrupt, 1u);
           sk = 1;
@@ -2136,6 +2168,29 @@ __global__ void __launch_bounds__(kTT, 6) k_pack_tile(Plan P, const BlockMeta* m
         uint32_t* list = reinterpret_cast<uint32_t*>(slot + sc.off_list);
         bitmap_list(list, bitsm, g.N, m.ncorr, warp_cnt);
         pack_sparse<true>(cw, list, k8, nullptr, m.ib, m.wk, m.ncorr);
+      }
+    }
+    if (m.nesc > 0) {
+      // escapes were listed in no particular order: each goes to its rank
+      // among them (element order, the indices being distinct)
+      const int ne = m.nesc;
+      const uint32_t* el = reinterpret_cast<const uint32_t*>(slot + sc.off_esc);
+      for (int i = tid; i < ne; i += kTT) esc_in[i] = el[i];
+      __syncthreads();
+      for (int i = tid; i < ne; i += kTT) {
+        const uint32_t e = esc_in[i];
+        int rank = 0;
+        for (int j = 0; j < ne; ++j) rank += esc_in[j] < e ? 1 : 0;
+        esc_sorted[rank] = e;
+      }
+      __syncthreads();
+      uint32_t* ei = reinterpret_cast<uint32_t*>(rec + lay.off_ei);
+      float* ev = reinterpret_cast<float*>(rec + lay.off_ev);
+      for (int i = tid; i < ne; i += kTT) {
+        const uint32_t e = esc_sorted[i];
+        const int64_t lt = e / g.M, ls = e - lt * g.M;
+        ei[i] = e;
+        ev[i] = in[gidx_plan(P, g, ls, (int)lt)];
       }
     }
     __syncthreads();
@@ -2303,14 +2358,15 @@ int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, in
 }
 
 // The deferred records of a compression (after the scan has placed them).
-int launch_pack_tile(const Plan& p, const MixedWork& w, void* d_out, cudaStream_t s) {
+int launch_pack_tile(const Plan& p, const MixedWork& w, const void* d_in, void* d_out, cudaStream_t s) {
   if (p.nb == 0) return DLS_OK;
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return DLS_ERR_CUDA;
   const int64_t cap = (int64_t)sms * 6;
   const int grid = (int)(p.nb < cap ? p.nb : cap);
-  k_pack_tile<<<grid, kTT, 0, s>>>(p, w.meta, w.staging, w.offsets, w.status, (uint8_t*)d_out);
+  k_pack_tile<<<grid, kTT, 0, s>>>(p, w.meta, w.staging, w.offsets, w.status, (uint8_t*)d_out,
+                                   static_cast<const float*>(d_in));
   return cudaGetLastError() == cudaSuccess ? DLS_OK : DLS_ERR_CUDA;
 }
 
