@@ -409,6 +409,10 @@ __device__ void derived_stats(const TileArgs& a, TileSmem& S, const Geom& g, int
 // are first projected onto the current basis (Rayleigh-Ritz matrix).
 // NF = 16: the Gram order is 16 and known at compile time (no per-column
 // predicates); NF = 0: any order n <= 16.
+// Shifted projection of a row onto one basis column (defined with the encode pass).
+template <int NF>
+__device__ __forceinline__ float project(const float* d, const float* v, float a0, float vsum, int n);
+
 template <bool PROJECT, int NF>
 __device__ __noinline__ bool pass_gram(const TileArgs& a, const Maps& tm, TileSmem& S, Cursor& cu, int64_t bi,
                           const Geom& g) {
@@ -437,18 +441,24 @@ __device__ __noinline__ bool pass_gram(const TileArgs& a, const Maps& tm, TileSm
 #pragma unroll
       for (int j = 0; j < NM; ++j) x[j] = j < n ? tile[j * rc + r] : 0.0f;
       if (PROJECT) {
+        // the coefficients on the current basis, as the encode pass computes them
         const float a0 = x[0];
-        float cc[NM];
+        float d[NM], cc[NM];
+#pragma unroll
+        for (int j = 0; j < NM; ++j) d[j] = j < n ? __fsub_rn(x[j], a0) : 0.0f;
 #pragma unroll
         for (int k = 0; k < NM; ++k) {
-          float v = 0.0f;
+          cc[k] = 0.0f;
           if (k < n) {
+            float v[NM];
+            const float4* vp = reinterpret_cast<const float4*>(&S.VstT[k * NM]);
 #pragma unroll
-            for (int j = 0; j < NM; ++j)
-              if (j < n) v = __fmaf_rn(__fsub_rn(x[j], a0), S.VstT[k * NM + j], v);
-            v = __fmaf_rn(a0, S.vsum[k], v);
+            for (int j4 = 0; j4 < NM / 4; ++j4) {
+              const float4 t = vp[j4];
+              v[4 * j4 + 0] = t.x; v[4 * j4 + 1] = t.y; v[4 * j4 + 2] = t.z; v[4 * j4 + 3] = t.w;
+            }
+            cc[k] = project<NF>(d, v, a0, S.vsum[k], n);
           }
-          cc[k] = v;
         }
 #pragma unroll
         for (int k = 0; k < NM; ++k) x[k] = cc[k];
