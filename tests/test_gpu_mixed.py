@@ -265,3 +265,31 @@ def test_mixed_stream_is_deterministic():
     runs = [dls.compress(f, block=(16, 16, 16, 16), eb=eb, rank_cap=16, precision=dls.PREC_FP32,
                          rank_mode=dls.RANK_TAIL).cpu().numpy() for _ in range(3)]
     assert all(r.size == runs[0].size and np.array_equal(r, runs[0]) for r in runs[1:])
+
+
+def test_mixed_escapes_in_deferred_records():
+    """A full block whose record the deferred packer writes can carry escapes:
+    the encode pass lists them as it finds them, in no particular order, and
+    the packer writes them in element order with their raw values."""
+    dims = (32, 32, 16, 16)
+    f = torch.zeros((1, dims[3], dims[2], dims[1], dims[0]), dtype=torch.float32)
+    # four spikes in block 0 at different time steps: a rank-1 basis keeps
+    # the largest, the other three need more than 2^20 steps of 2 eb and
+    # escape; the field is zero elsewhere, so no correction widens the record
+    # beyond what the deferred packer takes
+    spikes = [((2, 3, 5, 7), 1.0e4), ((5, 11, 2, 9), 3.0e3), ((9, 4, 13, 1), 2.6e3), ((12, 8, 8, 14), 2.2e3)]
+    for (t, z, y, x), v in spikes:
+        f[0, t, z, y, x] = v
+    eb = 1e-3
+    fd = f.cuda()
+    comp = dls.compress(fd, block=(16, 16, 16, 16), eb=eb, rank_cap=1, precision=dls.PREC_FP32,
+                        rank_mode=dls.RANK_SEARCH)
+    esc = _record_escapes(comp)
+    assert esc[0] == 3 and sum(esc[1:]) == 0, esc
+    rec = dls.decompress(comp)
+    assert (rec.double() - fd.double()).abs().max().item() <= eb
+    for (t, z, y, x), v in spikes[1:]:
+        assert rec[0, t, z, y, x].item() == v
+    st, rref = oracle.decompress(comp.cpu().numpy())
+    assert st == oracle.OK
+    assert np.array_equal(rref.astype(np.float32), rec.cpu().numpy())
