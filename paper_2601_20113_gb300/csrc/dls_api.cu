@@ -316,6 +316,72 @@ static int enqueue_compress(const Plan& P, const Layout& L, const void* d_in, vo
   return DLS_OK;
 }
 
+// Host-buffer compression with the copy of each slab of the field overlapped
+// with the compression of the slabs before it.  Blocks are ordered (variable,
+// time block, z, y, x) and the field (variable, t, z, y, x), so the blocks of
+// one slab of block[3] time steps of one variable are a contiguous range and
+// their values a contiguous byte range.  Taken for the mixed forms with an
+// absolute bound (no pass over the whole field first) whose blocks all go
+// through the tile kernel, over the whole block range.
+static bool host_pipelined(const Plan& P, const Layout& L) {
+  return L.mixed && P.eb_type == DLS_EB_ABS && !mixed_route(P).legacy && P.b0 == 0 && P.nb == P.nb_total &&
+         P.nvars * P.nbk[3] >= 2;
+}
+static int compress_host_pipelined(const Plan& P, const Layout& L, const void* h_in, uint8_t* d_in,
+                                   uint8_t* d_out, size_t bound, uint8_t* d_ws, cudaStream_t s, size_t* nb_out) {
+  int st;
+  Work w = carve(L, d_ws);
+  const MixedWork mw = mixed_work(P, L, d_ws);
+  const int mode = P.rank_mode == DLS_RANK_LEARNED ? kRankMlp : (P.rank_mode == DLS_RANK_TAIL ? kRankTail : kRankSearch);
+  const int64_t nseg = (int64_t)P.nvars * P.nbk[3];
+  const int64_t nbs = P.nbk[0] * P.nbk[1] * P.nbk[2];      // blocks of one slab
+  const size_t es = (size_t)esize(P.dtype);
+  cudaStream_t cs = nullptr;
+  cudaEvent_t* ev = new cudaEvent_t[nseg]();
+  auto done = [&](int rc) {
+    for (int64_t k = 0; k < nseg; ++k)
+      if (ev[k]) cudaEventDestroy(ev[k]);
+    delete[] ev;
+    if (cs) cudaStreamDestroy(cs);
+    return rc;
+  };
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return done(DLS_ERR_CUDA);
+  for (int64_t k = 0; k < nseg; ++k)
+    if (cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming) != cudaSuccess) return done(DLS_ERR_CUDA);
+  // the copies, slab by slab, on their own stream
+  for (int64_t k = 0; k < nseg; ++k) {
+    const int64_t v = k / P.nbk[3], tb = k % P.nbk[3];
+    const int64_t t0 = tb * P.block[3], t1 = (t0 + P.block[3]) < P.dims[3] ? t0 + P.block[3] : P.dims[3];
+    const size_t off = (size_t)(v * P.K + t0 * P.P) * es, len = (size_t)((t1 - t0) * P.P) * es;
+    if (cudaMemcpyAsync(d_in + off, (const uint8_t*)h_in + off, len, cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+        cudaEventRecord(ev[k], cs) != cudaSuccess)
+      return done(DLS_ERR_CUDA);
+  }
+  // the compression: each slab's blocks once its copy has landed
+  if (cudaMemsetAsync(w.status, 0, sizeof(Status), s) != cudaSuccess) return done(DLS_ERR_CUDA);
+  if ((st = launch_stats_resolve(P, d_in, w, (double*)(d_ws + L.partial), s)) != DLS_OK) return done(st);
+  if (cudaMemsetAsync(mw.phase, 0, sizeof(unsigned long long) * (size_t)L.ctas * kMixedPhases, s) != cudaSuccess)
+    return done(DLS_ERR_CUDA);
+  for (int64_t k = 0; k < nseg; ++k) {
+    if (cudaStreamWaitEvent(s, ev[k], 0) != cudaSuccess ||
+        cudaMemsetAsync(&w.status->pad[1], 0, sizeof(unsigned long long), s) != cudaSuccess)
+      return done(DLS_ERR_CUDA);
+    if ((st = launch_tile_compress(P, d_in, mw, mode, 2, s, k * nbs, (k + 1) * nbs)) != DLS_OK) return done(st);
+  }
+  if ((st = launch_scan(P, w, bound, d_out, s)) != DLS_OK) return done(st);
+  if ((st = launch_compact(P, mw, d_out, s)) != DLS_OK) return done(st);
+  if ((st = launch_pack_tile(P, mw, d_in, d_out, s)) != DLS_OK) return done(st);
+  Status hs;
+  if (cudaMemcpyAsync(&hs, w.status, sizeof(Status), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return done(DLS_ERR_CUDA);
+  if (hs.timeout) return done(DLS_ERR_TIMEOUT);
+  if (hs.nonfinite) return done(DLS_ERR_NONFINITE);
+  *nb_out = (size_t)hs.total_bytes;
+  if (hs.capacity) return done(DLS_ERR_CAPACITY);
+  return done(hs.corrupt ? DLS_ERR_CORRUPT : DLS_OK);
+}
+
 }  // namespace dls
 
 // ---------------------------------------------------------------- plans: autotune + CUDA graph
@@ -464,9 +530,15 @@ int dls_compress_host(const dls_params* p, const void* h_in, void* h_out, size_t
   if (staging_bytes < in + out + ws) return DLS_ERR_WORKSPACE;
   uint8_t* base = (uint8_t*)d_staging;
   cudaStream_t s = (cudaStream_t)stream;
-  CK(cudaMemcpyAsync(base, h_in, inb, cudaMemcpyHostToDevice, s));
   size_t nb = 0;
-  st = dls_compress(p, base, base + in, bound, &nb, base + in + out, ws, stream);
+  const Layout L = work_layout(P);
+  if (host_pipelined(P, L)) {
+    if (L.mixed && P.rank_mode == DLS_RANK_LEARNED && !rank_model_loaded()) return DLS_ERR_NO_MODEL;
+    st = compress_host_pipelined(P, L, h_in, base, base + in, bound, base + in + out, s, &nb);
+  } else {
+    CK(cudaMemcpyAsync(base, h_in, inb, cudaMemcpyHostToDevice, s));
+    st = dls_compress(p, base, base + in, bound, &nb, base + in + out, ws, stream);
+  }
   *out_bytes = nb;
   if (st != DLS_OK) return st;
   if (nb > out_cap) return DLS_ERR_CAPACITY;

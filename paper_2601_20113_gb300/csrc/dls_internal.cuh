@@ -237,7 +237,7 @@ constexpr int kRankSearch = 0, kRankMlp = 1, kRankTail = 2;
 int launch_mixed_compress(const Plan& p, const void* d_in, const MixedWork& w, int learned, int variant,
                           int spatial_only, cudaStream_t s);
 int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, int learned, int variant,
-                         cudaStream_t s);
+                         cudaStream_t s, int64_t blo = 0, int64_t bhi = -1);
 bool tile_chunk_box(const Plan& p, int* bxb, int* yc, int* zc, int* bt);
 int launch_compact(const Plan& p, const MixedWork& w, void* d_out, cudaStream_t s);
 int launch_pack_tile(const Plan& p, const MixedWork& w, const void* d_in, void* d_out, cudaStream_t s);

@@ -67,6 +67,7 @@ struct TileArgs {
   uint32_t mbx, myc;       // ceil(2^32 / bxb), ceil(2^32 / yc) (0 for a divisor of 1)
   int tc_gram;             // 1: Gram pass on the tensor cores (3xTF32), chunk box 16 x 16 x 1 x 16
   double jfloor;           // Jacobi skip floor as a fraction of the per-mode budget
+  int64_t blo, bhi;        // the blocks [blo, bhi) of the plan this launch compresses
 };
 
 struct __align__(128) TileSmem {
@@ -1863,8 +1864,8 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
   // blocks whose Gram side is time; the others are left to k_mixed
   auto grab = [&]() -> int64_t {
     for (;;) {
-      const int64_t b = (int64_t)atomicAdd(&a.status->pad[1], 1ull);
-      if (b >= P.nb) return P.nb;
+      const int64_t b = a.blo + (int64_t)atomicAdd(&a.status->pad[1], 1ull);
+      if (b >= a.bhi) return a.bhi;
       if (block_geom(P, P.b0 + b).side == 0) return b;
     }
   };
@@ -1875,7 +1876,7 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
   for (;;) {
     const int64_t bi = S.bnext;
     __syncthreads();
-    if (bi >= P.nb) break;
+    if (bi >= a.bhi) break;
     if (tid == 0) S.bnext = grab();
     const Geom g = block_geom(P, P.b0 + bi);
     const VarInfo vi = a.vars[g.v];
@@ -2082,7 +2083,7 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
     // the next block's first chunks load while this record is packed
     {
       const int64_t bn = S.bnext;
-      if (bn < P.nb) prefetch(a, tm, S, cu, bn, block_geom(P, P.b0 + bn), TC ? kLayoutGram : kLayoutRow);
+      if (bn < a.bhi) prefetch(a, tm, S, cu, bn, block_geom(P, P.b0 + bn), TC ? kLayoutGram : kLayoutRow);
     }
     if (deferred) defer_record(a, S, g, bi, r, bitp);
     else write_record(a, S, g, bi, raw, r, qs, k8, k32, bitp);
@@ -2284,11 +2285,15 @@ int tile_ctas_per_sm(int variant, bool tc) {
 }
 
 int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, int learned, int variant,
-                         cudaStream_t s) {
-  if (p.nb == 0) return DLS_OK;
+                         cudaStream_t s, int64_t blo, int64_t bhi) {
+  if (bhi < 0) bhi = p.nb;
+  if (blo < 0 || blo > bhi || bhi > p.nb) return DLS_ERR_INVALID_ARG;
+  if (bhi == blo) return DLS_OK;
   TileArgs a;
   memset(&a, 0, sizeof(a));
   a.P = p;
+  a.blo = blo;
+  a.bhi = bhi;
   a.in = (const float*)d_in;
   a.staging = w.staging;
   a.meta = w.meta;
@@ -2355,7 +2360,7 @@ int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, in
   if (per_sm < 1) return DLS_ERR_CUDA;
   int ctas = sms * per_sm;
   if (ctas > w.ctas) ctas = w.ctas;
-  if ((int64_t)ctas > p.nb) ctas = (int)p.nb;
+  if ((int64_t)ctas > bhi - blo) ctas = (int)(bhi - blo);
   const size_t smem = tile_smem_bytes(a.tc_gram != 0);
   if (a.tc_gram) {
     if (variant == 1) k_tile<2, true><<<ctas, kTT, smem, s>>>(tmap, tmapg, a);

@@ -293,3 +293,25 @@ def test_mixed_escapes_in_deferred_records():
     st, rref = oracle.decompress(comp.cpu().numpy())
     assert st == oracle.OK
     assert np.array_equal(rref.astype(np.float32), rec.cpu().numpy())
+
+
+@pytest.mark.parametrize("nvars,eb_type", [(1, dls.EB_ABS), (2, dls.EB_ABS), (2, dls.EB_REL_RANGE)])
+def test_host_entry_matches_device_entry(nvars, eb_type):
+    """dls_compress_host on pinned host buffers gives the device entry's stream
+    byte for byte.  With an absolute bound the copy of each (variable, time
+    block) slab overlaps the compression of the slabs before it; a bound
+    relative to the range needs the whole field first."""
+    dims = (64, 64, 32, 48)                         # three time blocks of 16
+    f = torch.cat([synth.modes3d(*dims, seed=11 + v, count=24) for v in range(nvars)], 0).contiguous()
+    eb = 1e-3 * float(f.max() - f.min()) if eb_type == dls.EB_ABS else 1e-3
+    ref = dls.compress(f.cuda(), block=(16, 16, 16, 16), eb=eb, eb_type=eb_type, rank_cap=16,
+                       precision=dls.PREC_FP32, rank_mode=dls.RANK_SEARCH).cpu().numpy()
+    p = dls.make_params(tuple(f.shape), torch.float32, (16, 16, 16, 16), eb, eb_type, 16,
+                        precision=dls.PREC_FP32, rank_mode=dls.RANK_SEARCH)
+    h_in = f.pin_memory()
+    h_out = torch.empty(dls.compress_bound(p), dtype=torch.uint8).pin_memory()
+    staging = torch.empty(dls.host_staging_size(p), dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        st, nb = dls.compress_host_into(p, h_in, h_out, staging)
+        assert st == 0
+        assert nb == ref.size and np.array_equal(h_out[:nb].numpy(), ref)
