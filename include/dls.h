@@ -147,6 +147,10 @@ size_t dls_host_staging_size(const dls_params* p);
 
 /* End-to-end compression of a HOST field (host in, host stream out): copies
  * h_in to the device, runs dls_compress, copies the stream back to h_out.
+ * The stream equals dls_compress's.  For the FP32/TF32X3 forms with an
+ * absolute bound, the field is copied one slab of block[3] time steps of one
+ * variable at a time on an internal stream, each slab's blocks compressed as
+ * soon as it has landed (so the copy hides most of the compression).
  * Pinned host memory (cudaHostAlloc) gives full copy bandwidth; pageable
  * memory works but is slower.  d_staging: staging_bytes >= dls_host_staging_size(p),
  * 256-byte aligned, owned by the caller.  out_cap bounds the host output.
