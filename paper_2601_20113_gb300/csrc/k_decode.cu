@@ -33,17 +33,32 @@ __device__ __forceinline__ uint32_t get_bits(const uint32_t* w, uint64_t pos, in
   return (uint32_t)(v & (width == 32 ? 0xffffffffull : ((1ull << width) - 1)));
 }
 
+// Field offset of a block's spatial point ls (x fastest) without the time
+// step: 32-bit division (a block's extents are small), once per point.
+__device__ __forceinline__ int64_t spatial_off(const Plan& p, const Geom& g, int ls) {
+  const int sx = g.sx, sxy = g.sx * g.sy;
+  const int lz = ls / sxy, rxy = ls - lz * sxy;
+  const int ly = rxy / sx, lx = rxy - ly * sx;
+  return (int64_t)g.v * p.K + (g.z0 + lz) * (p.dims[0] * p.dims[1]) + (g.y0 + ly) * p.dims[0] + (g.x0 + lx);
+}
+// elem_index (block element e = t_local * M + s_local) the same way.
+__device__ __forceinline__ int64_t elem_off(const Plan& p, const Geom& g, int64_t e) {
+  const int64_t lt = e / g.M;
+  return spatial_off(p, g, (int)(e - lt * g.M)) + (g.t0 + lt) * p.P;
+}
+
 template <typename T, int NM>
 __global__ void __launch_bounds__(kDecThreads) k_decode(Plan P, const uint8_t* __restrict__ comp,
                                                         unsigned long long comp_bytes, T* __restrict__ out,
                                                         Status* st) {
   __shared__ T vst[NM * NM];
   __shared__ int64_t wbase[NM + 1];
+  __shared__ int64_t soff_col[NM];   // spatial-side blocks: field offset of column j (time 0)
   __shared__ int bad;
   const int64_t bi = blockIdx.x;
   const int tid = threadIdx.x;
   const Geom g = block_geom(P, P.b0 + bi);
-  const int64_t N = g.N, L = g.L, M = g.M;
+  const int64_t N = g.N, L = g.L;
   const int n = g.n;
   const int es = (int)sizeof(T);
   const uint64_t* offs = reinterpret_cast<const uint64_t*>(comp + P.offsets_pos);
@@ -66,10 +81,7 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(Plan P, const uint8_t* _
       return;
     }
     const T* vals = reinterpret_cast<const T*>(rec + 16);
-    for (int64_t e = tid; e < N; e += kDecThreads) {
-      const int64_t lt = e / M, ls = e - lt * M;
-      out[elem_index(P, g, ls, lt)] = vals[e];
-    }
+    for (int64_t e = tid; e < N; e += kDecThreads) out[elem_off(P, g, e)] = vals[e];
     return;
   }
   const int rcap = P.rank_cap < n ? P.rank_cap : n;
@@ -106,11 +118,14 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(Plan P, const uint8_t* _
     const int c = i / n, j = i - c * n;
     vst[j * NM + c] = vin[i];
   }
+  if (g.side == 1 && tid < n) soff_col[tid] = spatial_off(P, g, tid);
   __syncthreads();
   const uint32_t* qw = reinterpret_cast<const uint32_t*>(rec + lay.off_q);
   const uint32_t* cw = reinterpret_cast<const uint32_t*>(rec + lay.off_c);
   const bool dense = lay.dense && wk > 0;
   for (int64_t l = tid; l < L; l += kDecThreads) {
+    // row l's field offset: a spatial point (time side) or a time step (spatial side)
+    const int64_t row_off = g.side == 0 ? spatial_off(P, g, (int)l) + g.t0 * P.P : (g.t0 + l) * P.P;
     T ch[NM];
 #pragma unroll
     for (int c = 0; c < NM; ++c) {
@@ -121,9 +136,11 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(Plan P, const uint8_t* _
         ch[c] = T(0);
       }
     }
-#pragma unroll
-    for (int j = 0; j < NM; ++j) {
-      if (j < n) {
+    // one output at a time: unrolled over j, the basis (loop-invariant over
+    // rows) would be held in registers, a CTA per SM
+#pragma unroll 1
+    for (int j = 0; j < n; ++j) {
+      {
         T acc = T(0);
 #pragma unroll
         for (int c = 0; c < NM; ++c)
@@ -133,7 +150,7 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(Plan P, const uint8_t* _
           const int32_t kv = unzigzag(get_bits(cw, (uint64_t)e * wk, wk));
           if (kv != 0) acc = tf<T>((T)kv, step_t, acc);
         }
-        out[a_index(P, g, l, j)] = acc;
+        out[row_off + (g.side == 0 ? (int64_t)j * P.P : soff_col[j])] = acc;
       }
     }
   }
@@ -144,8 +161,7 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(Plan P, const uint8_t* _
       const int64_t e = get_bits(cw, pos, ib);
       const int32_t kv = unzigzag(get_bits(cw, pos + ib, wk));
       if (e >= N) { atomicOr(&st->corrupt, 1u); continue; }
-      const int64_t lt = e / M, ls = e - lt * M;
-      const int64_t gi = elem_index(P, g, ls, lt);
+      const int64_t gi = elem_off(P, g, e);
       out[gi] = tf<T>((T)kv, step_t, out[gi]);
     }
   }
@@ -156,8 +172,7 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(Plan P, const uint8_t* _
     for (int64_t i = tid; i < nesc; i += kDecThreads) {
       const int64_t e = ei[i];
       if (e >= N) { atomicOr(&st->corrupt, 1u); continue; }
-      const int64_t lt = e / M, ls = e - lt * M;
-      out[elem_index(P, g, ls, lt)] = ev[i];
+      out[elem_off(P, g, e)] = ev[i];
     }
   }
 }
