@@ -1086,8 +1086,10 @@ extern "C" int dls_set_rank_model(const float* h_params, size_t count) {
     m.W3[h] = r(h_params[kMlpOffW3 + h]);
   }
   m.b3 = r(h_params[kMlpOffB3]);
-  for (int i = 0; i < kMlpH * kMlpF; ++i) m.W1[i] = __float2bfloat16_rn(h_params[kMlpOffW1 + i]);
-  for (int i = 0; i < kMlpH * kMlpH; ++i) m.W2[i] = __float2bfloat16_rn(h_params[kMlpOffW2 + i]);
+  for (int h = 0; h < kMlpH; ++h) {
+    for (int f = 0; f < kMlpF; ++f) m.W1t[f * kMlpH + h] = __float2bfloat16_rn(h_params[kMlpOffW1 + h * kMlpF + f]);
+    for (int k = 0; k < kMlpH; ++k) m.W2t[k * kMlpH + h] = __float2bfloat16_rn(h_params[kMlpOffW2 + h * kMlpH + k]);
+  }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DLS_ERR_CUDA;
   if (cudaMemcpyToSymbol(g_rank_model, &m, sizeof(m)) != cudaSuccess) return DLS_ERR_CUDA;

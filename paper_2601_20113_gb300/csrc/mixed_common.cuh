@@ -124,10 +124,13 @@ static __device__ __noinline__ int32_t corr_slow(float x, float xh, const CorrCo
 
 // ---------------------------------------------------------------- rank model
 // The trained block-rank MLP as the kernels read it (set by dls_set_rank_model).
+// The two hidden layers' weights are stored transposed (W1t[f * kMlpH + h] =
+// W1[h][f], W2t[k * kMlpH + h] = W2[h][k]) so that the 32 lanes of a warp, one
+// output h each, read 64 consecutive bytes per input index.
 struct MlpModel {
   float mu[kMlpF], sig[kMlpF];
   float b1[kMlpH], b2[kMlpH], W3[kMlpH], b3;
-  __nv_bfloat16 W1[kMlpH * kMlpF], W2[kMlpH * kMlpH];
+  __nv_bfloat16 W1t[kMlpF * kMlpH], W2t[kMlpH * kMlpH];
 };
 
 // Device copy of the model for the current device (null if none was set).
@@ -141,8 +144,9 @@ __device__ __forceinline__ int mlp_rank_warp(const MlpModel* M, const float* fea
   for (int hh = 0; hh < 2; ++hh) {
     const int h = lane + 32 * hh;
     float acc = M->b1[h];
+#pragma unroll 8
     for (int f = 0; f < kMlpF; ++f)
-      acc = fmaf(__bfloat162float(M->W1[h * kMlpF + f]), __shfl_sync(0xffffffffu, z, f), acc);
+      acc = fmaf(__bfloat162float(M->W1t[f * kMlpH + h]), __shfl_sync(0xffffffffu, z, f), acc);
     h1[h] = acc > 0.0f ? acc : 0.0f;
   }
   __syncwarp();
@@ -150,7 +154,8 @@ __device__ __forceinline__ int mlp_rank_warp(const MlpModel* M, const float* fea
   for (int hh = 0; hh < 2; ++hh) {
     const int h = lane + 32 * hh;
     float acc = M->b2[h];
-    for (int k = 0; k < kMlpH; ++k) acc = fmaf(__bfloat162float(M->W2[h * kMlpH + k]), h1[k], acc);
+#pragma unroll 8
+    for (int k = 0; k < kMlpH; ++k) acc = fmaf(__bfloat162float(M->W2t[k * kMlpH + h]), h1[k], acc);
     acc = acc > 0.0f ? acc : 0.0f;
     out = fmaf(M->W3[h], acc, out);
   }
