@@ -70,6 +70,12 @@ struct TileArgs {
   int64_t blo, bhi;        // the blocks [blo, bhi) of the plan this launch compresses
 };
 
+// Quantization constants of one variable (delta, and 1 / delta and delta in FP32).
+struct RowConst {
+  double delta;
+  float inv_delta, delta_f;
+};
+
 struct __align__(128) TileSmem {
   float ring[kStages][kStageFloats];
   unsigned long long full[kStages];
@@ -113,6 +119,12 @@ struct __align__(128) TileSmem {
   uint32_t tmem_base;             // TMEM columns of this CTA (tensor-core Gram)
   BlockMeta m;
   RecLayout lay;
+  // the current variable's constants (thread 0 recomputes them when a block
+  // of another variable starts) and the eigenvalue sum
+  int cvar;
+  RowConst crc;
+  CorrConst ccc;
+  double lam_tr;
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -832,11 +844,6 @@ __device__ void order_basis(TileSmem& S, int n, int lane) {
 }
 
 // ---------------------------------------------------------------- row arithmetic
-struct RowConst {
-  double delta;
-  float inv_delta, delta_f;
-};
-
 // Coefficient k of one row (shifted projection: sum_j (x_j - x_0) Vst[j][k]
 // + x_0 sum_j Vst[j][k], the differences exact when the row carries a large
 // common part), quantized with FP64 semantics and dequantized in float.
@@ -1871,7 +1878,7 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
   };
   Cursor cu;
   cu.iss = 0; cu.con = 0; cu.pf_blk = -1; cu.pf_cnt = 0; cu.pf_layout = kLayoutRow;
-  if (tid == 0) S.bnext = grab();
+  if (tid == 0) { S.bnext = grab(); S.cvar = -1; }
   __syncthreads();
   for (;;) {
     const int64_t bi = S.bnext;
@@ -1883,15 +1890,21 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
     const int n = g.n;
     const int rcap = P.rank_cap < n ? P.rank_cap : n;
     const bool pointwise = P.eb_type != DLS_EB_NRMSE;
-    RowConst rcst;
-    rcst.delta = vi.delta;
-    rcst.inv_delta = __double2float_rn(1.0 / vi.delta);
-    rcst.delta_f = __double2float_rn(vi.delta);
-    const CorrConst cc = make_corr_const(vi.eb, vi.step, pointwise);
     const double el2 = (P.eb_type == DLS_EB_NRMSE) ? (vi.eb * vi.eb) * ((double)g.N / (double)P.K)
                                                    : (vi.eb * vi.eb) * (double)g.N;
-    if (tid == 0) { S.nonfinite = 0; S.ovf = 0; }
+    if (tid == 0) {
+      S.nonfinite = 0; S.ovf = 0;
+      if (S.cvar != g.v) {
+        S.cvar = g.v;
+        S.crc.delta = vi.delta;
+        S.crc.inv_delta = __double2float_rn(1.0 / vi.delta);
+        S.crc.delta_f = __double2float_rn(vi.delta);
+        S.ccc = make_corr_const(vi.eb, vi.step, pointwise);
+      }
+    }
     __syncthreads();
+    const RowConst rcst = S.crc;
+    const CorrConst cc = S.ccc;
 
     if (tid == 0) tck = clock64();
     const bool full = n == NM;   // Gram order 16: the passes without per-column predicates
@@ -1916,15 +1929,22 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
     jacobi_tile(S, n, jfloor);
     mark(kPhJacobi);
     refine64(S, n);
-    if (warp == 0) order_basis(S, n, lane);
+    if (warp == 0) {
+      order_basis(S, n, lane);
+      __syncwarp();
+      if (lane == 0) {
+        double tr = 0.0;
+        for (int i = 0; i < n; ++i) tr += S.lam[i];
+        S.lam_tr = tr;
+      }
+    }
     __syncthreads();
     mark(kPhRefine);
     // Tight bounds need the modes an FP32 Gram cannot resolve (eigenvalues near
     // 2^-24 trace G): one Rayleigh-Ritz step on the projected data fixes them,
     // when that resolution reaches half the per-mode budget eb^2 L.
     {
-      double tr = 0.0;
-      for (int i = 0; i < n; ++i) tr += S.lam[i];
+      const double tr = S.lam_tr;
       const double budget = (vi.eb * vi.eb) * (double)g.L;
       const double noise = (P.eb_type == DLS_EB_NRMSE ? el2 / n : budget);
       if (n > 1 && 4.0 * 5.9604644775390625e-8 * tr > 0.5 * noise) {
