@@ -94,6 +94,19 @@ typedef struct {
   int32_t rank_mode;      /* DLS_RANK_* */
   int64_t block_begin;    /* compress blocks [block_begin, block_end) only; */
   int64_t block_end;      /* block_end < 0 means through the last block      */
+  /* Fixed basis (Sec. 4: data-adaptive SVD modes against fixed cosine or
+   * random modes).  Null: every block uses its own eigenvectors (the method).
+   * Otherwise a host array of basis_n x basis_n doubles, basis[a * basis_n + k]
+   * = component a of mode k, the columns orthonormal to 1e-12: blocks whose
+   * Gram order equals basis_n project on these modes, in the given order,
+   * instead of their own; other blocks are unchanged.  Requires
+   * DLS_PREC_FP64 and DLS_RANK_SEARCH (else DLS_ERR_INVALID_ARG), as does a
+   * basis_n outside [1, 32] or a basis that is not orthonormal.  Every record
+   * stores its modes, so decompression needs nothing more.  dls_compress
+   * copies the array on each call (it may be freed on return); a plan copies
+   * it once, at dls_plan_create, into its workspace. */
+  const double* basis;
+  int32_t basis_n;
 } dls_params;
 
 /* Worst-case stream size for these parameters (each record is at most the

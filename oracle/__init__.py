@@ -53,6 +53,8 @@ class Params(C.Structure):
         ("rank_cap", C.c_int32),
         ("block_begin", C.c_int64),
         ("block_end", C.c_int64),
+        ("basis", C.POINTER(C.c_double)),
+        ("basis_n", C.c_int32),
     ]
 
 
@@ -131,7 +133,7 @@ class Config:
     bound type and rank cap."""
 
     def __init__(self, dims, block, dtype, eb, eb_type=EB_ABS, rank_cap=32, nvars=1,
-                 block_begin=0, block_end=-1):
+                 block_begin=0, block_end=-1, basis=None):
         self.dims = tuple(int(d) for d in dims)
         self.block = tuple(int(b) for b in block)
         self.dtype = int(dtype)
@@ -141,6 +143,10 @@ class Config:
         self.nvars = int(nvars)
         self.block_begin = int(block_begin)
         self.block_end = int(block_end)
+        # fixed basis (Sec. 4): n x n, column k = mode k, for blocks of Gram order n
+        self.basis = None if basis is None else np.ascontiguousarray(basis, dtype=np.float64)
+        if self.basis is not None and (self.basis.ndim != 2 or self.basis.shape[0] != self.basis.shape[1]):
+            raise ValueError("basis must be a square matrix")
 
     def c(self) -> Params:
         p = Params()
@@ -154,6 +160,9 @@ class Config:
         p.rank_cap = self.rank_cap
         p.block_begin = self.block_begin
         p.block_end = self.block_end
+        if self.basis is not None:
+            p.basis = _p(self.basis, C.c_double)
+            p.basis_n = self.basis.shape[0]
         return p
 
 

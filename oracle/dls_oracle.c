@@ -95,6 +95,20 @@ int or_validate(const or_params* p) {
   int64_t nb = or_num_blocks(p);
   int64_t e = p->block_end < 0 ? nb : p->block_end;
   if (p->block_begin < 0 || p->block_begin > e || e > nb) return OR_ERR_INVALID_ARG;
+  if (p->basis) {
+    /* a fixed basis: order 1..32, finite, orthonormal columns to 1e-12 */
+    int bn = p->basis_n;
+    if (bn < 1 || bn > 32) return OR_ERR_INVALID_ARG;
+    for (int i = 0; i < bn; ++i)
+      for (int j = 0; j < bn; ++j) {
+        double d = 0.0;
+        for (int a = 0; a < bn; ++a) {
+          if (!isfinite(p->basis[a * bn + i])) return OR_ERR_INVALID_ARG;
+          d += p->basis[a * bn + i] * p->basis[a * bn + j];
+        }
+        if (fabs(d - (i == j ? 1.0 : 0.0)) > 1e-12) return OR_ERR_INVALID_ARG;
+      }
+  }
   return OR_OK;
 }
 
@@ -602,7 +616,19 @@ int64_t or_block_compress(const or_params* p, const void* field, int64_t b, cons
   or_gather(p, field, &g, A);
   or_gram(A, L, n, G);
   if (G_out) memcpy(G_out, G, sizeof(double) * n * n);
-  int sweeps = or_jacobi(G, n, lam, V);
+  int sweeps = 0;
+  if (p->basis && p->basis_n == n) {
+    /* the given modes, as given; lam_k = v_k^T G v_k, the energy of mode k */
+    memcpy(V, p->basis, sizeof(double) * n * n);
+    for (int k = 0; k < n; ++k) {
+      double e = 0.0;
+      for (int a = 0; a < n; ++a)
+        for (int c = 0; c < n; ++c) e += V[a * n + k] * G[a * n + c] * V[c * n + k];
+      lam[k] = e;
+    }
+  } else {
+    sweeps = or_jacobi(G, n, lam, V);
+  }
   or_round_basis(V, n, rcap, p->dtype, Vst);
   if (lam_out) memcpy(lam_out, lam, sizeof(double) * n);
   if (V_out) memcpy(V_out, V, sizeof(double) * n * n);

@@ -50,6 +50,12 @@ typedef struct {
   const double* eb;     /* nvars user values */
   int32_t rank_cap;
   int64_t block_begin, block_end;   /* [begin,end); end < 0 means all */
+  /* Fixed basis (Sec. 4, the SVD / cosine / random comparison): when basis is
+     not null, blocks whose Gram order equals basis_n use its columns
+     (basis[a * basis_n + k] = component a of mode k, orthonormal) in the given
+     order instead of their own eigenvectors; other blocks are unchanged. */
+  const double* basis;
+  int32_t basis_n;
 } or_params;
 
 /* Geometry of one block. */

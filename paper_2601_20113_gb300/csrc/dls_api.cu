@@ -30,8 +30,26 @@ int make_plan(const dls_params* p, Plan* out) {
   if (M * T > (1ll << 26)) return DLS_ERR_INVALID_ARG;
   for (int v = 0; v < p->nvars; ++v)
     if (!(p->eb[v] > 0.0) || !isfinite(p->eb[v])) return DLS_ERR_INVALID_ARG;
+  if (p->basis) {
+    // a fixed basis (Sec. 4): the plain form with the bisection only, order
+    // 1..32, finite entries, columns orthonormal to 1e-12
+    if (p->precision != DLS_PREC_FP64 || p->rank_mode != DLS_RANK_SEARCH) return DLS_ERR_INVALID_ARG;
+    const int bn = p->basis_n;
+    if (bn < 1 || bn > kMaxN) return DLS_ERR_INVALID_ARG;
+    for (int i = 0; i < bn; ++i) {
+      for (int j = i; j < bn; ++j) {
+        double d = 0.0;
+        for (int a = 0; a < bn; ++a) {
+          if (!isfinite(p->basis[a * bn + i])) return DLS_ERR_INVALID_ARG;
+          d = fma(p->basis[a * bn + i], p->basis[a * bn + j], d);
+        }
+        if (fabs(d - (i == j ? 1.0 : 0.0)) > 1e-12) return DLS_ERR_INVALID_ARG;
+      }
+    }
+  }
   Plan P;
   memset(&P, 0, sizeof(P));
+  P.basis_n = p->basis ? p->basis_n : 0;
   P.nvars = p->nvars;
   P.dtype = p->dtype;
   P.eb_type = p->eb_type;
@@ -68,7 +86,7 @@ int make_plan(const dls_params* p, Plan* out) {
 }
 
 struct Layout {
-  size_t meta, vst, q, kc, offsets, vars, status, partial, total;
+  size_t meta, vst, q, kc, offsets, vars, status, partial, basis, total;
   // mixed-precision form
   size_t staging, q_scr, k8_scr, k32_scr, bit_scr, feat, ranks, phase;
   int ctas;
@@ -170,6 +188,7 @@ static Layout work_layout(const Plan& P) {
   L.vars = take(sizeof(VarInfo) * kMaxVars);
   L.status = take(sizeof(Status));
   L.partial = take(sizeof(double) * (size_t)stats_partial_doubles(P));
+  L.basis = P.basis_n > 0 ? take(sizeof(double) * (size_t)P.basis_n * P.basis_n) : 0;
   L.total = off;
   return L;
 }
@@ -184,7 +203,18 @@ static Work carve(const Layout& L, void* ws) {
   w.offsets = (unsigned long long*)(b + L.offsets);
   w.vars = (VarInfo*)(b + L.vars);
   w.status = (Status*)(b + L.status);
+  w.basis = L.basis ? (const double*)(b + L.basis) : nullptr;
   return w;
+}
+
+// Copies the fixed basis (if any) into its workspace region, stream-ordered;
+// the host array may be freed once this returns.
+static int upload_basis(const dls_params* p, const Plan& P, const Layout& L, void* d_ws, cudaStream_t s) {
+  if (P.basis_n == 0) return DLS_OK;
+  const size_t bytes = sizeof(double) * (size_t)P.basis_n * P.basis_n;
+  return cudaMemcpyAsync((uint8_t*)d_ws + L.basis, p->basis, bytes, cudaMemcpyHostToDevice, s) == cudaSuccess
+             ? DLS_OK
+             : DLS_ERR_CUDA;
 }
 
 static int64_t bound_bytes(const Plan& P) {
@@ -246,6 +276,8 @@ static int read_header(const void* d_comp, size_t comp_bytes, cudaStream_t s, Ho
   p.block_begin = (int64_t)u64[9];
   p.block_end = (int64_t)u64[10];
   p.eb = h->eb_user;
+  p.basis = nullptr;   // records carry their modes
+  p.basis_n = 0;
   h->total_blocks = (int64_t)u64[11];
   h->offsets_pos = (int64_t)u64[13];
   h->payload_pos = (int64_t)u64[14];
@@ -497,6 +529,7 @@ int dls_compress(const dls_params* p, const void* d_in, void* d_out, size_t out_
   if (L.mixed && P.rank_mode == DLS_RANK_LEARNED && !rank_model_loaded()) return DLS_ERR_NO_MODEL;
   cudaStream_t s = (cudaStream_t)stream;
   Work w = carve(L, d_workspace);
+  if ((st = upload_basis(p, P, L, d_workspace, s)) != DLS_OK) return st;
   if ((st = enqueue_compress(P, L, d_in, d_out, out_cap, d_workspace, 2, s)) != DLS_OK) return st;
   Status hs;
   CK(cudaMemcpyAsync(&hs, w.status, sizeof(Status), cudaMemcpyDeviceToHost, s));
@@ -683,6 +716,9 @@ int dls_plan_create(const dls_params* p, const void* d_in, void* d_out, size_t o
   if (cudaEventCreate(&pl->kev[0]) != cudaSuccess || cudaEventCreate(&pl->kev[1]) != cudaSuccess)
     return fail(DLS_ERR_CUDA);
   if (cudaHostAlloc((void**)&pl->h_status, sizeof(Status), cudaHostAllocDefault) != cudaSuccess) return fail(DLS_ERR_CUDA);
+  // the fixed basis goes into the workspace once, outside the captured graph
+  if ((st = upload_basis(p, P, L, d_workspace, s)) != DLS_OK) return fail(st);
+  if (P.basis_n > 0 && cudaStreamSynchronize(s) != cudaSuccess) return fail(DLS_ERR_CUDA);
   // autotune: time each occupancy variant of the per-block kernel on the real work
   if (L.mixed) {
     const std::string key = tune_key(P);

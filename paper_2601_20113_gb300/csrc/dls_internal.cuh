@@ -46,6 +46,7 @@ struct Plan {
   int64_t nmax_full;       // Gram order of a full block
   int64_t offsets_pos, payload_pos;   // byte positions in the stream
   int64_t pt_base, pt_count;          // point range of the processed blocks (workspace indexing)
+  int32_t basis_n;                    // Gram order of the fixed basis (0: none)
   double eb_user[kMaxVars];
 };
 
@@ -133,6 +134,7 @@ struct Work {
   unsigned long long* offsets;  // nb + 1
   VarInfo* vars;        // nvars
   Status* status;
+  const double* basis;  // basis_n x basis_n fixed modes (null: none)
 };
 
 // ordered key for doubles (monotone map to unsigned)

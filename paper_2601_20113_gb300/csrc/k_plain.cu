@@ -327,9 +327,17 @@ __global__ void __launch_bounds__(kThreads) k_plain(Plan P, const T* __restrict_
     return;
   }
 
-  // ---- 2. eigensolve (warp 0) and stored basis
+  // ---- 2. eigensolve (warp 0) and stored basis; with a fixed basis of this
+  // Gram order (Sec. 4), its first rcap modes in the given order instead
   double* vst_out = W.vst + bi * (int64_t)P.nmax * P.nmax;
-  if (warp == 0) {
+  if (W.basis && n == P.basis_n) {
+    for (int e = tid; e < n * rcap; e += kThreads) {
+      const int a = e / rcap, k = e - a * rcap;
+      const double vs = to_dt<T>(W.basis[a * n + k]);
+      S.Vst[a * rcap + k] = vs;
+      vst_out[a * rcap + k] = vs;
+    }
+  } else if (warp == 0) {
     jacobi_warp<NM>(S, n, lane);
     __syncwarp();
     sort_and_store<T, NM>(S, n, rcap, lane, vst_out);

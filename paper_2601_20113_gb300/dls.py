@@ -44,6 +44,8 @@ class Params(C.Structure):
         ("rank_mode", C.c_int32),
         ("block_begin", C.c_int64),
         ("block_end", C.c_int64),
+        ("basis", C.POINTER(C.c_double)),
+        ("basis_n", C.c_int32),
     ]
 
 
@@ -141,8 +143,9 @@ def _dtype_code(t: torch.dtype) -> int:
 
 
 def make_params(shape, dtype, block, eb, eb_type=EB_ABS, rank_cap=32, precision=PREC_FP64,
-                rank_mode=RANK_SEARCH, block_begin=0, block_end=-1):
-    """shape = (nvars, nt, nz, ny, nx) of the field tensor."""
+                rank_mode=RANK_SEARCH, block_begin=0, block_end=-1, basis=None):
+    """shape = (nvars, nt, nz, ny, nx) of the field tensor; basis: optional
+    n x n orthonormal modes (column k = mode k) for the blocks of Gram order n."""
     nvars, nt, nz, ny, nx = shape
     p = Params()
     p.nvars = nvars
@@ -161,6 +164,14 @@ def make_params(shape, dtype, block, eb, eb_type=EB_ABS, rank_cap=32, precision=
     p.rank_mode = rank_mode
     p.block_begin = block_begin
     p.block_end = block_end
+    if basis is not None:
+        import numpy as np
+        b = np.ascontiguousarray(np.asarray(basis, dtype=np.float64))
+        if b.ndim != 2 or b.shape[0] != b.shape[1]:
+            raise ValueError("basis must be a square matrix")
+        p.basis = b.ctypes.data_as(C.POINTER(C.c_double))
+        p.basis_n = b.shape[0]
+        p._basis_keep = b
     return p
 
 
@@ -186,12 +197,12 @@ def compress_into(p: Params, field: torch.Tensor, out: torch.Tensor, workspace: 
 
 
 def compress(field: torch.Tensor, block, eb, eb_type=EB_ABS, rank_cap=32, precision=PREC_FP64,
-             rank_mode=RANK_SEARCH, block_begin=0, block_end=-1):
+             rank_mode=RANK_SEARCH, block_begin=0, block_end=-1, basis=None):
     """Compresses a CUDA field (nvars, nt, nz, ny, nx); returns a uint8 CUDA tensor."""
     if not field.is_cuda or not field.is_contiguous() or field.dim() != 5:
         raise ValueError("field must be a contiguous CUDA tensor (nvars, nt, nz, ny, nx)")
     p = make_params(tuple(field.shape), field.dtype, block, eb, eb_type, rank_cap, precision, rank_mode,
-                    block_begin, block_end)
+                    block_begin, block_end, basis)
     cap = compress_bound(p)
     ws = workspace_size(p)
     if cap == 0 or ws == 0:

@@ -180,3 +180,34 @@ def field_lowrank(nx, ny, nz, nt, rank, seed, dtype=torch.float64):
         g = torch.tensor(rng.standard_normal(nt))
         out[0] += g[:, None, None, None] * (fz[:, None, None] * fy[None, :, None] * fx[None, None, :])
     return out.to(dtype)
+
+
+# ---------------------------------------------------------------- fixed bases
+# The two non-adaptive bases of the basis comparison (Sec. 4), as inputs: an
+# n x n matrix whose column k is mode k (orthonormal columns).
+
+
+def dct_basis(n: int) -> np.ndarray:
+    """Orthonormal DCT-II modes in frequency order: column k, component a =
+    s_k cos(pi (a + 1/2) k / n), s_0 = sqrt(1/n), s_k = sqrt(2/n) for k > 0."""
+    a = np.arange(n, dtype=np.float64)[:, None]
+    k = np.arange(n, dtype=np.float64)[None, :]
+    B = np.cos(np.pi * (a + 0.5) * k / n) * math.sqrt(2.0 / n)
+    B[:, 0] = math.sqrt(1.0 / n)
+    return np.ascontiguousarray(B)
+
+
+def random_basis(n: int, seed: int) -> np.ndarray:
+    """Seeded random orthonormal modes: Q of the QR factorisation of an n x n
+    standard-normal matrix (numpy Philox), columns signed so that R has a
+    positive diagonal (a Haar-distributed orthogonal matrix); then one
+    Gram-Schmidt pass in FP64 so the columns are orthonormal to rounding."""
+    G = _rng(seed).standard_normal((n, n))
+    Q, R = np.linalg.qr(G)
+    Q = Q * np.sign(np.diag(R))[None, :]
+    for k in range(n):
+        v = Q[:, k].copy()
+        for j in range(k):
+            v -= (Q[:, j] @ v) * Q[:, j]
+        Q[:, k] = v / np.linalg.norm(v)
+    return np.ascontiguousarray(Q)
