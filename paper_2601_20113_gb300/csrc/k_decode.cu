@@ -13,6 +13,9 @@ namespace dls {
 namespace {
 
 constexpr int kDecThreads = 256;
+// Shared-memory words for a record's coefficient and correction sections
+// (96 KB: two CTAs per SM, the limit the registers set anyway).
+constexpr int kDecStageWords = 24576;
 
 template <typename T> __device__ __forceinline__ T dq(int32_t q, T d);
 template <> __device__ __forceinline__ float dq<float>(int32_t q, float d) { return __fmul_rn(__int2float_rn(q), d); }
@@ -51,6 +54,7 @@ template <typename T, int NM>
 __global__ void __launch_bounds__(kDecThreads) k_decode(Plan P, const uint8_t* __restrict__ comp,
                                                         unsigned long long comp_bytes, T* __restrict__ out,
                                                         Status* st) {
+  extern __shared__ __align__(16) uint32_t stage_sm[];   // kDecStageWords
   __shared__ T vst[NM * NM];
   __shared__ int64_t wbase[NM + 1];
   __shared__ int64_t soff_col[NM];   // spatial-side blocks: field offset of column j (time 0)
@@ -119,9 +123,18 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(Plan P, const uint8_t* _
     vst[j * NM + c] = vin[i];
   }
   if (g.side == 1 && tid < n) soff_col[tid] = spatial_off(P, g, tid);
-  __syncthreads();
+  // the coefficient and correction sections (contiguous words from off_q) go
+  // to shared memory in one pass with every load in flight, when they fit;
+  // the row loop then reads them at shared-memory latency
+  const int64_t cw_at = (lay.off_c - lay.off_q) / 4;
+  const int64_t nstage = cw_at + lay.corr_words;
+  const bool staged = nstage <= kDecStageWords;
   const uint32_t* qw = reinterpret_cast<const uint32_t*>(rec + lay.off_q);
-  const uint32_t* cw = reinterpret_cast<const uint32_t*>(rec + lay.off_c);
+  if (staged)
+    for (int64_t i = tid; i < nstage; i += kDecThreads) stage_sm[i] = qw[i];
+  __syncthreads();
+  if (staged) qw = stage_sm;
+  const uint32_t* cw = qw + cw_at;
   const bool dense = lay.dense && wk > 0;
   for (int64_t l = tid; l < L; l += kDecThreads) {
     // row l's field offset: a spatial point (time side) or a time step (spatial side)
@@ -156,6 +169,7 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(Plan P, const uint8_t* _
   }
   __syncthreads();
   if (!dense && wk > 0) {
+#pragma unroll 4
     for (int64_t i = tid; i < ncorr; i += kDecThreads) {
       const uint64_t pos = (uint64_t)i * (uint64_t)(ib + wk);
       const int64_t e = get_bits(cw, pos, ib);
@@ -249,12 +263,17 @@ int launch_decode(const Plan& p, const void* d_comp, unsigned long long comp_byt
   if (p.nb == 0) return DLS_OK;
   const unsigned grid = (unsigned)p.nb;
   const uint8_t* c = (const uint8_t*)d_comp;
+  const int sm = kDecStageWords * 4;
+  auto go = [&](auto kern, auto* outp) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess) return;
+    kern<<<grid, kDecThreads, sm, s>>>(p, c, comp_bytes, outp, st);
+  };
   if (p.dtype == DLS_F32) {
-    if (p.nmax <= 16) k_decode<float, 16><<<grid, kDecThreads, 0, s>>>(p, c, comp_bytes, (float*)d_out, st);
-    else k_decode<float, 32><<<grid, kDecThreads, 0, s>>>(p, c, comp_bytes, (float*)d_out, st);
+    if (p.nmax <= 16) go(k_decode<float, 16>, (float*)d_out);
+    else go(k_decode<float, 32>, (float*)d_out);
   } else {
-    if (p.nmax <= 16) k_decode<double, 16><<<grid, kDecThreads, 0, s>>>(p, c, comp_bytes, (double*)d_out, st);
-    else k_decode<double, 32><<<grid, kDecThreads, 0, s>>>(p, c, comp_bytes, (double*)d_out, st);
+    if (p.nmax <= 16) go(k_decode<double, 16>, (double*)d_out);
+    else go(k_decode<double, 32>, (double*)d_out);
   }
   return cudaGetLastError() == cudaSuccess ? DLS_OK : DLS_ERR_CUDA;
 }
