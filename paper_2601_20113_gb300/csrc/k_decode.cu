@@ -36,6 +36,19 @@ __device__ __forceinline__ uint32_t get_bits(const uint32_t* w, uint64_t pos, in
   return (uint32_t)(v & (width == 32 ? 0xffffffffull : ((1ull << width) - 1)));
 }
 
+// get_bits for bit positions below 2^32 (a column of L <= 2^26 values of at
+// most 32 bits); width 0 reads nothing.
+__device__ __forceinline__ uint32_t get_bits32(const uint32_t* w, uint32_t pos, int width) {
+  if (width == 0) return 0;
+  const uint32_t wi = pos >> 5;
+  const int sh = (int)(pos & 31);
+  uint32_t v = w[wi] >> sh;
+  if (sh + width > 32) v |= w[wi + 1] << (32 - sh);
+  return width == 32 ? v : (v & ((1u << width) - 1u));
+}
+
+template <int V> struct RankC { static constexpr int value = V; };
+
 // Field offset of a block's spatial point ls (x fastest) without the time
 // step: 32-bit division (a block's extents are small), once per point.
 __device__ __forceinline__ int64_t spatial_off(const Plan& p, const Geom& g, int ls) {
@@ -136,36 +149,77 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(Plan P, const uint8_t* _
   if (staged) qw = stage_sm;
   const uint32_t* cw = qw + cw_at;
   const bool dense = lay.dense && wk > 0;
-  for (int64_t l = tid; l < L; l += kDecThreads) {
-    // row l's field offset: a spatial point (time side) or a time step (spatial side)
-    const int64_t row_off = g.side == 0 ? spatial_off(P, g, (int)l) + g.t0 * P.P : (g.t0 + l) * P.P;
-    T ch[NM];
+  // Rank 1-4 (the common case) with the rank fixed at compile time: the
+  // coefficients of a row in registers, each output r FMAs; the time-side
+  // outputs of a row one time plane apart.  Other ranks: guarded up to NM.
+  auto rows_fixed = [&](auto RK) {
+    constexpr int R = decltype(RK)::value;
+    int wqc[R];
+    const uint32_t* qc[R];
 #pragma unroll
-    for (int c = 0; c < NM; ++c) {
-      if (c < r) {
-        const uint32_t z = get_bits(qw + wbase[c], (uint64_t)l * wq[c], wq[c]);
-        ch[c] = dq<T>(unzigzag(z), delta_t);
-      } else {
-        ch[c] = T(0);
-      }
-    }
-    // one output at a time: unrolled over j, the basis (loop-invariant over
-    // rows) would be held in registers, a CTA per SM
+    for (int c = 0; c < R; ++c) { wqc[c] = wq[c]; qc[c] = qw + wbase[c]; }
+    for (int64_t l = tid; l < L; l += kDecThreads) {
+      const int64_t row_off = g.side == 0 ? spatial_off(P, g, (int)l) + g.t0 * P.P : (g.t0 + l) * P.P;
+      T ch[R];
+#pragma unroll
+      for (int c = 0; c < R; ++c) ch[c] = dq<T>(unzigzag(get_bits32(qc[c], (uint32_t)l * (uint32_t)wqc[c], wqc[c])), delta_t);
+      T* o = out + row_off;
 #pragma unroll 1
-    for (int j = 0; j < n; ++j) {
-      {
+      for (int j = 0; j < n; ++j) {
         T acc = T(0);
 #pragma unroll
-        for (int c = 0; c < NM; ++c)
-          if (c < r) acc = tf<T>(ch[c], vst[j * NM + c], acc);
-        const int64_t e = a_elem(g, l, j);
+        for (int c = 0; c < R; ++c) acc = tf<T>(ch[c], vst[j * NM + c], acc);
         if (dense) {
-          const int32_t kv = unzigzag(get_bits(cw, (uint64_t)e * wk, wk));
+          const int32_t kv = unzigzag(get_bits(cw, (uint64_t)a_elem(g, l, j) * wk, wk));
           if (kv != 0) acc = tf<T>((T)kv, step_t, acc);
         }
-        out[row_off + (g.side == 0 ? (int64_t)j * P.P : soff_col[j])] = acc;
+        if (g.side == 0) {
+          *o = acc;
+          o += P.P;
+        } else {
+          out[row_off + soff_col[j]] = acc;
+        }
       }
     }
+  };
+  switch (r) {
+    case 1: rows_fixed(RankC<1>()); break;
+    case 2: rows_fixed(RankC<2>()); break;
+    case 3: rows_fixed(RankC<3>()); break;
+    case 4: rows_fixed(RankC<4>()); break;
+    default:
+      for (int64_t l = tid; l < L; l += kDecThreads) {
+        // row l's field offset: a spatial point (time side) or a time step (spatial side)
+        const int64_t row_off = g.side == 0 ? spatial_off(P, g, (int)l) + g.t0 * P.P : (g.t0 + l) * P.P;
+        T ch[NM];
+#pragma unroll
+        for (int c = 0; c < NM; ++c) {
+          if (c < r) {
+            const uint32_t z = get_bits(qw + wbase[c], (uint64_t)l * wq[c], wq[c]);
+            ch[c] = dq<T>(unzigzag(z), delta_t);
+          } else {
+            ch[c] = T(0);
+          }
+        }
+        // one output at a time: unrolled over j, the basis (loop-invariant over
+        // rows) would be held in registers, a CTA per SM
+#pragma unroll 1
+        for (int j = 0; j < n; ++j) {
+          {
+            T acc = T(0);
+#pragma unroll
+            for (int c = 0; c < NM; ++c)
+              if (c < r) acc = tf<T>(ch[c], vst[j * NM + c], acc);
+            const int64_t e = a_elem(g, l, j);
+            if (dense) {
+              const int32_t kv = unzigzag(get_bits(cw, (uint64_t)e * wk, wk));
+              if (kv != 0) acc = tf<T>((T)kv, step_t, acc);
+            }
+            out[row_off + (g.side == 0 ? (int64_t)j * P.P : soff_col[j])] = acc;
+          }
+        }
+      }
+      break;
   }
   __syncthreads();
   if (!dense && wk > 0) {
