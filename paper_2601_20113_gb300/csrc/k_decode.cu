@@ -14,8 +14,9 @@ namespace {
 
 constexpr int kDecThreads = 256;
 // Shared-memory words for a record's coefficient and correction sections
-// (96 KB: two CTAs per SM, the limit the registers set anyway).
-constexpr int kDecStageWords = 24576;
+// (72 KB: three CTAs per SM, as the launch bounds ask of the registers).
+constexpr int kDecStageWords = 18432;
+constexpr int kDecMinBlocks = 3;
 
 template <typename T> __device__ __forceinline__ T dq(int32_t q, T d);
 template <> __device__ __forceinline__ float dq<float>(int32_t q, float d) { return __fmul_rn(__int2float_rn(q), d); }
@@ -64,7 +65,7 @@ __device__ __forceinline__ int64_t elem_off(const Plan& p, const Geom& g, int64_
 }
 
 template <typename T, int NM>
-__global__ void __launch_bounds__(kDecThreads) k_decode(Plan P, const uint8_t* __restrict__ comp,
+__global__ void __launch_bounds__(kDecThreads, kDecMinBlocks) k_decode(Plan P, const uint8_t* __restrict__ comp,
                                                         unsigned long long comp_bytes, T* __restrict__ out,
                                                         Status* st) {
   extern __shared__ __align__(16) uint32_t stage_sm[];   // kDecStageWords
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(Plan P, const uint8_t* _
   if (staged) qw = stage_sm;
   const uint32_t* cw = qw + cw_at;
   const bool dense = lay.dense && wk > 0;
-  // Rank 1-4 (the common case) with the rank fixed at compile time: the
+  // Rank 1-8 (the common case) with the rank fixed at compile time: the
   // coefficients of a row in registers, each output r FMAs; the time-side
   // outputs of a row one time plane apart.  Other ranks: guarded up to NM.
   auto rows_fixed = [&](auto RK) {
@@ -187,6 +188,10 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(Plan P, const uint8_t* _
     case 2: rows_fixed(RankC<2>()); break;
     case 3: rows_fixed(RankC<3>()); break;
     case 4: rows_fixed(RankC<4>()); break;
+    case 5: rows_fixed(RankC<5>()); break;
+    case 6: rows_fixed(RankC<6>()); break;
+    case 7: rows_fixed(RankC<7>()); break;
+    case 8: rows_fixed(RankC<8>()); break;
     default:
       for (int64_t l = tid; l < L; l += kDecThreads) {
         // row l's field offset: a spatial point (time side) or a time step (spatial side)
