@@ -323,18 +323,18 @@ int launch_decode(const Plan& p, const void* d_comp, unsigned long long comp_byt
   const unsigned grid = (unsigned)p.nb;
   const uint8_t* c = (const uint8_t*)d_comp;
   const int sm = kDecStageWords * 4;
-  auto go = [&](auto kern, auto* outp) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess) return;
+  // the stage buffer is above the 48 KB default: opt in before each launch
+  auto go = [&](auto kern, auto* outp) -> bool {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess) return false;
     kern<<<grid, kDecThreads, sm, s>>>(p, c, comp_bytes, outp, st);
+    return true;
   };
-  if (p.dtype == DLS_F32) {
-    if (p.nmax <= 16) go(k_decode<float, 16>, (float*)d_out);
-    else go(k_decode<float, 32>, (float*)d_out);
-  } else {
-    if (p.nmax <= 16) go(k_decode<double, 16>, (double*)d_out);
-    else go(k_decode<double, 32>, (double*)d_out);
-  }
-  return cudaGetLastError() == cudaSuccess ? DLS_OK : DLS_ERR_CUDA;
+  bool ok;
+  if (p.dtype == DLS_F32)
+    ok = p.nmax <= 16 ? go(k_decode<float, 16>, (float*)d_out) : go(k_decode<float, 32>, (float*)d_out);
+  else
+    ok = p.nmax <= 16 ? go(k_decode<double, 16>, (double*)d_out) : go(k_decode<double, 32>, (double*)d_out);
+  return ok && cudaGetLastError() == cudaSuccess ? DLS_OK : DLS_ERR_CUDA;
 }
 
 int launch_verify(const Plan& p, const void* d_orig, const void* d_recon, const void* d_comp,
