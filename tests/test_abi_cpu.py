@@ -63,3 +63,34 @@ def test_compress_bound_matches_oracle(libpath):
         cfg = oracle.Config(dims, block, dt, eb=1.0, nvars=nv)
         p = dls.make_params((nv, dims[3], dims[2], dims[1], dims[0]), dt, block, 1.0)
         assert dls.compress_bound(p) == oracle.compress_bound(cfg)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every struct the ABI passes (parameters, verification report, stream
+    information) has the same size and field offsets in include/dls.h, as
+    compiled by the host C compiler, as in its ctypes mirror in the binding;
+    the oracle's own parameter struct likewise matches its header."""
+    import shutil
+    import subprocess
+    import oracle
+    from paper_2601_20113_gb300 import dls
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    cases = [("dls_params", dls.Params, "dls.h", os.path.join(ROOT, "include")),
+             ("dls_report", dls.Report, "dls.h", os.path.join(ROOT, "include")),
+             ("dls_stream_info", dls.StreamInfo, "dls.h", os.path.join(ROOT, "include")),
+             ("or_params", oracle.Params, "dls_oracle.h", os.path.join(ROOT, "oracle"))]
+    for cname, py, hdr, inc in cases:
+        lines = [f'#include "{hdr}"', "#include <stdio.h>", "#include <stddef.h>", "int main(void) {",
+                 f'  printf("%zu\\n", sizeof({cname}));']
+        for name, _ in py._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({cname}, {name}));')
+        lines += ["  return 0;", "}"]
+        src = tmp_path / f"{cname}.c"
+        src.write_text("\n".join(lines) + "\n")
+        exe = tmp_path / cname
+        subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True, capture_output=True)
+        got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+        want = [ctypes.sizeof(py)] + [getattr(py, name).offset for name, _ in py._fields_]
+        assert got == want, (cname, got, want)
