@@ -1,0 +1,159 @@
+"""Oracle of the global-basis mode: Algorithm 1 as the paper states it.
+
+Test infrastructure: only the tests (and the benchmark's CPU baseline) may
+import it.  Plain numpy in FP64, one function per step, no blocking or fusion;
+numpy's SVD and matrix-vector product serve as library steps.
+
+- learn_basis: one orthonormal basis per variable from random patches of the
+  first snapshot (Algorithm 1 step 1; Sec. 2.3, Eq. 2-3): the right singular
+  vectors of the sample matrix, by decreasing singular value.
+- local_tolerance: the per-patch L2 budget (Sec. 2.4, Eq. 4).
+- compress_patch: projection on the basis (Sec. 2.5, Eq. 5), coefficients
+  ordered by decreasing magnitude, and the smallest prefix meeting the
+  tolerance found by bisection (Eq. 6; Algorithm 1 step 3).
+- compress / decompress: every patch of every snapshot, and back.
+
+Readings where the paper is silent or loose:
+- G1 patches tile each snapshot from the origin (x fastest within a patch);
+  the snapshot's extents must be multiples of the patch, since an edge patch
+  would not fit the basis; a 2-D field (nz = 1) uses m x m patches.
+- G2 the sample: S patch origins drawn uniformly with replacement over every
+  position where a patch fits, handed in by the caller (the method's random
+  draws are inputs); Algorithm 1 uses S = 4 m^3.
+- G3 mode k is the right singular vector of the k-th largest singular value,
+  signed so that its largest-magnitude component is positive (lowest index on
+  ties).
+- G4 the budget: eps = eps_t ||u|| / 100 over all points of the variable, and
+  eps_l^2 = eps^2 M / K for a patch of M points out of K (all snapshots), so
+  meeting eps_l on every patch of every snapshot meets the global target.
+- G5 coefficients are ranked by decreasing magnitude; equal magnitudes keep
+  index order.
+- G6 stored values: q = rint(alpha / delta), ties to even, with delta =
+  eps / sqrt(K) (the global budget's RMS per point), standing in for
+  bit-grooming; the test of a prefix uses the stored values, so it also
+  covers their rounding: pass(n) <=> ||u - sum_{s<n} q_s delta phi_s||^2 <=
+  eps_l^2 (Algorithm 1 prints <=), the kept modes added in kept order.  With
+  every mode kept the error is the rounding alone, at most M delta^2 / 4 <
+  eps_l^2, so every patch passes at some n <= M.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def patch_shape(dims, m: int):
+    """(px, py, pz) of the patches of a field with dims (nx, ny, nz, nt) (G1)."""
+    return (int(m), int(m), int(m) if int(dims[2]) > 1 else 1)
+
+
+def _check_tiling(dims, patch):
+    for d, p in zip(dims[:3], patch):
+        if int(d) % int(p):
+            raise ValueError("the snapshot extents must be multiples of the patch (G1)")
+
+
+def gather_patch(snap: np.ndarray, origin, patch) -> np.ndarray:
+    """The M values of the patch at origin (x0, y0, z0) of a snapshot laid out
+    (nz, ny, nx), x fastest."""
+    x0, y0, z0 = (int(v) for v in origin)
+    px, py, pz = patch
+    return np.asarray(snap[z0:z0 + pz, y0:y0 + py, x0:x0 + px], dtype=np.float64).reshape(-1)
+
+
+def learn_basis(snap0: np.ndarray, origins: np.ndarray, patch):
+    """Algorithm 1 step 1: Q (S x M) from the sampled patches of the first
+    snapshot, Q = U Sigma V^T, Phi = V (M x M, column k = mode k), with the
+    singular values (zero beyond the rank of Q) and the sign rule G3."""
+    Q = np.stack([gather_patch(snap0, o, patch) for o in origins])
+    _, s, vt = np.linalg.svd(Q, full_matrices=True)
+    phi = vt.T.copy()
+    M = phi.shape[0]
+    sv = np.zeros(M)
+    sv[:s.size] = s
+    for k in range(M):
+        col = phi[:, k]
+        if col[int(np.argmax(np.abs(col)))] < 0.0:
+            phi[:, k] = -col
+    return phi, sv
+
+
+def local_tolerance(field: np.ndarray, eps_t: float, M: int):
+    """G4 and G6: (eps_l^2, delta) for a variable (all snapshots) and a target
+    NRMSE eps_t in percent."""
+    x = np.asarray(field, dtype=np.float64)
+    K = x.size
+    eps = eps_t * np.sqrt(np.sum(x * x)) / 100.0
+    return eps * eps * M / K, eps / np.sqrt(K)
+
+
+def reconstruct(phi: np.ndarray, idx: np.ndarray, q: np.ndarray, delta: float) -> np.ndarray:
+    """sum over the kept modes, in kept order, of q_s delta phi_s."""
+    rec = np.zeros(phi.shape[0])
+    for s in range(len(idx)):
+        rec = rec + (float(q[s]) * delta) * phi[:, int(idx[s])]
+    return rec
+
+
+def compress_patch(u: np.ndarray, phi: np.ndarray, eps_l2: float, delta: float):
+    """Algorithm 1 step 3 for one patch: alpha = Phi^T u, the coefficients
+    ranked by decreasing magnitude (G5), quantized (G6), and the smallest n
+    with pass(n) by bisection over [0, M].  Returns (kept mode indices in kept
+    order, their q, the squared error at n)."""
+    u = np.asarray(u, dtype=np.float64)
+    if delta == 0.0:
+        # an all-zero variable: eps = 0 and every patch is zero, kept by no mode
+        return np.zeros(0, np.int64), np.zeros(0, np.int64), float(np.dot(u, u))
+    alpha = phi.T @ u
+    order = np.argsort(-np.abs(alpha), kind="stable")
+    q_all = np.rint(alpha / delta)
+
+    def err2(n):
+        d = u - reconstruct(phi, order[:n], q_all[order[:n]], delta)
+        return float(np.dot(d, d))
+
+    lo, hi = 0, phi.shape[0]
+    while lo < hi:
+        mid = (lo + hi) // 2
+        if err2(mid) <= eps_l2:
+            hi = mid
+        else:
+            lo = mid + 1
+    idx = order[:lo].copy()
+    return idx, q_all[idx].astype(np.int64), err2(lo)
+
+
+def compress(field: np.ndarray, m: int, eps_t: float, origins: np.ndarray):
+    """One variable laid out (nt, nz, ny, nx): the basis from the first
+    snapshot's sampled patches, then every patch of every snapshot.  Returns a
+    dict with the basis, the singular values, the patch shape, eps_l^2, delta
+    and the records (t, origin, kept indices, q, squared error)."""
+    f = np.asarray(field, dtype=np.float64)
+    nt, nz, ny, nx = f.shape
+    dims = (nx, ny, nz, nt)
+    patch = patch_shape(dims, m)
+    _check_tiling(dims, patch)
+    phi, sv = learn_basis(f[0], origins, patch)
+    M = phi.shape[0]
+    eps_l2, delta = local_tolerance(f, eps_t, M)
+    recs = []
+    px, py, pz = patch
+    for t in range(nt):
+        for z0 in range(0, nz, pz):
+            for y0 in range(0, ny, py):
+                for x0 in range(0, nx, px):
+                    u = gather_patch(f[t], (x0, y0, z0), patch)
+                    idx, q, e2 = compress_patch(u, phi, eps_l2, delta)
+                    recs.append((t, (x0, y0, z0), idx, q, e2))
+    return dict(phi=phi, sv=sv, patch=patch, dims=dims, eps_l2=eps_l2, delta=delta, recs=recs)
+
+
+def decompress(res) -> np.ndarray:
+    """The field (nt, nz, ny, nx) from the records: every patch rebuilt from its
+    kept modes (Algorithm 2 for the global basis)."""
+    nx, ny, nz, nt = res["dims"]
+    px, py, pz = res["patch"]
+    out = np.zeros((nt, nz, ny, nx))
+    for t, (x0, y0, z0), idx, q, _ in res["recs"]:
+        rec = reconstruct(res["phi"], idx, q, res["delta"])
+        out[t, z0:z0 + pz, y0:y0 + py, x0:x0 + px] = rec.reshape(pz, py, px)
+    return out

@@ -211,3 +211,15 @@ def random_basis(n: int, seed: int) -> np.ndarray:
             v -= (Q[:, j] @ v) * Q[:, j]
         Q[:, k] = v / np.linalg.norm(v)
     return np.ascontiguousarray(Q)
+
+
+def patch_origins(dims, patch, count: int, seed: int) -> np.ndarray:
+    """Seeded origins (x, y, z) of `count` patches of shape `patch` (px, py, pz)
+    inside a snapshot of dims (nx, ny, nz), uniform over every position where
+    the patch fits (numpy Philox): the random sample of Algorithm 1 step 1,
+    drawn here so that every implementation receives the same patches."""
+    rng = _rng(seed)
+    hi = [int(d) - int(p) + 1 for d, p in zip(dims[:3], patch)]
+    if min(hi) < 1:
+        raise ValueError("patch larger than the snapshot")
+    return np.stack([rng.integers(0, h, size=count) for h in hi], axis=1).astype(np.int64)
