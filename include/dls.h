@@ -152,6 +152,9 @@ int dls_plan_info(const dls_plan* plan, int32_t* variant, float* tune_ms);
  * for that execution), and the number of kernel nodes in the plan's graph.
  * Either pointer may be null. */
 int dls_plan_timing(const dls_plan* plan, float* kernel_ms, int32_t* kernel_nodes);
+/* Releases the plan's graph, events and pinned status buffer (not the
+ * caller's buffers).  A null plan is accepted.  Call it once the last
+ * execution has returned (dls_plan_execute synchronizes its stream). */
 int dls_plan_destroy(dls_plan* plan);
 
 /* Device staging bytes dls_compress_host needs: the input field, the stream
@@ -286,7 +289,13 @@ int dls_mlp_train(float* d_params, float* d_adam, const float* d_feat, const flo
  * the tensor cores (DLS_PREC_TF32X3).  count >= 14.  Synchronous copy. */
 int dls_phase_cycles(const dls_params* p, const void* d_workspace, unsigned long long* h_cycles, int32_t count);
 
-/* Stream header as a host struct (reads the header with one synchronous copy). */
+/* Stream header as a host struct (Sec. 2.7.2: the header and offset table
+ * that make every record addressable).  Reads the header with one
+ * synchronous copy from device memory; the eb, delta and step arrays hold the
+ * resolved per-variable values (first nvars entries).  DLS_ERR_INVALID_ARG for
+ * a null pointer or a stream shorter than the header or not 16-byte aligned,
+ * DLS_ERR_CORRUPT when the header fails the decoder's checks (magic, version,
+ * sizes, offsets), DLS_ERR_CUDA if the copy fails. */
 typedef struct {
   int32_t version, nvars, dtype, eb_type, precision, rank_mode, rank_cap;
   int64_t dims[4];
@@ -297,6 +306,7 @@ typedef struct {
 } dls_stream_info;
 int dls_stream_info_get(const void* d_comp, size_t comp_bytes, dls_stream_info* h_info);
 
+/* Static text for a DLS_* status ("unknown status" for other values). */
 const char* dls_status_string(int status);
 
 #ifdef __cplusplus
