@@ -120,6 +120,16 @@ def lib():
             L.or_compress.argtypes = [C.POINTER(Params), C.c_void_p, C.c_void_p, C.c_int64,
                                       C.POINTER(C.c_int64), C.POINTER(Trace), C.c_int]
             L.or_decompress.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int]
+            i32p = C.POINTER(C.c_int32)
+            u32p = C.POINTER(C.c_uint32)
+            L.or_rice_bits.restype = C.c_int64
+            L.or_rice_bits.argtypes = [i32p, C.c_int64, C.c_int, C.c_int, C.c_int]
+            L.or_rice_choose.restype = None
+            L.or_rice_choose.argtypes = [i32p, C.c_int64, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+            L.or_rice_encode.restype = C.c_int64
+            L.or_rice_encode.argtypes = [i32p, C.c_int64, C.c_int, C.c_int, C.c_int, u32p, C.c_int64, u32p]
+            L.or_rice_decode.restype = C.c_int
+            L.or_rice_decode.argtypes = [u32p, C.c_int64, u32p, C.c_int64, C.c_int, C.c_int, C.c_int, i32p]
             L.or_pack_record.restype = C.c_int64
             L.or_pack_record.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int,
                                          dp, ip, ip, up, dp, up, C.c_int64]
@@ -354,3 +364,42 @@ def decompress(stream: np.ndarray, nthreads: int = 0):
     out = np.zeros((nvars, dims[3], dims[2], dims[1], dims[0]), _np_dtype(dtype))
     st = lib().or_decompress(s.ctypes.data, s.size, out.ctypes.data, out.nbytes, nthreads)
     return st, out
+
+
+# ---------------------------------------------------------------- Rice-coded corrections
+def rice_bits(k: np.ndarray, chunk: int, kr: int, wv: int) -> int:
+    """Exact size in bits of the Rice-coded correction section (a proposed
+    record section; see dls_oracle.c)."""
+    k = np.ascontiguousarray(k, dtype=np.int32)
+    return int(lib().or_rice_bits(_p(k, C.c_int32), k.size, chunk, kr, wv))
+
+
+def rice_choose(k: np.ndarray, chunk: int):
+    """(kr, wv) with the fewest bits."""
+    k = np.ascontiguousarray(k, dtype=np.int32)
+    kr, wv = C.c_int(0), C.c_int(0)
+    lib().or_rice_choose(_p(k, C.c_int32), k.size, chunk, C.byref(kr), C.byref(wv))
+    return kr.value, wv.value
+
+
+def rice_encode(k: np.ndarray, chunk: int, kr: int, wv: int):
+    """(words, chunk bit offsets, bits)."""
+    k = np.ascontiguousarray(k, dtype=np.int32)
+    nbits = rice_bits(k, chunk, kr, wv)
+    words = np.zeros(max(1, (nbits + 31) // 32), np.uint32)
+    off = np.zeros(max(1, -(-k.size // chunk)), np.uint32)
+    got = lib().or_rice_encode(_p(k, C.c_int32), k.size, chunk, kr, wv, _p(words, C.c_uint32), words.size,
+                               _p(off, C.c_uint32))
+    if got < 0:
+        raise RuntimeError("or_rice_encode: capacity")
+    return words, off, int(got)
+
+
+def rice_decode(words: np.ndarray, off: np.ndarray, N: int, chunk: int, kr: int, wv: int):
+    """The corrections, or None for a malformed section."""
+    words = np.ascontiguousarray(words, dtype=np.uint32)
+    off = np.ascontiguousarray(off, dtype=np.uint32)
+    k = np.zeros(max(1, N), np.int32)
+    st = lib().or_rice_decode(_p(words, C.c_uint32), words.size, _p(off, C.c_uint32), N, chunk, kr, wv,
+                              _p(k, C.c_int32))
+    return None if st != 0 else k[:N]

@@ -957,3 +957,140 @@ int or_decompress(const void* stream, int64_t bytes, void* out, int64_t out_cap,
   }
   return err;
 }
+
+/* ------------------------------------------------------------------ */
+/* Rice-coded corrections: a proposed record section (records do not   */
+/* use it yet).  The corrections k[0..N) of a block, in element order,  */
+/* are cut into chunks of `chunk` elements.  Within a chunk every       */
+/* nonzero is written as the Rice code of the zeros before it (counted  */
+/* from the chunk start or the previous nonzero), then zigzag(k) - 1 in */
+/* wv bits; one more Rice code gives the zeros up to the chunk end.  The */
+/* Rice code of r with parameter kr: (r >> kr) one bits, a zero bit, the */
+/* kr low bits of r.  Bits are LSB-first in 32-bit words; chunk c starts */
+/* at bit off[c], the chunks one after another from bit 0, so that the  */
+/* chunks decode independently.                                         */
+/* ------------------------------------------------------------------ */
+static uint32_t rz_zig(int32_t v) { return ((uint32_t)v << 1) ^ (uint32_t)(v >> 31); }
+static int32_t rz_unzig(uint32_t u) { return (int32_t)(u >> 1) ^ -(int32_t)(u & 1u); }
+static int rz_width(uint32_t x) { int w = 0; while (x) { ++w; x >>= 1; } return w; }
+
+int64_t or_rice_bits(const int32_t* k, int64_t N, int chunk, int kr, int wv) {
+  int64_t bits = 0;
+  for (int64_t c0 = 0; c0 < N; c0 += chunk) {
+    const int64_t c1 = c0 + chunk < N ? c0 + chunk : N;
+    int64_t run = 0;
+    for (int64_t e = c0; e < c1; ++e) {
+      if (k[e] == 0) { ++run; continue; }
+      bits += (run >> kr) + 1 + kr + wv;
+      run = 0;
+    }
+    bits += (run >> kr) + 1 + kr;
+  }
+  return bits;
+}
+
+/* wv: the bit width of the largest zigzag(k) - 1 over the nonzeros; kr in
+ * [0, 20] with the fewest bits (the smallest such kr). */
+void or_rice_choose(const int32_t* k, int64_t N, int chunk, int* kr_out, int* wv_out) {
+  uint32_t mx = 0;
+  for (int64_t e = 0; e < N; ++e)
+    if (k[e] != 0 && rz_zig(k[e]) - 1u > mx) mx = rz_zig(k[e]) - 1u;
+  const int wv = rz_width(mx);
+  int best = 0;
+  int64_t bb = -1;
+  for (int kr = 0; kr <= 20; ++kr) {
+    const int64_t b = or_rice_bits(k, N, chunk, kr, wv);
+    if (bb < 0 || b < bb) { bb = b; best = kr; }
+  }
+  *kr_out = best;
+  *wv_out = wv;
+}
+
+static int rz_put(uint32_t* w, int64_t cap_words, int64_t pos, uint32_t v, int width) {
+  for (int i = 0; i < width; ++i) {
+    const int64_t p = pos + i;
+    if ((p >> 5) >= cap_words) return -1;
+    if ((v >> i) & 1u) w[p >> 5] |= 1u << (p & 31);
+  }
+  return 0;
+}
+
+static int rz_code(uint32_t* w, int64_t cap, int64_t* pos, int64_t run, int kr) {
+  for (int64_t i = 0; i < (run >> kr); ++i) {
+    if (rz_put(w, cap, *pos, 1u, 1) < 0) return -1;
+    ++*pos;
+  }
+  if (rz_put(w, cap, *pos, 0u, 1) < 0) return -1;
+  ++*pos;
+  if (rz_put(w, cap, *pos, (uint32_t)(run & ((1ll << kr) - 1)), kr) < 0) return -1;
+  *pos += kr;
+  return 0;
+}
+
+/* Returns the bits written (-1 if cap_words is too small); off gets the bit
+ * offset of each of the ceil(N / chunk) chunks. */
+int64_t or_rice_encode(const int32_t* k, int64_t N, int chunk, int kr, int wv, uint32_t* words,
+                       int64_t cap_words, uint32_t* off) {
+  memset(words, 0, sizeof(uint32_t) * (size_t)cap_words);
+  int64_t pos = 0, c = 0;
+  for (int64_t c0 = 0; c0 < N; c0 += chunk, ++c) {
+    const int64_t c1 = c0 + chunk < N ? c0 + chunk : N;
+    off[c] = (uint32_t)pos;
+    int64_t run = 0;
+    for (int64_t e = c0; e < c1; ++e) {
+      if (k[e] == 0) { ++run; continue; }
+      if (rz_code(words, cap_words, &pos, run, kr) < 0) return -1;
+      if (rz_put(words, cap_words, pos, rz_zig(k[e]) - 1u, wv) < 0) return -1;
+      pos += wv;
+      run = 0;
+    }
+    if (rz_code(words, cap_words, &pos, run, kr) < 0) return -1;
+  }
+  return pos;
+}
+
+static int rz_get(const uint32_t* w, int64_t nwords, int64_t pos, int width, uint32_t* v) {
+  uint32_t x = 0;
+  for (int i = 0; i < width; ++i) {
+    const int64_t p = pos + i;
+    if ((p >> 5) >= nwords) return -1;
+    x |= ((w[p >> 5] >> (p & 31)) & 1u) << i;
+  }
+  *v = x;
+  return 0;
+}
+
+/* 0, or -1 for a malformed section (a run past its chunk, a read past the
+ * words). */
+int or_rice_decode(const uint32_t* words, int64_t nwords, const uint32_t* off, int64_t N, int chunk, int kr,
+                   int wv, int32_t* k) {
+  int64_t c = 0;
+  for (int64_t c0 = 0; c0 < N; c0 += chunk, ++c) {
+    const int64_t c1 = c0 + chunk < N ? c0 + chunk : N;
+    int64_t pos = off[c], e = c0;
+    for (;;) {
+      int64_t q = 0;
+      uint32_t bit = 1;
+      while (1) {
+        if (rz_get(words, nwords, pos, 1, &bit) < 0) return -1;
+        ++pos;
+        if (!bit) break;
+        if (((q + 1) << kr) > c1 - e) return -1;
+        ++q;
+      }
+      uint32_t lo = 0;
+      if (rz_get(words, nwords, pos, kr, &lo) < 0) return -1;
+      pos += kr;
+      const int64_t run = (q << kr) | lo;
+      if (run > c1 - e) return -1;
+      for (int64_t i = 0; i < run; ++i) k[e + i] = 0;
+      e += run;
+      if (e == c1) break;
+      uint32_t v = 0;
+      if (rz_get(words, nwords, pos, wv, &v) < 0) return -1;
+      pos += wv;
+      k[e++] = rz_unzig(v + 1u);
+    }
+  }
+  return 0;
+}

@@ -128,6 +128,18 @@ int64_t or_pack_record(int r, int side, int n, int64_t L, int64_t M, int dtype,
                        const double* Vst, const int32_t* q, const int32_t* k,
                        const uint8_t* esc, const double* A, uint8_t* rec, int64_t cap);
 
+/* Rice-coded corrections, a proposed record section that records do not use
+ * yet (the layout is described in dls_oracle.c): exact size in bits, the
+ * parameters with the fewest bits, encoder (bits written, -1 if cap_words is
+ * too small; off gets each chunk's bit offset) and decoder (0, or -1 for a
+ * malformed section). */
+int64_t or_rice_bits(const int32_t* k, int64_t N, int chunk, int kr, int wv);
+void    or_rice_choose(const int32_t* k, int64_t N, int chunk, int* kr, int* wv);
+int64_t or_rice_encode(const int32_t* k, int64_t N, int chunk, int kr, int wv, uint32_t* words,
+                       int64_t cap_words, uint32_t* off);
+int     or_rice_decode(const uint32_t* words, int64_t nwords, const uint32_t* off, int64_t N, int chunk,
+                       int kr, int wv, int32_t* k);
+
 #ifdef __cplusplus
 }
 #endif
