@@ -55,6 +55,7 @@ class Params(C.Structure):
         ("block_end", C.c_int64),
         ("basis", C.POINTER(C.c_double)),
         ("basis_n", C.c_int32),
+        ("corr_codec", C.c_int32),
     ]
 
 
@@ -132,7 +133,7 @@ def lib():
             L.or_rice_decode.argtypes = [u32p, C.c_int64, u32p, C.c_int64, C.c_int, C.c_int, C.c_int, i32p]
             L.or_pack_record.restype = C.c_int64
             L.or_pack_record.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int,
-                                         dp, ip, ip, up, dp, up, C.c_int64]
+                                         dp, ip, ip, up, dp, up, C.c_int64, C.c_int]
             _lib = L
     return _lib
 
@@ -143,7 +144,7 @@ class Config:
     bound type and rank cap."""
 
     def __init__(self, dims, block, dtype, eb, eb_type=EB_ABS, rank_cap=32, nvars=1,
-                 block_begin=0, block_end=-1, basis=None):
+                 block_begin=0, block_end=-1, basis=None, corr_codec=0):
         self.dims = tuple(int(d) for d in dims)
         self.block = tuple(int(b) for b in block)
         self.dtype = int(dtype)
@@ -154,6 +155,7 @@ class Config:
         self.block_begin = int(block_begin)
         self.block_end = int(block_end)
         # fixed basis (Sec. 4): n x n, column k = mode k, for blocks of Gram order n
+        self.corr_codec = int(corr_codec)   # 1: Rice-coded corrections where smaller (proposed format)
         self.basis = None if basis is None else np.ascontiguousarray(basis, dtype=np.float64)
         if self.basis is not None and (self.basis.ndim != 2 or self.basis.shape[0] != self.basis.shape[1]):
             raise ValueError("basis must be a square matrix")
@@ -173,6 +175,7 @@ class Config:
         if self.basis is not None:
             p.basis = _p(self.basis, C.c_double)
             p.basis_n = self.basis.shape[0]
+        p.corr_codec = self.corr_codec
         return p
 
 
@@ -284,7 +287,7 @@ def correct(A, D, side, M, dtype, eb, step):
     return k, esc
 
 
-def pack_record(r, side, n, L, M, dtype, Vst, q, k, esc, A) -> bytes:
+def pack_record(r, side, n, L, M, dtype, Vst, q, k, esc, A, corr_codec=0) -> bytes:
     Vst = np.ascontiguousarray(Vst, np.float64)
     q = np.ascontiguousarray(q, np.int32)
     k = np.ascontiguousarray(k, np.int32)
@@ -294,7 +297,7 @@ def pack_record(r, side, n, L, M, dtype, Vst, q, k, esc, A) -> bytes:
     buf = np.zeros(cap, np.uint8)
     sz = lib().or_pack_record(r, side, n, L, M, dtype, _p(Vst, C.c_double), _p(q, C.c_int32),
                               _p(k, C.c_int32), _p(esc, C.c_uint8), _p(A, C.c_double),
-                              _p(buf, C.c_uint8), cap)
+                              _p(buf, C.c_uint8), cap, int(corr_codec))
     if sz < 0:
         raise RuntimeError(f"or_pack_record failed: {sz}")
     return buf[:sz].tobytes()

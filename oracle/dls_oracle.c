@@ -30,6 +30,8 @@
 #define OR_FLAG_RAW 1u
 #define OR_FLAG_SPATIAL 2u
 #define OR_FLAG_DENSE 4u
+#define OR_FLAG_RICE 8u
+#define OR_RICE_CHUNK 1024
 #define OR_QMAX_F32 16777216.0    /* 2^24: |q| must stay below, so float(q) is exact */
 #define OR_QMAX_F64 1073741824.0  /* 2^30 */
 #define OR_KMAX 1048576.0         /* 2^20: larger corrections become escapes */
@@ -507,10 +509,14 @@ static int64_t write_raw(const double* A, int64_t L, int n, int side, int64_t M,
  *   escapes: n_esc u32 element indices (increasing), padded to 8, then
  *            n_esc raw values in dtype, padded to 8
  *   record padded to 16 bytes.
- * Dense is used only when strictly smaller than sparse. */
+ * Dense is used only when strictly smaller than sparse.
+ * With corr_codec = 1 a third form is taken when strictly smaller than both
+ * (flag OR_FLAG_RICE): words [0] = number of Rice words, [1] = kr | wv << 8,
+ * then ceil(N / OR_RICE_CHUNK) chunk bit offsets, then the Rice words of the
+ * corrections with the escaped points as zeros (or_rice_encode). */
 int64_t or_pack_record(int r, int side, int n, int64_t L, int64_t M, int dtype,
                        const double* Vst, const int32_t* q, const int32_t* k,
-                       const uint8_t* esc, const double* A, uint8_t* rec, int64_t cap) {
+                       const uint8_t* esc, const double* A, uint8_t* rec, int64_t cap, int corr_codec) {
   int64_t N = L * n;
   int es = esize(dtype);
   uint8_t wq[32];
@@ -530,6 +536,20 @@ int64_t or_pack_record(int r, int side, int n, int64_t L, int64_t M, int dtype,
   int64_t dense_w = (N * wk + 31) / 32, sparse_w = (ncorr * (ib + wk) + 31) / 32;
   int dense = (wk > 0) && (dense_w < sparse_w);
   int64_t corr_w = wk == 0 ? 0 : (dense ? dense_w : sparse_w);
+  int rice = 0, kr = 0, wv = 0;
+  int32_t* kz = NULL;
+  int64_t nchunks = (N + OR_RICE_CHUNK - 1) / OR_RICE_CHUNK, rice_words = 0;
+  if (corr_codec == 1 && wk > 0) {
+    kz = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+    for (int64_t e = 0; e < N; ++e) kz[e] = esc[e] ? 0 : k[e];
+    or_rice_choose(kz, N, OR_RICE_CHUNK, &kr, &wv);
+    rice_words = (or_rice_bits(kz, N, OR_RICE_CHUNK, kr, wv) + 31) / 32;
+    if (2 + nchunks + rice_words < corr_w) {
+      rice = 1;
+      dense = 0;
+      corr_w = 2 + nchunks + rice_words;
+    }
+  }
 
   int64_t off_wq = 16;
   int64_t off_v = off_wq + al(r, 8);
@@ -540,10 +560,10 @@ int64_t or_pack_record(int r, int side, int n, int64_t L, int64_t M, int dtype,
   int64_t off_ei = off_c + al(corr_w * 4, 8);
   int64_t off_ev = off_ei + al(nesc * 4, 8);
   int64_t sz = al(off_ev + al(nesc * es, 8), 16);
-  if (sz > cap) return OR_ERR_CAPACITY;
+  if (sz > cap) { free(kz); return OR_ERR_CAPACITY; }
   memset(rec, 0, (size_t)sz);
   rec[0] = (uint8_t)r;
-  rec[1] = (uint8_t)((side ? OR_FLAG_SPATIAL : 0) | (dense ? OR_FLAG_DENSE : 0));
+  rec[1] = (uint8_t)((side ? OR_FLAG_SPATIAL : 0) | (dense ? OR_FLAG_DENSE : 0) | (rice ? OR_FLAG_RICE : 0));
   rec[2] = (uint8_t)wk;
   rec[3] = (uint8_t)ib;
   wr32(rec + 4, (uint32_t)ncorr);
@@ -559,7 +579,11 @@ int64_t or_pack_record(int r, int side, int n, int64_t L, int64_t M, int dtype,
     wbase += (L * wq[c] + 31) / 32;
   }
   uint32_t* cw = (uint32_t*)(rec + off_c);
-  if (wk > 0) {
+  if (rice) {
+    cw[0] = (uint32_t)rice_words;
+    cw[1] = (uint32_t)kr | ((uint32_t)wv << 8);
+    or_rice_encode(kz, N, OR_RICE_CHUNK, kr, wv, cw + 2 + nchunks, rice_words, cw + 2);
+  } else if (wk > 0) {
     if (dense) {
       for (int64_t e = 0; e < N; ++e) put_bits(cw, (uint64_t)e * wk, esc[e] ? 0u : zz(k[e]), wk);
     } else {
@@ -582,6 +606,7 @@ int64_t or_pack_record(int r, int side, int n, int64_t L, int64_t M, int dtype,
     put_val(rec + off_ev + i * es, A[l * n + j], dtype);
     ++i;
   }
+  free(kz);
   return sz;
 }
 
@@ -687,7 +712,7 @@ int64_t or_block_compress(const or_params* p, const void* field, int64_t b, cons
     int64_t rawsz = raw_record_bytes(N, p->dtype);
     uint8_t* tmp = (uint8_t*)malloc((size_t)(rawsz + 4096 + 64 * (int64_t)n * n));
     sz = or_pack_record(r, g.side, n, L, g.M, p->dtype, Vr, qr, kk, esc, A, tmp,
-                        rawsz + 4096 + 64 * (int64_t)n * n);
+                        rawsz + 4096 + 64 * (int64_t)n * n, p->corr_codec);
     if (sz >= rawsz) {
       raw = 1;
     } else if (sz > rec_cap) {
@@ -883,8 +908,14 @@ int or_decompress(const void* stream, int64_t bytes, void* out, int64_t out_cap,
       int bad = 0;
       for (int c = 0; c < r; ++c) { if (wq[c] > 32) bad = 1; qwords += (L * wq[c] + 31) / 32; }
       int dense = (flags & OR_FLAG_DENSE) ? 1 : 0;
-      int64_t corr_w = wk == 0 ? 0 : (dense ? (N * wk + 31) / 32 : (ncorr * (ib + wk) + 31) / 32);
+      int rice = (flags & OR_FLAG_RICE) ? 1 : 0;
       int64_t off_c = off_q + al(qwords * 4, 8);
+      int64_t nchunks = (N + OR_RICE_CHUNK - 1) / OR_RICE_CHUNK, rice_words = 0;
+      if (rice && (wk == 0 || dense || off_c + 8 > nbytes)) { err = OR_ERR_CORRUPT; free(X); continue; }
+      if (rice) rice_words = rd32(rec + off_c);
+      int64_t corr_w = wk == 0 ? 0
+                       : rice ? 2 + nchunks + rice_words
+                              : (dense ? (N * wk + 31) / 32 : (ncorr * (ib + wk) + 31) / 32);
       int64_t off_ei = off_c + al(corr_w * 4, 8);
       int64_t off_ev = off_ei + al(nesc * 4, 8);
       int64_t need = al(off_ev + al(nesc * es, 8), 16);
@@ -910,7 +941,22 @@ int or_decompress(const void* stream, int64_t bytes, void* out, int64_t out_cap,
           X[e] = D[l * n + j];
         }
       const uint32_t* cw = (const uint32_t*)(rec + off_c);
-      if (wk > 0) {
+      if (rice) {
+        const int kr = (int)(cw[1] & 0xffu), wv = (int)((cw[1] >> 8) & 0xffu);
+        int32_t* kd = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+        if (kr > 20 || wv > 32 ||
+            or_rice_decode(cw + 2 + nchunks, rice_words, cw + 2, N, OR_RICE_CHUNK, kr, wv, kd) != 0) {
+          bad = 1;
+        } else {
+          for (int64_t e = 0; e < N; ++e) {
+            const int32_t kv = kd[e];
+            if (kv == 0) continue;
+            if (p.dtype == OR_F32) X[e] = (double)fmaf((float)kv, (float)step, (float)X[e]);
+            else X[e] = fma((double)kv, step, X[e]);
+          }
+        }
+        free(kd);
+      } else if (wk > 0) {
         if (dense) {
           for (int64_t e = 0; e < N; ++e) {
             uint32_t z = get_bits(cw, (uint64_t)e * wk, wk);

@@ -56,6 +56,10 @@ typedef struct {
      order instead of their own eigenvectors; other blocks are unchanged. */
   const double* basis;
   int32_t basis_n;
+  /* 0: corrections as dense or index list (the stream the CUDA library
+     writes); 1: a Rice-coded section too, wherever it is smaller (a proposed
+     format, see or_pack_record). */
+  int32_t corr_codec;
 } or_params;
 
 /* Geometry of one block. */
@@ -126,7 +130,7 @@ int     or_decompress(const void* stream, int64_t bytes, void* out, int64_t out_
  * order, esc marks escaped points (raw values taken from A). */
 int64_t or_pack_record(int r, int side, int n, int64_t L, int64_t M, int dtype,
                        const double* Vst, const int32_t* q, const int32_t* k,
-                       const uint8_t* esc, const double* A, uint8_t* rec, int64_t cap);
+                       const uint8_t* esc, const double* A, uint8_t* rec, int64_t cap, int corr_codec);
 
 /* Rice-coded corrections, a proposed record section that records do not use
  * yet (the layout is described in dls_oracle.c): exact size in bits, the

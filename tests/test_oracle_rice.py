@@ -116,3 +116,49 @@ def test_smaller_than_the_current_section_on_real_corrections():
         kr, wv = oracle.rice_choose(k, 1024)
         rice += oracle.rice_bits(k, 1024, kr, wv) + 32 * (-(-N // 1024)) + 10   # offsets + parameters
     assert used >= 4 and rice < 0.55 * cur, (used, rice, cur)
+
+
+@pytest.mark.parametrize("rel,eb_type", [(1e-3, oracle.EB_ABS), (1e-4, oracle.EB_ABS), (1e-3, oracle.EB_REL_RANGE)])
+def test_rice_records_decode_to_the_same_field(rel, eb_type):
+    """Records with the Rice section (corr_codec = 1) carry the same
+    corrections as the default records: the decompressed fields are
+    bit-identical, the bound holds, and the stream is smaller."""
+    dims = (48, 48, 32, 32)
+    f = synth.modes3d(*dims, seed=2, count=64).numpy()
+    eb = rel * float(f.max() - f.min()) if eb_type == oracle.EB_ABS else rel
+    base = oracle.Config(dims, (16, 16, 16, 16), oracle.F32, eb=eb, eb_type=eb_type, rank_cap=16)
+    rice = oracle.Config(dims, (16, 16, 16, 16), oracle.F32, eb=eb, eb_type=eb_type, rank_cap=16, corr_codec=1)
+    st0, s0, _ = oracle.compress(base, f)
+    st1, s1, _ = oracle.compress(rice, f)
+    assert st0 == 0 and st1 == 0
+    st0, r0 = oracle.decompress(s0)
+    st1, r1 = oracle.decompress(s1)
+    assert st0 == 0 and st1 == 0
+    assert np.array_equal(r0.view(np.uint32), r1.view(np.uint32))
+    bound = eb if eb_type == oracle.EB_ABS else rel * float(f.max() - f.min())
+    assert np.abs(r1.astype(np.float64) - f.astype(np.float64)).max() <= bound
+    assert s1.size < s0.size, (s1.size, s0.size)
+
+
+def test_rice_record_corruption_is_detected():
+    dims = (32, 32, 16, 16)
+    f = synth.modes3d(*dims, seed=3, count=64).numpy()
+    cfg = oracle.Config(dims, (16, 16, 16, 16), oracle.F32, eb=1e-4 * float(f.max() - f.min()), rank_cap=16,
+                        corr_codec=1)
+    st, s, _ = oracle.compress(cfg, f)
+    assert st == 0
+    hdr = s[:128].view(np.uint64)
+    payp, offp = int(hdr[14]), int(hdr[13])
+    off0 = int(s[offp:offp + 8].view(np.uint64)[0])
+    rec = payp + off0
+    assert s[rec + 1] & 8                                   # the first record took the Rice section
+    bad = s.copy()
+    # the Rice word count sits at the start of the correction section; make it disagree with the record size
+    r = int(s[rec])
+    n, es, L = 16, 4, 16 * 16 * 16
+    wq = s[rec + 16:rec + 16 + r]
+    al = lambda x, a: (x + a - 1) // a * a
+    off_c = 16 + al(r, 8) + al(n * r * es, 8) + al(sum((L * int(w) + 31) // 32 for w in wq) * 4, 8)
+    bad[rec + off_c:rec + off_c + 4] = np.frombuffer(np.uint32(10 ** 6).tobytes(), np.uint8)
+    st, _ = oracle.decompress(bad)
+    assert st != 0
