@@ -157,3 +157,133 @@ def decompress(res) -> np.ndarray:
         rec = reconstruct(res["phi"], idx, q, res["delta"])
         out[t, z0:z0 + pz, y0:y0 + py, x0:x0 + px] = rec.reshape(pz, py, px)
     return out
+
+
+# ---------------------------------------------------------------- stream
+# Readings for the stored form (the paper keeps the DOFs and the basis, then
+# gzip, Sec. 2.5-2.6; it gives no layout):
+# - header (little-endian): b"DLSG", u32 version 1, u32 M, u32 px, py, pz,
+#   u64 nx, ny, nz, nt, f64 eps_l^2, f64 delta, u64 records  (80 bytes);
+# - the basis once, M x M float64, mode after mode;
+# - (records + 1) u64 byte offsets of the records (a scan of their sizes, so
+#   that every record is addressable, Sec. 2.7.2);
+# - records in (t, z, y, x) patch order: u32 n, u8 wv, 3 zero bytes, then n
+#   mode indices of ib = bit_width(M - 1) bits and n zigzag(q) of wv bits,
+#   LSB first in 32-bit words; each record padded to 8 bytes.
+_MAGIC = b"DLSG"
+_HDR = 80
+
+
+def _width(x: int) -> int:
+    return int(x).bit_length()
+
+
+def _zz(q):
+    q = np.asarray(q, dtype=np.int64)
+    return ((q << 1) ^ (q >> 63)).astype(np.uint64)
+
+
+def _pack_bits(vals, width, nbits_total):
+    words = np.zeros(max(1, (nbits_total + 31) // 32), np.uint64)
+    pos = 0
+    for v in vals:
+        v = int(v)
+        for i in range(width):
+            if (v >> i) & 1:
+                words[(pos + i) >> 5] |= np.uint64(1 << ((pos + i) & 31))
+        pos += width
+    return words.astype(np.uint32), pos
+
+
+def _record(idx, q, M):
+    n = len(idx)
+    ib = _width(M - 1)
+    z = _zz(q)
+    wv = _width(int(z.max())) if n else 0
+    nbits = n * (ib + wv)
+    w1, p1 = _pack_bits(idx, ib, nbits)
+    words = w1.astype(np.uint64)
+    pos = p1
+    for v in z:                                   # values after the indices
+        v = int(v)
+        for i in range(wv):
+            if (v >> i) & 1:
+                words[(pos + i) >> 5] |= np.uint64(1 << ((pos + i) & 31))
+        pos += wv
+    body = words.astype(np.uint32)[: (nbits + 31) // 32].tobytes()
+    rec = np.uint32(n).tobytes() + bytes([wv, 0, 0, 0]) + body
+    return rec + bytes((-len(rec)) % 8)
+
+
+def pack(res) -> bytes:
+    """The stream of a compress() result."""
+    phi = res["phi"]
+    M = phi.shape[0]
+    px, py, pz = res["patch"]
+    nx, ny, nz, nt = res["dims"]
+    recs = [_record(idx, q, M) for _, _, idx, q, _ in res["recs"]]
+    offs = np.zeros(len(recs) + 1, np.uint64)
+    offs[1:] = np.cumsum([len(r) for r in recs])
+    hdr = (_MAGIC + np.array([1, M, px, py, pz], np.uint32).tobytes()
+           + np.array([nx, ny, nz, nt], np.uint64).tobytes()
+           + np.array([res["eps_l2"], res["delta"]], np.float64).tobytes()
+           + np.uint64(len(recs)).tobytes())
+    assert len(hdr) == _HDR
+    basis = np.ascontiguousarray(phi.T).astype(np.float64).tobytes()   # mode after mode
+    return hdr + basis + offs.tobytes() + b"".join(recs)
+
+
+def _get_bits(words, pos, width):
+    v = 0
+    for i in range(width):
+        p = pos + i
+        v |= int((int(words[p >> 5]) >> (p & 31)) & 1) << i
+    return v
+
+
+def unpack(stream: bytes):
+    """The compress()-like result of a stream (records without their errors),
+    or None when the stream is malformed."""
+    b = bytes(stream)
+    if len(b) < _HDR or b[:4] != _MAGIC:
+        return None
+    ver, M, px, py, pz = np.frombuffer(b[4:24], np.uint32)
+    nx, ny, nz, nt = (int(v) for v in np.frombuffer(b[24:56], np.uint64))
+    eps_l2, delta = np.frombuffer(b[56:72], np.float64)
+    nrec = int(np.frombuffer(b[72:80], np.uint64)[0])
+    M, px, py, pz = int(M), int(px), int(py), int(pz)
+    if ver != 1 or M != px * py * pz or M < 1:
+        return None
+    if any(d % p for d, p in zip((nx, ny, nz), (px, py, pz))) or nrec != nt * (nx // px) * (ny // py) * (nz // pz):
+        return None
+    at = _HDR + 8 * M * M
+    if len(b) < at + 8 * (nrec + 1):
+        return None
+    phi = np.frombuffer(b[_HDR:at], np.float64).reshape(M, M).T.copy()
+    offs = np.frombuffer(b[at:at + 8 * (nrec + 1)], np.uint64).astype(np.int64)
+    base = at + 8 * (nrec + 1)
+    if offs[0] != 0 or np.any(np.diff(offs) < 8) or base + offs[-1] != len(b):
+        return None
+    ib = _width(M - 1)
+    recs = []
+    i = 0
+    for t in range(nt):
+        for z0 in range(0, nz, pz):
+            for y0 in range(0, ny, py):
+                for x0 in range(0, nx, px):
+                    r = b[base + offs[i]: base + offs[i + 1]]
+                    n = int(np.frombuffer(r[:4], np.uint32)[0])
+                    wv = r[4]
+                    need = 8 + ((n * (ib + wv) + 31) // 32) * 4
+                    if n > M or wv > 63 or need + ((-need) % 8) != len(r):
+                        return None
+                    words = np.frombuffer(r[8:8 + ((n * (ib + wv) + 31) // 32) * 4], np.uint32)
+                    idx = np.array([_get_bits(words, s * ib, ib) for s in range(n)], np.int64)
+                    zz = [_get_bits(words, n * ib + s * wv, wv) for s in range(n)]
+                    q = np.array([(v >> 1) ^ -(v & 1) for v in zz], np.int64)
+                    if np.any(idx >= M):
+                        return None
+                    recs.append((t, (x0, y0, z0), idx, q, None))
+                    i += 1
+    return dict(phi=phi, sv=None, patch=(px, py, pz), dims=(nx, ny, nz, nt), eps_l2=float(eps_l2),
+                delta=float(delta), recs=recs)

@@ -137,3 +137,41 @@ def test_tiling_rule_and_origins():
     o2 = synth.patch_origins((20, 12, 9), (4, 4, 4), 500, seed=8)
     assert np.array_equal(o1, o2) and o1.min() >= 0
     assert o1[:, 0].max() <= 16 and o1[:, 1].max() <= 8 and o1[:, 2].max() <= 5
+
+
+def _small_result(eps_t=1.0):
+    f = synth.modes3d(16, 16, 16, 8, seed=5, count=24).numpy()[0].astype(np.float64)
+    origins = synth.patch_origins((16, 16, 16), (4, 4, 4), 256, seed=6)
+    return f, gb.compress(f, 4, eps_t, origins)
+
+
+def test_stream_round_trip_and_size():
+    """pack/unpack keep every record's kept modes and values; the size is the
+    header, the basis, the offsets and the records as laid out."""
+    f, res = _small_result()
+    s = gb.pack(res)
+    back = gb.unpack(s)
+    assert back is not None and len(back["recs"]) == len(res["recs"])
+    for a, b in zip(res["recs"], back["recs"]):
+        assert a[0] == b[0] and a[1] == b[1]
+        assert np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3])
+    assert np.array_equal(gb.decompress(back), gb.decompress(res))
+    M = res["phi"].shape[0]
+    ib = (M - 1).bit_length()
+    size = 80 + 8 * M * M + 8 * (len(res["recs"]) + 1)
+    for _, _, idx, q, _ in res["recs"]:
+        wv = max((int(abs(2 * v) - (v < 0)) for v in q), default=0).bit_length()
+        body = 8 + 4 * ((len(idx) * (ib + wv) + 31) // 32)
+        size += body + (-body) % 8
+    assert len(s) == size
+
+
+def test_malformed_streams_are_rejected():
+    _, res = _small_result()
+    s = gb.pack(res)
+    assert gb.unpack(s[:100]) is None                      # truncated
+    assert gb.unpack(b"XXXX" + s[4:]) is None              # magic
+    bad = bytearray(s)
+    at = 80 + 8 * 64 * 64 + 8                              # second offset
+    bad[at:at + 8] = np.uint64(3).tobytes()                # a record shorter than its header
+    assert gb.unpack(bytes(bad)) is None
