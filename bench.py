@@ -73,7 +73,8 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_r{index}.csv")
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), f"dls_bench_clocks_{os.getpid()}_{index}.csv")
 
     def start(self):
         try:

@@ -185,10 +185,15 @@ int dls_compress_host(const dls_params* p, const void* h_in, void* h_out, size_t
  *     workspace per point: up to roughly 8 million points).
  *   - The first call on each device looks up the array's device address with
  *     that device current; make that first call before any stream capture.
+ *     Under CUDA's lazy module loading (the default) that lookup is also when
+ *     the array is placed in device memory, so the first call needs 64 MiB of
+ *     free device memory: make it before the caller's pools take the device,
+ *     or set CUDA_MODULE_LOADING=EAGER.  Later calls allocate nothing.
+ *   - Invalid parameters return the status dls_compress returns for them.
  *   - Every call on a device shares the array: calls that overlap on the GPU
  *     (different streams or host threads) race and must be serialised by the
  *     caller.  Each call clears what it needs and overwrites the rest.
- *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call. */
+ *   - Calls no cudaMalloc, cudaFree or allocating library routine. */
 int dls_compress_noalloc(const dls_params* p, const void* d_in, void* d_out, size_t out_cap,
                          size_t* out_bytes, dls_stream_t stream);
 
@@ -234,6 +239,22 @@ int dls_stage_quantize(const float* d_c, int64_t n, double delta, int32_t* d_q, 
                        dls_stream_t stream);
 int dls_stage_correct(const float* d_x, const float* d_xh, int64_t n, double eb, int32_t* d_k,
                       dls_stream_t stream);
+/* The same correction through the code path a compression takes, so that
+ * each path can be tested on identical inputs against the FP64 definition:
+ *   DLS_CORR_PATH_EXACT:  the decision of the row-loading kernel (as
+ *                         dls_stage_correct);
+ *   DLS_CORR_PATH_SPARSE: the per-block kernel's sparse encode pass: elements
+ *                         with |fl(x - xh)| below eb (1 - 1e-6), rounded down,
+ *                         get k = 0 without a decision; the others take its
+ *                         branch-free FP32 test and, where that test cannot
+ *                         decide, the FP64 definition;
+ *   DLS_CORR_PATH_DENSE:  the per-block kernel's dense encode pass: every
+ *                         element takes the FP32 test, then the FP64
+ *                         definition where the test cannot decide.
+ * All three return exactly what dls_stage_correct returns. */
+enum { DLS_CORR_PATH_EXACT = 0, DLS_CORR_PATH_SPARSE = 1, DLS_CORR_PATH_DENSE = 2 };
+int dls_stage_correct_path(const float* d_x, const float* d_xh, int64_t n, double eb, int32_t path, int32_t* d_k,
+                           dls_stream_t stream);
 
 /* Block-rank MLP (not in the paper): 32 block features -> 64 -> 64 -> 1, ReLU,
  * BF16 weights with FP32 accumulation.  Parameters are DLS_MLP_NPARAM floats:
@@ -305,6 +326,18 @@ typedef struct {
   double eb[64], delta[64], step[64];
 } dls_stream_info;
 int dls_stream_info_get(const void* d_comp, size_t comp_bytes, dls_stream_info* h_info);
+
+/* Fault injection for tests (no GPU fault is involved).  kind
+ * DLS_FAULT_WITHHOLD_CHUNK: in every compression launched after this call
+ * (plans: captured at dls_plan_create), the per-block kernel of the FP32 and
+ * TF32X3 forms never issues the copy of the first staged chunk of block
+ * `arg` (an index into the call's block range).  Its bounded wait for that
+ * chunk runs out after about a second of SM clock, the kernel drains the
+ * copies it did issue and ends, and the call returns DLS_ERR_TIMEOUT.
+ * DLS_FAULT_NONE (arg ignored) switches the hook off.  Not thread-safe with
+ * respect to concurrent compressions; meant for tests only. */
+enum { DLS_FAULT_NONE = 0, DLS_FAULT_WITHHOLD_CHUNK = 1 };
+int dls_set_fault_hook(int32_t kind, int64_t arg);
 
 /* Static text for a DLS_* status ("unknown status" for other values). */
 const char* dls_status_string(int status);

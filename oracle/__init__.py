@@ -131,6 +131,11 @@ def lib():
             L.or_rice_encode.argtypes = [i32p, C.c_int64, C.c_int, C.c_int, C.c_int, u32p, C.c_int64, u32p]
             L.or_rice_decode.restype = C.c_int
             L.or_rice_decode.argtypes = [u32p, C.c_int64, u32p, C.c_int64, C.c_int, C.c_int, C.c_int, i32p]
+            L.or_parse_record.restype = C.c_int
+            L.or_parse_record.argtypes = [up, C.c_int64, C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int,
+                                          C.POINTER(C.c_int), C.POINTER(C.c_int), dp, ip, ip, up, dp]
+            L.or_project_f32.restype = None
+            L.or_project_f32.argtypes = [dp, C.c_int64, C.c_int, dp, C.c_int, dp]
             L.or_pack_record.restype = C.c_int64
             L.or_pack_record.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int,
                                          dp, ip, ip, up, dp, up, C.c_int64, C.c_int]
@@ -301,6 +306,42 @@ def pack_record(r, side, n, L, M, dtype, Vst, q, k, esc, A, corr_codec=0) -> byt
     if sz < 0:
         raise RuntimeError(f"or_pack_record failed: {sz}")
     return buf[:sz].tobytes()
+
+
+def parse_record(rec, side, n, L, M, dtype):
+    """Inverse of pack_record for one record of the given block geometry
+    (the record layout of Sec. 2.7.2).  Returns None for a record that does
+    not follow the layout exactly, else a dict with r, flags, Vst (n x r),
+    q (L x r), k and esc (element order) and escval (the raw values of
+    escaped points; all values for a raw record)."""
+    rec = np.ascontiguousarray(np.frombuffer(bytes(rec), np.uint8))
+    N = L * n
+    r, fl = C.c_int(0), C.c_int(0)
+    Vst = np.zeros(n * n, np.float64)
+    q = np.zeros(L * n, np.int32)
+    k = np.zeros(N, np.int32)
+    esc = np.zeros(N, np.uint8)
+    ev = np.zeros(N, np.float64)
+    st = lib().or_parse_record(_p(rec, C.c_uint8), rec.size, side, n, L, M, dtype, C.byref(r), C.byref(fl),
+                               _p(Vst, C.c_double), _p(q, C.c_int32), _p(k, C.c_int32), _p(esc, C.c_uint8),
+                               _p(ev, C.c_double))
+    if st != OK:
+        return None
+    rr = r.value
+    return dict(r=rr, flags=fl.value, Vst=Vst[: n * rr].reshape(n, rr), q=q[: L * rr].reshape(L, rr), k=k,
+                esc=esc.astype(bool), escval=ev)
+
+
+def project_f32(A: np.ndarray, Vst: np.ndarray) -> np.ndarray:
+    """Coefficients as the FP32 form defines them (shifted binary32
+    projection in a fixed order; Sec. 2.5 Eq. 5 evaluated in that precision)."""
+    A = np.ascontiguousarray(A, np.float64)
+    Vst = np.ascontiguousarray(Vst, np.float64)
+    L, n = A.shape
+    r = Vst.shape[1]
+    Cm = np.zeros((L, max(r, 1)), np.float64)
+    lib().or_project_f32(_p(A, C.c_double), L, n, _p(Vst, C.c_double), r, _p(Cm, C.c_double))
+    return Cm[:, :r]
 
 
 def block_compress(cfg: Config, field: np.ndarray, b: int, want_linear=False):

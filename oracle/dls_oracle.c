@@ -1005,8 +1005,10 @@ int or_decompress(const void* stream, int64_t bytes, void* out, int64_t out_cap,
 }
 
 /* ------------------------------------------------------------------ */
-/* Rice-coded corrections: a proposed record section (records do not   */
-/* use it yet).  The corrections k[0..N) of a block, in element order,  */
+/* Rice-coded corrections: a record section that or_pack_record takes  */
+/* with corr_codec = 1 (flag 8) where it is smaller; the CUDA packers   */
+/* and decoder do not write or read it.  The corrections k[0..N) of a   */
+/* block, in element order,                                             */
 /* are cut into chunks of `chunk` elements.  Within a chunk every       */
 /* nonzero is written as the Rice code of the zeros before it (counted  */
 /* from the chunk start or the previous nonzero), then zigzag(k) - 1 in */
@@ -1139,4 +1141,118 @@ int or_rice_decode(const uint32_t* words, int64_t nwords, const uint32_t* off, i
     }
   }
   return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Record parser: the inverse of or_pack_record (Sec. 2.7.2 record      */
+/* layout), for tests that replay a stored record through the steps     */
+/* above.  Given the block's geometry it returns the rank, the flags,   */
+/* the stored modes Vst (n x r, leading dimension r), the coefficient   */
+/* codes q (L x r, leading dimension r), the corrections k and the      */
+/* escape marks esc (element order), and the raw escaped values escval  */
+/* (element order, 0 elsewhere).  Raw records give r = 0, flags with    */
+/* OR_FLAG_RAW and the values in escval.  0, or OR_ERR_CORRUPT when the */
+/* record does not follow the layout exactly.                           */
+/* ------------------------------------------------------------------ */
+int or_parse_record(const uint8_t* rec, int64_t nbytes, int side, int n, int64_t L, int64_t M, int dtype,
+                    int* r_out, int* flags_out, double* Vst, int32_t* q, int32_t* k, uint8_t* esc,
+                    double* escval) {
+  const int64_t N = L * n;
+  const int es = esize(dtype);
+  if (nbytes < 16 || (int64_t)rd32(rec + 12) != nbytes) return OR_ERR_CORRUPT;
+  const int r = rec[0], flags = rec[1], wk = rec[2], ib = rec[3];
+  const int64_t ncorr = rd32(rec + 4), nesc = rd32(rec + 8);
+  *r_out = 0;
+  *flags_out = flags;
+  memset(k, 0, sizeof(int32_t) * (size_t)N);
+  memset(esc, 0, (size_t)N);
+  memset(escval, 0, sizeof(double) * (size_t)N);
+  if (((flags & OR_FLAG_SPATIAL) ? 1 : 0) != side) return OR_ERR_CORRUPT;
+  if (flags & OR_FLAG_RAW) {
+    if (nbytes != raw_record_bytes(N, dtype)) return OR_ERR_CORRUPT;
+    for (int64_t e = 0; e < N; ++e) escval[e] = get_val(rec + 16 + e * es, dtype);
+    return OR_OK;
+  }
+  if ((flags & ~(OR_FLAG_SPATIAL | OR_FLAG_DENSE)) != 0) return OR_ERR_CORRUPT;   /* no Rice here */
+  if (r > n || wk > 32 || ib != nbits((uint32_t)(N - 1)) || ncorr > N || nesc > N) return OR_ERR_CORRUPT;
+  const uint8_t* wq = rec + 16;
+  const int64_t off_v = 16 + al(r, 8);
+  const int64_t off_q = off_v + al((int64_t)n * r * es, 8);
+  int64_t qwords = 0;
+  for (int c = 0; c < r; ++c) {
+    if (wq[c] > 32) return OR_ERR_CORRUPT;
+    qwords += (L * wq[c] + 31) / 32;
+  }
+  const int dense = (flags & OR_FLAG_DENSE) ? 1 : 0;
+  const int64_t corr_w = wk == 0 ? 0 : (dense ? (N * wk + 31) / 32 : (ncorr * (ib + wk) + 31) / 32);
+  const int64_t off_c = off_q + al(qwords * 4, 8);
+  const int64_t off_ei = off_c + al(corr_w * 4, 8);
+  const int64_t off_ev = off_ei + al(nesc * 4, 8);
+  if (al(off_ev + al(nesc * es, 8), 16) != nbytes) return OR_ERR_CORRUPT;
+  for (int c = 0; c < r; ++c)
+    for (int j = 0; j < n; ++j) Vst[j * r + c] = get_val(rec + off_v + ((int64_t)c * n + j) * es, dtype);
+  const uint32_t* qw = (const uint32_t*)(rec + off_q);
+  int64_t wbase = 0;
+  for (int c = 0; c < r; ++c) {
+    for (int64_t l = 0; l < L; ++l) {
+      const uint32_t z = get_bits(qw + wbase, (uint64_t)l * wq[c], wq[c]);
+      q[l * r + c] = (int32_t)((z >> 1) ^ (0u - (z & 1u)));
+    }
+    wbase += (L * wq[c] + 31) / 32;
+  }
+  const uint32_t* cw = (const uint32_t*)(rec + off_c);
+  if (wk > 0 && dense) {
+    for (int64_t e = 0; e < N; ++e) {
+      const uint32_t z = get_bits(cw, (uint64_t)e * wk, wk);
+      k[e] = (int32_t)((z >> 1) ^ (0u - (z & 1u)));
+    }
+  } else if (wk > 0) {
+    int64_t prev = -1;
+    for (int64_t ci = 0; ci < ncorr; ++ci) {
+      const uint64_t pos = (uint64_t)ci * (ib + wk);
+      const int64_t e = get_bits(cw, pos, ib);
+      const uint32_t z = get_bits(cw, pos + ib, wk);
+      if (e >= N || e <= prev) return OR_ERR_CORRUPT;     /* increasing element order */
+      k[e] = (int32_t)((z >> 1) ^ (0u - (z & 1u)));
+      prev = e;
+    }
+  }
+  int64_t prev = -1;
+  for (int64_t i = 0; i < nesc; ++i) {
+    const int64_t e = rd32(rec + off_ei + 4 * i);
+    if (e >= N || e <= prev) return OR_ERR_CORRUPT;
+    esc[e] = 1;
+    escval[e] = get_val(rec + off_ev + i * es, dtype);
+    prev = e;
+  }
+  *r_out = r;
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Coefficients as the FP32 (mixed-precision) form defines them, so     */
+/* that its quantized codes can be compared code for code: the          */
+/* projection of Sec. 2.5 Eq. 5 evaluated in binary32 on a shifted row, */
+/*   d_j = fl(x_j - x_0),  s_m = fma chain over j = m, m+4, ... (m < 4), */
+/*   c = fma(x_0, vsum_k, fl(fl(s_0 + s_1) + fl(s_2 + s_3))),           */
+/* with vsum_k = fl32(sum_j Vst[j][k]) summed in double, j ascending.   */
+/* The FP64-semantics quantizer (or_quantize on these values) then      */
+/* takes the same decision as the kernel.  C is L x r (leading r).      */
+/* ------------------------------------------------------------------ */
+void or_project_f32(const double* A, int64_t L, int n, const double* Vst, int r, double* C) {
+  for (int k = 0; k < r; ++k) {
+    double cs = 0.0;
+    for (int j = 0; j < n; ++j) cs += (double)(float)Vst[j * r + k];
+    const float vsum = (float)cs;
+    for (int64_t l = 0; l < L; ++l) {
+      const float a0 = (float)A[l * n];
+      float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      for (int j = 0; j < n; ++j) {
+        const float d = (float)A[l * n + j] - a0;
+        s[j & 3] = fmaf(d, (float)Vst[j * r + k], s[j & 3]);
+      }
+      const float sum = (s[0] + s[1]) + (s[2] + s[3]);
+      C[l * r + k] = (double)fmaf(a0, vsum, sum);
+    }
+  }
 }

@@ -20,7 +20,8 @@
  *   - the stream (addressable header, offset table from an exclusive scan,
  *     tightly packed per-block arrays) follows Sec. 2.7.2.
  * Quantization of coefficients (in place of bit-grooming) and the pointwise
- * correction pass are the readings documented in the design doc.
+ * correction pass are readings of the paper's L-infinity metric (Sec. 2.4)
+ * and of its bit-grooming step (Sec. 2.5), stated where they are defined.
  *
  * All functions are plain C, single-threaded per block; or_compress and
  * or_decompress run blocks in parallel with OpenMP.
@@ -132,8 +133,8 @@ int64_t or_pack_record(int r, int side, int n, int64_t L, int64_t M, int dtype,
                        const double* Vst, const int32_t* q, const int32_t* k,
                        const uint8_t* esc, const double* A, uint8_t* rec, int64_t cap, int corr_codec);
 
-/* Rice-coded corrections, a proposed record section that records do not use
- * yet (the layout is described in dls_oracle.c): exact size in bits, the
+/* Rice-coded corrections, the record section or_pack_record takes with
+ * corr_codec = 1 (the layout is described in dls_oracle.c): exact size in bits, the
  * parameters with the fewest bits, encoder (bits written, -1 if cap_words is
  * too small; off gets each chunk's bit offset) and decoder (0, or -1 for a
  * malformed section). */
@@ -143,6 +144,14 @@ int64_t or_rice_encode(const int32_t* k, int64_t N, int chunk, int kr, int wv, u
                        int64_t cap_words, uint32_t* off);
 int     or_rice_decode(const uint32_t* words, int64_t nwords, const uint32_t* off, int64_t N, int chunk,
                        int kr, int wv, int32_t* k);
+
+/* Inverse of or_pack_record for one record of the given geometry (raw
+ * records return their values in escval); 0 or OR_ERR_CORRUPT. */
+int     or_parse_record(const uint8_t* rec, int64_t nbytes, int side, int n, int64_t L, int64_t M, int dtype,
+                        int* r, int* flags, double* Vst, int32_t* q, int32_t* k, uint8_t* esc, double* escval);
+/* Coefficients of the FP32 (mixed-precision) form: the shifted binary32
+ * projection in its fixed order (see dls_oracle.c). */
+void    or_project_f32(const double* A, int64_t L, int n, const double* Vst, int r, double* C);
 
 #ifdef __cplusplus
 }

@@ -1,5 +1,6 @@
 // Host side of the C ABI: parameter validation, block plan, workspace layout,
 // launch sequence and status readback.  See include/dls.h for the contract.
+#include <atomic>
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -485,6 +486,13 @@ static void tune_store(const std::string& key, int variant, const float* ms) {
 
 }  // namespace dls
 
+namespace dls {
+namespace {
+std::atomic<int64_t> g_withheld{-1};
+}
+int64_t fault_withheld_block() { return g_withheld.load(); }
+}  // namespace dls
+
 using namespace dls;
 
 extern "C" {
@@ -660,6 +668,16 @@ int dls_mlp_train(float* d_params, float* d_adam, const float* d_feat, const flo
   return DLS_OK;
 }
 
+int dls_set_fault_hook(int32_t kind, int64_t arg) {
+  if (kind == DLS_FAULT_NONE) {
+    g_withheld.store(-1);
+    return DLS_OK;
+  }
+  if (kind != DLS_FAULT_WITHHOLD_CHUNK || arg < 0) return DLS_ERR_INVALID_ARG;
+  g_withheld.store(arg);
+  return DLS_OK;
+}
+
 int dls_stage_quantize(const float* d_c, int64_t n, double delta, int32_t* d_q, int32_t* d_ovf,
                        dls_stream_t stream) {
   if (n < 0 || (n > 0 && (!d_c || !d_q || !d_ovf)) || !(delta > 0.0) || !isfinite(delta)) return DLS_ERR_INVALID_ARG;
@@ -670,8 +688,15 @@ int dls_stage_quantize(const float* d_c, int64_t n, double delta, int32_t* d_q, 
 }
 
 int dls_stage_correct(const float* d_x, const float* d_xh, int64_t n, double eb, int32_t* d_k, dls_stream_t stream) {
-  if (n < 0 || (n > 0 && (!d_x || !d_xh || !d_k)) || !(eb > 0.0) || !isfinite(eb)) return DLS_ERR_INVALID_ARG;
-  int st = launch_stage_correct(d_x, d_xh, n, eb, d_k, (cudaStream_t)stream);
+  return dls_stage_correct_path(d_x, d_xh, n, eb, DLS_CORR_PATH_EXACT, d_k, stream);
+}
+
+int dls_stage_correct_path(const float* d_x, const float* d_xh, int64_t n, double eb, int32_t path, int32_t* d_k,
+                           dls_stream_t stream) {
+  if (n < 0 || (n > 0 && (!d_x || !d_xh || !d_k)) || !(eb > 0.0) || !isfinite(eb) || path < DLS_CORR_PATH_EXACT ||
+      path > DLS_CORR_PATH_DENSE)
+    return DLS_ERR_INVALID_ARG;
+  int st = launch_stage_correct(d_x, d_xh, n, eb, path, d_k, (cudaStream_t)stream);
   if (st != DLS_OK) return st;
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   return DLS_OK;

@@ -235,6 +235,14 @@ constexpr int kMlpNParam = kMlpOffB3 + 1;   // 6401
 // rank modes of the kernel
 constexpr int kRankSearch = 0, kRankMlp = 1, kRankTail = 2;
 
+// Validates the parameters and builds the plan (dls_api.cu); DLS_OK or the
+// status dls_compress would return for them.
+int make_plan(const dls_params* p, Plan* out);
+
+// Test hook (dls_set_fault_hook): the block, in a call's block range, whose
+// first staged chunk the per-block kernel never copies; -1 for none.
+int64_t fault_withheld_block();
+
 // ---------------------------------------------------------------- launchers (defined in .cu files)
 int launch_mixed_compress(const Plan& p, const void* d_in, const MixedWork& w, int learned, int variant,
                           int spatial_only, cudaStream_t s);
@@ -252,7 +260,8 @@ int launch_mlp_forward(const float* params, const float* feat, int64_t n, float*
 int mlp_max_batch();
 bool rank_model_loaded();
 int launch_stage_quantize(const float* c, int64_t n, double delta, int32_t* q, int32_t* ovf, cudaStream_t s);
-int launch_stage_correct(const float* x, const float* xh, int64_t n, double eb, int32_t* k, cudaStream_t s);
+int launch_stage_correct(const float* x, const float* xh, int64_t n, double eb, int path, int32_t* k,
+                         cudaStream_t s);
 int launch_plain_compress(const Plan& p, const void* d_in, const Work& w, cudaStream_t s);
 int launch_scan(const Plan& p, const Work& w, size_t out_cap, void* d_out, cudaStream_t s);
 int launch_pack(const Plan& p, const void* d_in, const Work& w, void* d_out, size_t out_cap, cudaStream_t s);

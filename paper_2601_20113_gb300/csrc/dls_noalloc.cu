@@ -11,9 +11,13 @@
 // field and the output buffer.
 //
 // The array is 64 MiB and every GPU on which this library is loaded keeps it
-// until the process exits.  All calls share it: overlapping calls (two streams,
-// two host threads) race on it and must be serialised by the caller.  The
-// previous call's contents are left in it; dls_compress clears the status
+// until the process exits.  Under CUDA's lazy module loading (the default) the
+// array is placed in device memory when the first call on a device looks up
+// its address, so that first call needs 64 MiB of free device memory: make it
+// before the caller's pools take the device (or load modules eagerly with
+// CUDA_MODULE_LOADING=EAGER).  All calls share it: overlapping calls (two
+// streams, two host threads) race on it and must be serialised by the caller.
+// The previous call's contents are left in it; dls_compress clears the status
 // words it reads and writes every other workspace entry before reading it.
 #include <mutex>
 
@@ -49,6 +53,10 @@ int scratch_on_current_device(void** out) {
 
 extern "C" int dls_compress_noalloc(const dls_params* p, const void* d_in, void* d_out, size_t out_cap,
                                     size_t* out_bytes, dls_stream_t stream) {
+  // invalid parameters report what dls_compress would report for them
+  dls::Plan P;
+  const int pst = dls::make_plan(p, &P);
+  if (pst != DLS_OK) return pst;
   const size_t need = dls_workspace_size(p);
   if (need == 0) return DLS_ERR_INVALID_ARG;
   if (need > kNoAllocScratchBytes) return DLS_ERR_WORKSPACE;

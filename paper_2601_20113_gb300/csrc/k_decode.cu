@@ -89,7 +89,9 @@ __global__ void __launch_bounds__(kDecThreads, kDecMinBlocks) k_decode(Plan P, c
   const uint32_t* rec32 = reinterpret_cast<const uint32_t*>(rec);
   const int r = rec[0], flags = rec[1], wk = rec[2], ib = rec[3];
   const int64_t ncorr = rec32[1], nesc = rec32[2], nbytes = rec32[3];
-  if (nbytes != (int64_t)(o1 - o0) || nbytes < 16) {
+  // a flag outside raw / spatial side / dense corrections (a record section
+  // this decoder does not read, such as Rice-coded corrections) is refused
+  if (nbytes != (int64_t)(o1 - o0) || nbytes < 16 || (flags & ~(int)(kFlagRaw | kFlagSpatial | kFlagDense)) != 0) {
     if (tid == 0) atomicOr(&st->corrupt, 1u);
     return;
   }

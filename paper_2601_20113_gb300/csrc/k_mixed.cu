@@ -218,6 +218,30 @@ __device__ void refine64(MxSmem& S, int n) {
   __syncthreads();
 }
 
+// First-order orthonormalisation in FP64 (all threads): X <- X (I + R/2),
+// R = I - X^T X.  It takes the second-order orthogonality error the one
+// refinement step leaves (pairs of modes with gaps near its threshold) to its
+// square, below the rounding of the stored modes to binary32.
+__device__ void reorth64(MxSmem& S, int n) {
+  const int tid = threadIdx.x;
+  const int i = tid / NM, j = tid % NM;
+  const bool act = i < n && j < n;
+  if (act) {
+    double rr = 0.0;
+    for (int k = 0; k < n; ++k) rr = fma(S.X64[k * NM + i], S.X64[k * NM + j], rr);
+    S.R64[i * NM + j] = (i == j ? 1.0 : 0.0) - rr;
+  }
+  __syncthreads();
+  double xn = 0.0;
+  if (act) {
+    xn = S.X64[i * NM + j];
+    for (int k = 0; k < n; ++k) xn = fma(S.X64[i * NM + k], 0.5 * S.R64[k * NM + j], xn);
+  }
+  __syncthreads();
+  if (act) S.X64[i * NM + j] = xn;
+  __syncthreads();
+}
+
 // Sort (stable, descending, lambda < 0 -> 0), sign-normalise, round to f32 (warp 0).
 __device__ void order_basis(MxSmem& S, int n, int lane) {
   if (lane < n) {
@@ -260,13 +284,15 @@ __device__ __forceinline__ void row_coeffs(const MxSmem& S, const float* x, int 
     chat[k] = 0.0f;
     if (k < kq) {
       // shifted by the row's first value: the differences are exact when the
-      // row carries a large common part, so no cancellation error remains
+      // row carries a large common part, so no cancellation error remains.
+      // Four partial sums over j mod 4, combined as (s0 + s1) + (s2 + s3):
+      // the coefficient definition the staged-tile kernel uses as well.
       const float a0 = x[0];
-      float c = 0.0f;
+      float s4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
       for (int j = 0; j < NM; ++j)
-        if (j < n) c = __fmaf_rn(__fsub_rn(x[j], a0), S.Vst[j * NM + k], c);
-      c = __fmaf_rn(a0, S.vsum[k], c);
+        if (j < n) s4[j & 3] = __fmaf_rn(__fsub_rn(x[j], a0), S.Vst[j * NM + k], s4[j & 3]);
+      const float c = __fmaf_rn(a0, S.vsum[k], __fadd_rn(__fadd_rn(s4[0], s4[1]), __fadd_rn(s4[2], s4[3])));
       q[k] = quant_exact(c, delta, inv_delta, ovf);
       chat[k] = __fmul_rn(__int2float_rn(q[k]), delta_f);
     }
@@ -876,6 +902,7 @@ __device__ __forceinline__ void mixed_body(const MxArgs& a) {
     jacobi_cta<kMT>(S.G32, S.Vj, S.lam_t, n, 0.0f, S.jp);
     mark(kPhJacobi);
     refine64(S, n);
+    reorth64(S, n);
     if (warp == 0) order_basis(S, n, lane);
     __syncthreads();
     mark(kPhRefine);
@@ -899,25 +926,7 @@ __device__ __forceinline__ void mixed_body(const MxArgs& a) {
           }
         }
         __syncthreads();
-        // first-order orthonormalisation in FP64: V <- V (I + R/2), R = I - V^T V
-        {
-          const int i = tid / NM, j = tid % NM;
-          const bool act = i < n && j < n;
-          if (act) {
-            double rr = 0.0;
-            for (int k = 0; k < n; ++k) rr = fma(S.X64[k * NM + i], S.X64[k * NM + j], rr);
-            S.R64[i * NM + j] = (i == j ? 1.0 : 0.0) - rr;
-          }
-          __syncthreads();
-          double xn = 0.0;
-          if (act) {
-            xn = S.X64[i * NM + j];
-            for (int k = 0; k < n; ++k) xn = fma(S.X64[i * NM + k], 0.5 * S.R64[k * NM + j], xn);
-          }
-          __syncthreads();
-          if (act) S.X64[i * NM + j] = xn;
-        }
-        __syncthreads();
+        reorth64(S, n);
         if (warp == 0) order_basis(S, n, lane);
         __syncthreads();
       }
@@ -1025,10 +1034,17 @@ __global__ void k_stage_quantize(const float* c, int64_t n, double delta, int32_
   }
 }
 
-__global__ void k_stage_correct(const float* x, const float* xh, int64_t n, double eb, int32_t* k) {
+// path 0: corr_exact (the row-loading kernel's decision); 1: the per-block
+// kernel's candidate filter, then corr_decide for candidates (its sparse
+// encode pass); 2: corr_decide for every element (its dense encode pass).
+__global__ void k_stage_correct(const float* x, const float* xh, int64_t n, double eb, int path, int32_t* k) {
   const CorrConst cc = make_corr_const(eb, 2.0 * eb, true);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    k[i] = corr_exact(x[i], xh[i], cc);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float xi = x[i], hi = xh[i];
+    if (path == 0) k[i] = corr_exact(xi, hi, cc);
+    else if (path == 1) k[i] = corr_candidate(__fsub_rn(xi, hi), cc) ? corr_decide(xi, hi, cc) : 0;
+    else k[i] = corr_decide(xi, hi, cc);
+  }
 }
 
 }  // namespace
@@ -1039,9 +1055,10 @@ int launch_stage_quantize(const float* c, int64_t n, double delta, int32_t* q, i
   return cudaGetLastError() == cudaSuccess ? DLS_OK : DLS_ERR_CUDA;
 }
 
-int launch_stage_correct(const float* x, const float* xh, int64_t n, double eb, int32_t* k, cudaStream_t s) {
+int launch_stage_correct(const float* x, const float* xh, int64_t n, double eb, int path, int32_t* k,
+                         cudaStream_t s) {
   if (n <= 0) return DLS_OK;
-  k_stage_correct<<<(unsigned)(n < 65536 * 256 ? cdiv(n, 256) : 65536), 256, 0, s>>>(x, xh, n, eb, k);
+  k_stage_correct<<<(unsigned)(n < 65536 * 256 ? cdiv(n, 256) : 65536), 256, 0, s>>>(x, xh, n, eb, path, k);
   return cudaGetLastError() == cudaSuccess ? DLS_OK : DLS_ERR_CUDA;
 }
 

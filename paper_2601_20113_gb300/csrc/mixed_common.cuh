@@ -96,6 +96,18 @@ __device__ __forceinline__ int32_t corr_fast(float x, float xh, const CorrConst&
   *unsure = !zero && !(clear && (in || out));
   return zero ? 0 : (out ? kEscape : (int32_t)r);
 }
+// The decision of one element the per-block kernel selected as a candidate
+// (|fl(x - xhat)| at or above eb, rounded down): the branch-free FP32 test,
+// and the FP64 definition where that test leaves the decision open.
+static __device__ __noinline__ int32_t corr_slow(float x, float xh, const CorrConst& cc);
+__device__ __forceinline__ int32_t corr_decide(float x, float xh, const CorrConst& cc) {
+  bool u;
+  const int32_t k = corr_fast(x, xh, cc, &u);
+  return u ? corr_slow(x, xh, cc) : k;
+}
+// The candidate filter of the per-block kernel: elements with |fl(x - xhat)|
+// below eb (1 - 1e-6), rounded down, need no correction and no decision.
+__device__ __forceinline__ bool corr_candidate(float R, const CorrConst& cc) { return !(fabsf(R) < cc.eb_lo_f); }
 static __device__ __noinline__ int32_t corr_slow(float x, float xh, const CorrConst& cc) {
   const float R = __fsub_rn(x, xh);
   const float y = __fmul_rn(R, cc.inv_step_f);

@@ -21,6 +21,7 @@ PREC_FP64, PREC_TF32X3, PREC_BF16X3, PREC_FP32 = 0, 1, 2, 3
 RANK_SEARCH, RANK_LEARNED, RANK_TAIL = 0, 1, 2
 MLP_NPARAM, MLP_NFEAT = 6401, 32
 OK = 0
+ERR_TIMEOUT = -6
 ERR = {-1: "INVALID_ARG", -2: "CAPACITY", -3: "NONFINITE", -4: "CORRUPT", -5: "CUDA", -6: "TIMEOUT",
        -7: "BOUND_VIOLATED", -8: "WORKSPACE", -9: "NO_MODEL"}
 
@@ -106,6 +107,9 @@ _SIGS = {
     "dls_phase_cycles": (C.c_int, [C.POINTER(Params), C.c_void_p, C.POINTER(C.c_ulonglong), C.c_int32]),
     "dls_stage_quantize": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dls_stage_correct": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_void_p]),
+    "dls_stage_correct_path": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_int32, C.c_void_p,
+                                         C.c_void_p]),
+    "dls_set_fault_hook": (C.c_int, [C.c_int32, C.c_int64]),
     "dls_status_string": (C.c_char_p, [C.c_int]),
 }
 
@@ -294,6 +298,27 @@ def stage_correct(x: torch.Tensor, xh: torch.Tensor, eb: float):
     if st != OK:
         raise DlsError(st, "dls_stage_correct")
     return k
+
+
+CORR_PATH_EXACT, CORR_PATH_SPARSE, CORR_PATH_DENSE = 0, 1, 2
+FAULT_NONE, FAULT_WITHHOLD_CHUNK = 0, 1
+
+
+def stage_correct_path(x: torch.Tensor, xh: torch.Tensor, eb: float, path: int):
+    """The pointwise correction through one of the compression's code paths
+    (CORR_PATH_*): int32 k, INT32_MIN = escape."""
+    k = torch.empty(x.shape, dtype=torch.int32, device=x.device)
+    st = lib().dls_stage_correct_path(C.c_void_p(x.data_ptr()), C.c_void_p(xh.data_ptr()), x.numel(), float(eb),
+                                      int(path), C.c_void_p(k.data_ptr()), _stream(None))
+    if st != OK:
+        raise DlsError(st, "dls_stage_correct_path")
+    return k
+
+
+def set_fault_hook(kind: int, arg: int = 0) -> int:
+    """Test hook: FAULT_WITHHOLD_CHUNK withholds the first chunk copy of block
+    `arg` in later compressions (they return ERR_TIMEOUT); FAULT_NONE clears it."""
+    return lib().dls_set_fault_hook(int(kind), int(arg))
 
 
 def _ptr(t):

@@ -5,13 +5,16 @@ Stage tests feed identical inputs to the GPU's FP32-filtered decisions and to
 the oracle's FP64 definitions and require identical results, with inputs placed
 on the rounding boundaries where a filter could go wrong.  End-to-end tests
 require the pointwise bound at every point and the compression ratio within 1%
-of the oracle's, and report the reconstruction difference from the oracle.
+of the oracle's, and replay every record through the oracle from its own
+stored modes (oracle/replay.py): codes, rank, corrections, escapes and record
+bytes must match exactly.
 """
 import numpy as np
 import pytest
 import torch
 
 import oracle
+from oracle import replay
 from paper_2601_20113_gb300 import dls, synth
 
 pytestmark = pytest.mark.gpu
@@ -99,9 +102,11 @@ def test_mixed_bound_and_ratio(rel):
     ratio_gpu = f.nbytes / comp.numel()
     ratio_ref = f.nbytes / ref.size
     assert abs(ratio_gpu / ratio_ref - 1) <= 0.01, (ratio_gpu, ratio_ref)
-    st, rref = oracle.decompress(ref)
-    diff = np.linalg.norm(rec.cpu().numpy().astype(np.float64) - rref) / np.linalg.norm(f.astype(np.float64))
-    print(f"rel {rel}: ratio gpu {ratio_gpu:.4f} oracle {ratio_ref:.4f}; ||x_gpu - x_oracle|| / ||x|| = {diff:.3e}")
+    # every record replayed through the oracle from its own stored modes
+    # (codes, rank property, corrections, escapes and record bytes exact)
+    cfg = oracle.Config(dims, (16, 16, 16, 16), oracle.F32, eb=eb, rank_cap=16)
+    res, errs = replay.replay_stream(cfg, f, comp.cpu().numpy())
+    assert errs == [] and all(r["errors"] == [] for r in res), [r["errors"] for r in res if r["errors"]][:3]
 
 
 def _same_payload(a, b):
@@ -144,6 +149,8 @@ def test_mixed_multivariable_uneven_blocks():
     for v in range(5):
         assert np.abs(y[v] - x[v]).max() <= ebs[v] * (x[v].max() - x[v].min())
     assert abs((f.nbytes / comp.numel()) / (f.nbytes / ref.size) - 1) <= 0.01
+    res, errs = replay.replay_stream(cfg, f, comp.cpu().numpy())
+    assert errs == [] and all(r["errors"] == [] for r in res), [r["errors"] for r in res if r["errors"]][:3]
 
 
 def test_mixed_nrmse_mode():
@@ -195,6 +202,8 @@ def test_tf32x3_tensor_core_gram(rel):
     rec = dls.decompress(out[:nb])
     assert (rec.double() - fd.double()).abs().max().item() <= eb
     assert abs((f.nbytes / nb) / (f.nbytes / ref.size) - 1) <= 0.01
+    res, errs = replay.replay_stream(cfg, f, out[:nb].cpu().numpy())
+    assert errs == [] and all(r["errors"] == [] for r in res), [r["errors"] for r in res if r["errors"]][:3]
 
 
 def test_mixed_both_block_sides():
@@ -207,6 +216,9 @@ def test_mixed_both_block_sides():
     ref, comp, rec, fd, _ = _mixed_vs_oracle(f, dims, (4, 4, 1, 16), eb)
     assert (rec.double() - fd.double()).abs().max().item() <= eb
     assert abs((f.nbytes / comp.numel()) / (f.nbytes / ref.size) - 1) <= 0.01
+    cfg = oracle.Config(dims, (4, 4, 1, 16), oracle.F32, eb=eb, rank_cap=16)
+    res, errs = replay.replay_stream(cfg, f, comp.cpu().numpy())
+    assert errs == [] and all(r["errors"] == [] for r in res), [r["errors"] for r in res if r["errors"]][:3]
 
 
 @pytest.mark.parametrize("dims,block", [((48, 20, 20, 16), (12, 8, 8, 16)),     # TMA, several z-planes per chunk
@@ -218,6 +230,9 @@ def test_mixed_chunk_shapes(dims, block):
     ref, comp, rec, fd, _ = _mixed_vs_oracle(f, dims, block, eb, rank_mode=dls.RANK_TAIL)
     assert (rec.double() - fd.double()).abs().max().item() <= eb
     assert abs((f.nbytes / comp.numel()) / (f.nbytes / ref.size) - 1) <= 0.01
+    cfg = oracle.Config(dims, block, oracle.F32, eb=eb, rank_cap=16)
+    res, errs = replay.replay_stream(cfg, f, comp.cpu().numpy())
+    assert errs == [] and all(r["errors"] == [] for r in res), [r["errors"] for r in res if r["errors"]][:3]
 
 
 def _record_escapes(comp):
@@ -293,6 +308,11 @@ def test_mixed_escapes_in_deferred_records():
     st, rref = oracle.decompress(comp.cpu().numpy())
     assert st == oracle.OK
     assert np.array_equal(rref.astype(np.float32), rec.cpu().numpy())
+    # the escape-carrying deferred record, byte for byte against the oracle's packer
+    cfg = oracle.Config(dims, (16, 16, 16, 16), oracle.F32, eb=eb, rank_cap=1)
+    res, errs = replay.replay_stream(cfg, f.numpy(), comp.cpu().numpy())
+    assert errs == [] and all(r["errors"] == [] for r in res), [r["errors"] for r in res if r["errors"]][:3]
+    assert res[0]["nesc"] == 3
 
 
 @pytest.mark.parametrize("nvars,eb_type", [(1, dls.EB_ABS), (2, dls.EB_ABS), (2, dls.EB_REL_RANGE)])
