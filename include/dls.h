@@ -48,8 +48,10 @@ enum { DLS_EB_ABS = 0, DLS_EB_REL_RANGE = 1, DLS_EB_NRMSE = 2 };
 /* Arithmetic of the Gram and projection products.
  *   FP64:   double precision everywhere (the plain form).
  *   FP32:   FP32 products on the CUDA cores with FP32 accumulation; FP32
- *           Jacobi refined to FP64 accuracy; every stored decision (quantized
- *           coefficient, rank test, correction, escape) keeps FP64 semantics.
+ *           Jacobi eigensolve, its eigenvectors orthonormalised in FP64 (to
+ *           below the rounding of the stored modes); every stored decision
+ *           (quantized coefficient, rank test, correction, escape) keeps FP64
+ *           semantics.
  *   TF32X3: as FP32, with the block Gram on the tensor cores (tcgen05) as a
  *           3-term TF32 split product (hi hi + hi lo + lo hi, FP32
  *           accumulation) for 16 x 16 x bz x 16 blocks of a field whose x
@@ -152,6 +154,17 @@ int dls_plan_info(const dls_plan* plan, int32_t* variant, float* tune_ms);
  * for that execution), and the number of kernel nodes in the plan's graph.
  * Either pointer may be null. */
 int dls_plan_timing(const dls_plan* plan, float* kernel_ms, int32_t* kernel_nodes);
+/* Device time in ms of each stage of the most recent dls_plan_execute of a
+ * mixed-precision plan (FP32 / TF32X3; zeros for the FP64 form and for plans
+ * without time-side blocks), from events inside the graph (waits for that
+ * execution): ms[0] the Gram pass (k_gram), ms[1] the eigensolve and rank
+ * prediction (k_eig), ms[2] the Rayleigh-Ritz pass of the blocks that need it
+ * (k_rrgram, k_eig), ms[3] the encode pass at the predicted rank with its
+ * exact test and deferred records (k_enc), ms[4] the blocks left to the
+ * searching kernel (k_tile, and k_mixed for blocks whose Gram side is space),
+ * ms[5] the scan of record sizes and the record packing.  count >= 6
+ * (further entries are set to 0). */
+int dls_plan_phase_timing(const dls_plan* plan, float* ms, int32_t count);
 /* Releases the plan's graph, events and pinned status buffer (not the
  * caller's buffers).  A null plan is accepted.  Call it once the last
  * execution has returned (dls_plan_execute synchronizes its stream). */

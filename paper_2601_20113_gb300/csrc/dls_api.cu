@@ -89,7 +89,7 @@ int make_plan(const dls_params* p, Plan* out) {
 struct Layout {
   size_t meta, vst, q, kc, offsets, vars, status, partial, basis, total;
   // mixed-precision form
-  size_t staging, q_scr, k8_scr, k32_scr, bit_scr, feat, ranks, phase;
+  size_t staging, q_scr, k8_scr, k32_scr, bit_scr, feat, ranks, phase, fast;
   int ctas;
   bool mixed;
 };
@@ -142,10 +142,10 @@ static MixedRoute mixed_route(const Plan& P) {
 }
 
 static int launch_mixed_all(const Plan& P, const void* d_in, const MixedWork& mw, int mode, int variant,
-                            cudaStream_t s) {
+                            cudaStream_t s, const cudaEvent_t* pev = nullptr) {
   const MixedRoute rt = mixed_route(P);
   int st;
-  if (rt.tile && (st = launch_tile_compress(P, d_in, mw, mode, variant, s)) != DLS_OK) return st;
+  if (rt.tile && (st = launch_tile_compress(P, d_in, mw, mode, variant, s, 0, -1, pev)) != DLS_OK) return st;
   if (rt.legacy && (st = launch_mixed_compress(P, d_in, mw, mode, variant, rt.spatial_only ? 1 : 0, s)) != DLS_OK)
     return st;
   return DLS_OK;
@@ -178,6 +178,7 @@ static Layout work_layout(const Plan& P) {
     L.feat = take(sizeof(float) * 32 * (size_t)nb1);
     L.ranks = take(sizeof(int32_t) * (size_t)nb1);
     L.phase = take(sizeof(unsigned long long) * (size_t)L.ctas * kMixedPhases);
+    L.fast = take(tile_fast_bytes(P.nb));
     L.total = off;
     return L;
   }
@@ -315,15 +316,19 @@ static MixedWork mixed_work(const Plan& P, const Layout& L, void* ws) {
   mw.nptmax = align_up((int64_t)P.nmax * P.lmax, 16);
   mw.ctas = L.ctas;
   mw.phase = (unsigned long long*)(b + L.phase);
+  mw.fast = b + L.fast;
   return mw;
 }
 
 // Enqueues the whole compression on `s` (no host synchronisation): status
 // reset, bound resolution, the per-block kernel of the chosen form, the scan
 // writing header and offset table, and the record packer / compaction.
+// ev0 / ev1 (optional) bracket the per-block kernels; pev (optional, five
+// events) marks the ends of k_gram, k_eig, the Rayleigh-Ritz kernels, k_enc
+// and of the record packing.
 static int enqueue_compress(const Plan& P, const Layout& L, const void* d_in, void* d_out, size_t out_cap,
                             void* d_ws, int variant, cudaStream_t s, cudaEvent_t ev0 = nullptr,
-                            cudaEvent_t ev1 = nullptr) {
+                            cudaEvent_t ev1 = nullptr, const cudaEvent_t* pev = nullptr) {
   int st;
   Work w = carve(L, d_ws);
   CK(cudaMemsetAsync(w.status, 0, sizeof(Status), s));
@@ -334,11 +339,12 @@ static int enqueue_compress(const Plan& P, const Layout& L, const void* d_in, vo
     CK(cudaMemsetAsync(mw.phase, 0, sizeof(unsigned long long) * (size_t)L.ctas * kMixedPhases, s));
     const int mode = P.rank_mode == DLS_RANK_LEARNED ? kRankMlp : (P.rank_mode == DLS_RANK_TAIL ? kRankTail : kRankSearch);
     if (ev0) CK(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
-    if ((st = launch_mixed_all(P, d_in, mw, mode, variant, s)) != DLS_OK) return st;
+    if ((st = launch_mixed_all(P, d_in, mw, mode, variant, s, pev)) != DLS_OK) return st;
     if (ev1) CK(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
     if ((st = launch_scan(P, w, out_cap, d_out, s)) != DLS_OK) return st;
     if ((st = launch_compact(P, mw, d_out, s)) != DLS_OK) return st;
     if ((st = launch_pack_tile(P, mw, d_in, d_out, s)) != DLS_OK) return st;
+    if (pev && pev[4]) CK(cudaEventRecordWithFlags(pev[4], s, cudaEventRecordExternal));
   } else {
     if (ev0) CK(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
     if ((st = launch_plain_compress(P, d_in, w, s)) != DLS_OK) return st;
@@ -431,6 +437,7 @@ struct dls_plan {
   cudaGraphExec_t exec;
   dls::Status* h_status;   // pinned
   cudaEvent_t kev[2];      // recorded around the per-block kernels inside the graph
+  cudaEvent_t pev[5];      // ends of k_gram, k_eig, the Rayleigh-Ritz kernels, k_enc, the record packing
   int kernel_nodes;
 };
 
@@ -622,13 +629,10 @@ int dls_block_features(const dls_params* p, const void* d_in, float* d_feat, int
   uint8_t* b = (uint8_t*)d_workspace;
   CK(cudaMemsetAsync(w.status, 0, sizeof(Status), s));
   if ((st = launch_stats_resolve(P, d_in, w, (double*)(b + L.partial), s)) != DLS_OK) return st;
-  MixedWork mw;
-  mw.meta = w.meta; mw.offsets = w.offsets; mw.vars = w.vars; mw.status = w.status;
-  mw.staging = b + L.staging; mw.q_scr = (int32_t*)(b + L.q_scr); mw.k8_scr = (int8_t*)(b + L.k8_scr);
-  mw.k32_scr = (int32_t*)(b + L.k32_scr); mw.feat = d_feat; mw.ranks = d_rank;
-  mw.bit_scr = (uint32_t*)(b + L.bit_scr);
-  mw.lmax = align_up(P.lmax, 4); mw.nptmax = align_up((int64_t)P.nmax * P.lmax, 16); mw.ctas = L.ctas;
-  mw.phase = (unsigned long long*)(b + L.phase);
+  // the workspace as a compression uses it, with the caller's feature and rank arrays
+  MixedWork mw = mixed_work(P, L, d_workspace);
+  mw.feat = d_feat;
+  mw.ranks = d_rank;
   if ((st = launch_mixed_all(P, d_in, mw, kRankSearch, 2, s)) != DLS_OK) return st;
   Status hs;
   CK(cudaMemcpyAsync(&hs, w.status, sizeof(Status), cudaMemcpyDeviceToHost, s));
@@ -728,6 +732,7 @@ int dls_plan_create(const dls_params* p, const void* d_in, void* d_out, size_t o
   pl->exec = nullptr;
   pl->h_status = nullptr;
   pl->kev[0] = pl->kev[1] = nullptr;
+  for (int i = 0; i < 5; ++i) pl->pev[i] = nullptr;
   pl->kernel_nodes = 0;
   auto fail = [&](int code) {
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
@@ -735,11 +740,15 @@ int dls_plan_create(const dls_params* p, const void* d_in, void* d_out, size_t o
     if (pl->h_status) cudaFreeHost(pl->h_status);
     for (int i = 0; i < 2; ++i)
       if (pl->kev[i]) cudaEventDestroy(pl->kev[i]);
+    for (int i = 0; i < 5; ++i)
+      if (pl->pev[i]) cudaEventDestroy(pl->pev[i]);
     delete pl;
     return code;
   };
   if (cudaEventCreate(&pl->kev[0]) != cudaSuccess || cudaEventCreate(&pl->kev[1]) != cudaSuccess)
     return fail(DLS_ERR_CUDA);
+  for (int i = 0; i < 5; ++i)
+    if (cudaEventCreate(&pl->pev[i]) != cudaSuccess) return fail(DLS_ERR_CUDA);
   if (cudaHostAlloc((void**)&pl->h_status, sizeof(Status), cudaHostAllocDefault) != cudaSuccess) return fail(DLS_ERR_CUDA);
   // the fixed basis goes into the workspace once, outside the captured graph
   if ((st = upload_basis(p, P, L, d_workspace, s)) != DLS_OK) return fail(st);
@@ -775,7 +784,8 @@ int dls_plan_create(const dls_params* p, const void* d_in, void* d_out, size_t o
     cudaStreamDestroy(cs);
     return fail(DLS_ERR_CUDA);
   }
-  st = enqueue_compress(P, L, d_in, d_out, out_cap, d_workspace, pl->variant, cs, pl->kev[0], pl->kev[1]);
+  st = enqueue_compress(P, L, d_in, d_out, out_cap, d_workspace, pl->variant, cs, pl->kev[0], pl->kev[1],
+                        L.mixed ? pl->pev : nullptr);
   Work w = carve(L, d_workspace);
   cudaError_t ce = cudaMemcpyAsync(pl->h_status, w.status, sizeof(Status), cudaMemcpyDeviceToHost, cs);
   cudaGraph_t g = nullptr;
@@ -830,6 +840,16 @@ int dls_plan_timing(const dls_plan* pl, float* kernel_ms, int32_t* kernel_nodes)
   return DLS_OK;
 }
 
+int dls_plan_phase_timing(const dls_plan* pl, float* ms, int32_t count) {
+  if (!pl || !ms || count < 6) return DLS_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i) ms[i] = 0.0f;
+  if (!pl->L.mixed || !pl->exec || !mixed_route(pl->P).tile) return DLS_OK;
+  CK(cudaEventSynchronize(pl->pev[4]));
+  const cudaEvent_t seq[7] = {pl->kev[0], pl->pev[0], pl->pev[1], pl->pev[2], pl->pev[3], pl->kev[1], pl->pev[4]};
+  for (int i = 0; i < 6; ++i) CK(cudaEventElapsedTime(&ms[i], seq[i], seq[i + 1]));
+  return DLS_OK;
+}
+
 int dls_plan_destroy(dls_plan* pl) {
   if (!pl) return DLS_OK;
   if (pl->exec) cudaGraphExecDestroy(pl->exec);
@@ -837,6 +857,8 @@ int dls_plan_destroy(dls_plan* pl) {
   if (pl->h_status) cudaFreeHost(pl->h_status);
   for (int i = 0; i < 2; ++i)
     if (pl->kev[i]) cudaEventDestroy(pl->kev[i]);
+  for (int i = 0; i < 5; ++i)
+    if (pl->pev[i]) cudaEventDestroy(pl->pev[i]);
   delete pl;
   return DLS_OK;
 }

@@ -218,6 +218,7 @@ struct MixedWork {
   int64_t lmax, nptmax;
   int ctas;
   unsigned long long* phase;   // ctas x kMixedPhases cycle counters
+  uint8_t* fast;        // per-block state of the tile route's phase kernels (tile_fast_bytes)
 };
 constexpr int kMaxMixedN = 16;
 constexpr int kMixedPhases = 14;
@@ -246,9 +247,12 @@ int64_t fault_withheld_block();
 // ---------------------------------------------------------------- launchers (defined in .cu files)
 int launch_mixed_compress(const Plan& p, const void* d_in, const MixedWork& w, int learned, int variant,
                           int spatial_only, cudaStream_t s);
+// pev (optional): four events recorded after k_gram, k_eig, the
+// Rayleigh-Ritz kernels and k_enc (for the phase timing of captured plans).
 int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, int learned, int variant,
-                         cudaStream_t s, int64_t blo = 0, int64_t bhi = -1);
+                         cudaStream_t s, int64_t blo = 0, int64_t bhi = -1, const cudaEvent_t* pev = nullptr);
 bool tile_chunk_box(const Plan& p, int* bxb, int* yc, int* zc, int* bt);
+size_t tile_fast_bytes(int64_t nb);
 int launch_compact(const Plan& p, const MixedWork& w, void* d_out, cudaStream_t s);
 int launch_pack_tile(const Plan& p, const MixedWork& w, const void* d_in, void* d_out, cudaStream_t s);
 size_t mixed_smem_bytes();

@@ -53,13 +53,12 @@ enum { kPhGram = 0, kPhJacobi, kPhRefine, kPhRR, kPhPredict, kPhEncode, kPhDecid
 struct MxSmem {
   float G32[NM * NM];
   float Vj[NM * NM];
-  double G64[NM * NM], X64[NM * NM], R64[NM * NM], GV64[NM * NM], S64[NM * NM], E64[NM * NM];
+  double G64[NM * NM], X64[NM * NM], R64[NM * NM];
   double lam_t[NM];        // refined eigenvalues (unsorted)
   double lam[NM];          // sorted
   float Vst[NM * NM];      // stored basis, Vst[j*NM + k]
   float vsum[NM];          // sum_j Vst[j][k] (for the shifted projection)
   float red[8][kNP + 8];
-  double dlt;
   float ered[8][NM + 2];
   double Ered[NM + 2];
   int sh_warp[32];
@@ -150,78 +149,10 @@ __device__ void cta_reduce_floats(MxSmem& S, float* v, int cnt) {
   __syncthreads();
 }
 
-// ---------------------------------------------------------------- FP64 refinement (all threads)
-// One Ogita-Aishima step on A = G (FP64 copy of the FP32 Gram) and the FP32
-// Jacobi eigenvectors X: R = I - X^T X, S = X^T A X, lambda_i = s_ii/(1-r_ii),
-// E_ij = (s_ij + lambda_j r_ij)/(lambda_j - lambda_i) when the gap exceeds
-// delta = 2(||S - diag||_F + ||A||_F ||R||_F), else r_ij / 2; X <- X + X E.
-__device__ void refine64(MxSmem& S, int n) {
-  const int tid = threadIdx.x;
-  const int i = tid / NM, j = tid % NM;
-  const bool act = (i < n && j < n);
-  if (act) S.X64[i * NM + j] = (double)S.Vj[i * NM + j];
-  __syncthreads();
-  if (act) {
-    double r = 0.0, gv = 0.0;
-    for (int k = 0; k < n; ++k) {
-      r = fma(S.X64[k * NM + i], S.X64[k * NM + j], r);
-      gv = fma(S.G64[i * NM + k], S.X64[k * NM + j], gv);
-    }
-    S.R64[i * NM + j] = (i == j ? 1.0 : 0.0) - r;
-    S.GV64[i * NM + j] = gv;
-  }
-  __syncthreads();
-  if (act) {
-    double s = 0.0;
-    for (int k = 0; k < n; ++k) s = fma(S.X64[k * NM + i], S.GV64[k * NM + j], s);
-    S.S64[i * NM + j] = s;
-  }
-  __syncthreads();
-  if (tid < 32) {
-    double offs = 0.0, g2 = 0.0, r2 = 0.0;
-    if (tid < n) {
-      S.lam_t[tid] = S.S64[tid * NM + tid] / (1.0 - S.R64[tid * NM + tid]);
-      for (int b = 0; b < n; ++b) {
-        if (b != tid) offs = fma(S.S64[tid * NM + b], S.S64[tid * NM + b], offs);
-        g2 = fma(S.G64[tid * NM + b], S.G64[tid * NM + b], g2);
-        r2 = fma(S.R64[tid * NM + b], S.R64[tid * NM + b], r2);
-      }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      offs += __shfl_xor_sync(0xffffffffu, offs, o);
-      g2 += __shfl_xor_sync(0xffffffffu, g2, o);
-      r2 += __shfl_xor_sync(0xffffffffu, r2, o);
-    }
-    if (tid == 0) S.dlt = 2.0 * (sqrt(offs) + sqrt(g2) * sqrt(r2));
-  }
-  __syncthreads();
-  if (act) {
-    double e;
-    if (i == j) {
-      e = 0.5 * S.R64[i * NM + j];
-    } else {
-      const double li = S.lam_t[i], lj = S.lam_t[j];
-      const double d = lj - li;
-      if (fabs(d) > S.dlt) e = (S.S64[i * NM + j] + lj * S.R64[i * NM + j]) / d;
-      else e = 0.5 * S.R64[i * NM + j];
-    }
-    S.E64[i * NM + j] = e;
-  }
-  __syncthreads();
-  double xn = 0.0;
-  if (act) {
-    xn = S.X64[i * NM + j];
-    for (int k = 0; k < n; ++k) xn = fma(S.X64[i * NM + k], S.E64[k * NM + j], xn);
-  }
-  __syncthreads();
-  if (act) S.X64[i * NM + j] = xn;
-  __syncthreads();
-}
-
 // First-order orthonormalisation in FP64 (all threads): X <- X (I + R/2),
-// R = I - X^T X.  It takes the second-order orthogonality error the one
-// refinement step leaves (pairs of modes with gaps near its threshold) to its
-// square, below the rounding of the stored modes to binary32.
+// R = I - X^T X.  The FP32 Jacobi's eigenvectors are orthonormal to about
+// 1e-5; this step takes that to its square, below the rounding of the stored
+// modes to binary32.
 __device__ void reorth64(MxSmem& S, int n) {
   const int tid = threadIdx.x;
   const int i = tid / NM, j = tid % NM;
@@ -901,7 +832,12 @@ __device__ __forceinline__ void mixed_body(const MxArgs& a) {
     }
     jacobi_cta<kMT>(S.G32, S.Vj, S.lam_t, n, 0.0f, S.jp);
     mark(kPhJacobi);
-    refine64(S, n);
+    {
+      // FP64 copy of the Jacobi eigenvectors, then one orthonormalisation
+      const int i = tid / NM, j = tid % NM;
+      if (i < n && j < n) S.X64[i * NM + j] = (double)S.Vj[i * NM + j];
+    }
+    __syncthreads();
     reorth64(S, n);
     if (warp == 0) order_basis(S, n, lane);
     __syncthreads();

@@ -69,6 +69,11 @@ struct TileArgs {
   double jfloor;           // Jacobi skip floor as a fraction of the per-mode budget
   int64_t blo, bhi;        // the blocks [blo, bhi) of the plan this launch compresses
   int64_t withhold;        // test hook: the first chunk of this block is never copied (-1: none)
+  struct FastBlock* fb;    // per-block state of the phase kernels (plan-relative index)
+  struct FastCtl* ctl;     // their block counters and the list k_enc fills
+  int32_t* list;           // blocks left to k_tile
+  int from_list;           // k_tile: blocks from the list
+  int ctas;                // phase-counter slots
 };
 
 // Quantization constants of one variable (delta, and 1 / delta and delta in FP32).
@@ -77,11 +82,13 @@ struct RowConst {
   float inv_delta, delta_f;
 };
 
-struct __align__(128) TileSmem {
-  float ring[kStages][kStageFloats];
+// The staging ring is the last member, so that the kernels that stream no
+// block (k_eig) allocate only the part before it.
+struct __align__(1024) TileSmem {
   unsigned long long full[kStages];
   float G32[NM * NM];
   float Vj[NM * NM];
+  float red[kWarps][kNP + 8];
   __align__(16) float VstT[NM * NM];     // VstT[k * NM + j] = Vst[j][k]
   float vsum[NM];
   // FP64 eigen scratch; from the encode pass through the record it holds the
@@ -93,10 +100,8 @@ struct __align__(128) TileSmem {
     uint32_t bitsm[8 * NM * NM];
   };
   double lam_t[NM], lam[NM];
-  float red[kWarps][kNP + 8];
   float ered[kWarps][NM + 2];
   double Ered[NM + 2];
-  double dlt;
   float featv[kMlpF];
   float mh1[kMlpH];
   float st_min[kWarps], st_max[kWarps], st_tg[kWarps], st_xg[kWarps], st_rowmax[kWarps];
@@ -126,6 +131,7 @@ struct __align__(128) TileSmem {
   RowConst crc;
   CorrConst ccc;
   double lam_tr;
+  alignas(1024) float ring[kStages][kStageFloats];
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -324,8 +330,18 @@ struct Cursor {
   int pf_cnt, pf_layout;
 };
 
+// Drops chunks in flight that belong to another block.
+__device__ void drain(TileSmem& S, Cursor& cu);
+
+// Starts the first chunks of block bi (all threads call).  Chunks already in
+// flight for the same block and layout are kept; any others are drained first,
+// so the ring never holds more chunks than it has stages.
 __device__ void prefetch(const TileArgs& a, const Maps& tm, TileSmem& S, Cursor& cu, int64_t bi, const Geom& g,
                          int layout) {
+  if (cu.pf_cnt > 0) {
+    if (cu.pf_blk == bi && cu.pf_layout == layout) return;
+    drain(S, cu);
+  }
   const Chunks ch = chunks_of(a, g);
   const int k = ch.n < kStages ? ch.n : kStages;
   for (int c = 0; c < k; ++c) issue_chunk(a, tm, S, bi, g, ch, c, cu.iss, layout);
@@ -433,6 +449,44 @@ __device__ void derived_stats(const TileArgs& a, TileSmem& S, const Geom& g, int
 template <int NF>
 __device__ __forceinline__ float project(const float* d, const float* v, float a0, float vsum, int n);
 
+// Gram accumulation order.  The upper triangle is covered by the diagonal
+// singles (i, i), i even, and the pairs {(i, j), (i + 1, j)}, i even,
+// j = i + 1 .. 15, taken i-major.  Group g keeps pairs 2k + g as accumulators
+// acc[2k], acc[2k + 1] (rows i, i + 1) and singles 2k + g as acc[64 + k].
+constexpr int kGramPairs = 64, kGramSingles = 8;
+static_assert(kGramPairs + kGramSingles / 2 * 2 == 72 && kGramPairs + kGramSingles / 2 == kHalf, "layout");
+template <int G>
+__device__ __forceinline__ void gram_row(const float (&x)[NM], float (&acc)[kHalf]) {
+  int pc = 0, sc = 0;
+#pragma unroll
+  for (int i = 0; i < NM; i += 2) {
+    if ((sc & 1) == G) acc[kGramPairs + (sc >> 1)] = __fmaf_rn(x[i], x[i], acc[kGramPairs + (sc >> 1)]);
+    ++sc;
+#pragma unroll
+    for (int j = i + 1; j < NM; ++j, ++pc) {
+      if ((pc & 1) == G) {
+        const int q = (pc >> 1) * 2;
+        const float2 r = __ffma2_rn(make_float2(x[i], x[i + 1]), make_float2(x[j], x[j]),
+                                    make_float2(acc[q], acc[q + 1]));
+        acc[q] = r.x;
+        acc[q + 1] = r.y;
+      }
+    }
+  }
+}
+// Entry (i, j) of accumulator q of group grp.
+__device__ __forceinline__ void gram_entry(int grp, int q, int& i, int& j) {
+  if (q >= kGramPairs) {
+    i = j = 2 * (2 * (q - kGramPairs) + grp);
+    return;
+  }
+  int pc = 2 * (q >> 1) + grp;                  // global pair index
+  int ib = 0;
+  while (pc >= NM - 1 - ib) { pc -= NM - 1 - ib; ib += 2; }
+  j = ib + 1 + pc;
+  i = ib + (q & 1);
+}
+
 template <bool PROJECT, int NF>
 __device__ __noinline__ bool pass_gram(const TileArgs& a, const Maps& tm, TileSmem& S, Cursor& cu, int64_t bi,
                           const Geom& g) {
@@ -499,19 +553,11 @@ __device__ __noinline__ bool pass_gram(const TileArgs& a, const Maps& tm, TileSm
             if (j < n) { const float d = tile[j * rc + r + 1] - x[j]; xg = __fmaf_rn(d, d, xg); }
         }
       }
-      if (grp == 0) {
-#pragma unroll
-        for (int i = 0, p = 0; i < NM; ++i)
-#pragma unroll
-          for (int j = i; j < NM; ++j, ++p)
-            if (p < kHalf) acc[p] = __fmaf_rn(x[i], x[j], acc[p]);
-      } else {
-#pragma unroll
-        for (int i = 0, p = 0; i < NM; ++i)
-#pragma unroll
-          for (int j = i; j < NM; ++j, ++p)
-            if (p >= kHalf) acc[p - kHalf] = __fmaf_rn(x[i], x[j], acc[p - kHalf]);
-      }
+      // entries of rows i, i + 1 (i even) in column j as one packed FMA
+      // (each component rounds as __fmaf_rn: the same sums as one FMA per
+      // entry); groups take alternate pairs and alternate diagonal singles
+      if (grp == 0) gram_row<0>(x, acc);
+      else gram_row<1>(x, acc);
     }
   });
   if (!ok) return false;
@@ -538,9 +584,8 @@ __device__ __noinline__ bool pass_gram(const TileArgs& a, const Maps& tm, TileSm
   for (int p = tid; p < kNP; p += kTT) {
     const int gw = (p / kHalf) * 2, pp = p % kHalf;
     const float v = __fadd_rn(S.red[gw][pp], S.red[gw + 1][pp]);
-    int i = 0, rem = p;
-    while (rem >= NM - i) { rem -= NM - i; ++i; }
-    const int j = i + rem;
+    int i, j;
+    gram_entry(p / kHalf, pp, i, j);
     if (i < n && j < n) {
       S.G32[i * NM + j] = v; S.G32[j * NM + i] = v;
       S.G64[i * NM + j] = (double)v; S.G64[j * NM + i] = (double)v;
@@ -706,145 +751,72 @@ __device__ __noinline__ bool pass_gram_tc(const TileArgs& a, const Maps& tm, Til
   return true;
 }
 
-// ---------------------------------------------------------------- FP64 refinement
-// One Ogita-Aishima step on A = G64 and the FP32 eigenvectors Vj:
-// R = I - X^T X, S = X^T A X, lambda_i = s_ii / (1 - r_ii),
-// E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) when the gap exceeds
-// delta = 2 (||S - diag S||_F + ||A||_F ||R||_F), else r_ij / 2; X <- X + X E.
-__device__ __noinline__ void refine64(TileSmem& S, int n) {
+// ---------------------------------------------------------------- orthonormalisation
+// First-order orthonormalisation of the eigenvector matrix X (columns = modes;
+// all threads), into X64 for the ordering: X <- X + X R / 2, R = I - X^T X.
+// The FP32 Jacobi's rotations are orthogonal to a few ulps each, so its
+// eigenvectors are orthonormal to about 1e-5; the step takes that to its
+// square.  R is formed without rounding error that matters: each product
+// a b is split exactly into fl(a b) + fma(a, b, -fl(a b)) and the sums are
+// kept as unevaluated pairs (Knuth's two-sum), so R is exact to about 1e-14
+// with FP32 arithmetic alone (GB300's FP64 pipe is 1/64 of its FP32 rate);
+// the correction X R / 2, of size |R|, and the final rounding need only FP32.
+// With `rotate`, X = Vst W first (the Rayleigh-Ritz rotation of the first
+// basis, in FP32: its rounding is orthonormalised away with the rest).
+__device__ __noinline__ void orth_basis(TileSmem& S, int n, bool rotate) {
   const int tid = threadIdx.x;
-  for (int e = tid; e < NM * NM; e += kTT) {
-    const int i = e / NM, j = e % NM;
-    if (i < n && j < n) S.X64[e] = (double)S.Vj[e];
-  }
-  __syncthreads();
-  for (int e = tid; e < NM * NM; e += kTT) {
-    const int i = e / NM, j = e % NM;
-    if (i < n && j < n) {
-      double gv = 0.0;
-      for (int k = 0; k < n; ++k) gv = fma(S.G64[i * NM + k], S.X64[k * NM + j], gv);
-      S.T64[e] = gv;
-      if (i <= j) {
-        double r = 0.0;
-        for (int k = 0; k < n; ++k) r = fma(S.X64[k * NM + i], S.X64[k * NM + j], r);
-        r = (i == j ? 1.0 : 0.0) - r;
-        S.R64[i * NM + j] = r;
-        S.R64[j * NM + i] = r;
-      }
+  if (rotate) {
+    float* X = &S.red[0][0];                    // scratch (>= NM * NM floats)
+    static_assert(sizeof(S.red) >= NM * NM * sizeof(float), "scratch");
+    for (int e = tid; e < NM * NM; e += kTT) {
+      const int i = e / NM, j = e % NM;
+      float v = 0.0f;
+      if (i < n && j < n)
+        for (int k = 0; k < n; ++k) v = __fmaf_rn(S.VstT[k * NM + i], S.Vj[k * NM + j], v);
+      X[e] = v;
     }
+    __syncthreads();
+    for (int e = tid; e < NM * NM; e += kTT) S.Vj[e] = X[e];
+    __syncthreads();
   }
-  __syncthreads();
-  // S = X^T (A X) (symmetric: upper triangle, mirrored) replaces A X in T64
-  double sv[2] = {0.0, 0.0};
-  int cnt = 0;
-  for (int e = tid; e < NM * NM; e += kTT, ++cnt) {
-    const int i = e / NM, j = e % NM;
-    double s = 0.0;
-    if (i < n && j < n && i <= j)
-      for (int k = 0; k < n; ++k) s = fma(S.X64[k * NM + i], S.T64[k * NM + j], s);
-    sv[cnt] = s;
-  }
-  __syncthreads();
-  cnt = 0;
-  for (int e = tid; e < NM * NM; e += kTT, ++cnt) {
-    const int i = e / NM, j = e % NM;
-    if (i < n && j < n && i <= j) { S.T64[i * NM + j] = sv[cnt]; S.T64[j * NM + i] = sv[cnt]; }
-  }
-  __syncthreads();
-  if (tid < 32) {
-    double offs = 0.0, g2 = 0.0, r2 = 0.0;
-    if (tid < n) {
-      S.lam_t[tid] = S.T64[tid * NM + tid] / (1.0 - S.R64[tid * NM + tid]);
-      for (int b = 0; b < n; ++b) {
-        if (b != tid) offs = fma(S.T64[tid * NM + b], S.T64[tid * NM + b], offs);
-        g2 = fma(S.G64[tid * NM + b], S.G64[tid * NM + b], g2);
-        r2 = fma(S.R64[tid * NM + b], S.R64[tid * NM + b], r2);
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      offs += __shfl_xor_sync(FULL, offs, o);
-      g2 += __shfl_xor_sync(FULL, g2, o);
-      r2 += __shfl_xor_sync(FULL, r2, o);
-    }
-    if (tid == 0) S.dlt = 2.0 * (sqrt(offs) + sqrt(g2) * sqrt(r2));
-  }
-  __syncthreads();
-  // E into T64 (S no longer needed after this read)
-  double ev[2] = {0.0, 0.0};
-  cnt = 0;
-  for (int e = tid; e < NM * NM; e += kTT, ++cnt) {
-    const int i = e / NM, j = e % NM;
-    double v = 0.0;
-    if (i < n && j < n) {
-      if (i == j) {
-        v = 0.5 * S.R64[e];
-      } else {
-        const double li = S.lam_t[i], lj = S.lam_t[j];
-        const double d = lj - li;
-        if (fabs(d) > S.dlt) v = (S.T64[e] + lj * S.R64[e]) / d;
-        else v = 0.5 * S.R64[e];
-      }
-    }
-    ev[cnt] = v;
-  }
-  __syncthreads();
-  cnt = 0;
-  for (int e = tid; e < NM * NM; e += kTT, ++cnt) S.T64[e] = ev[cnt];
-  __syncthreads();
-  double xn[2] = {0.0, 0.0};
-  cnt = 0;
-  for (int e = tid; e < NM * NM; e += kTT, ++cnt) {
-    const int i = e / NM, j = e % NM;
-    if (i < n && j < n) {
-      double v = S.X64[e];
-      for (int k = 0; k < n; ++k) v = fma(S.X64[i * NM + k], S.T64[k * NM + j], v);
-      xn[cnt] = v;
-    }
-  }
-  __syncthreads();
-  cnt = 0;
-  for (int e = tid; e < NM * NM; e += kTT, ++cnt) {
-    const int i = e / NM, j = e % NM;
-    if (i < n && j < n) S.X64[e] = xn[cnt];
-  }
-  __syncthreads();
-}
-
-// First-order orthonormalisation in FP64: X <- X (I + R/2), R = I - X^T X
-// (all threads).  After the refinement, pairs of modes whose eigenvalue gap is
-// near the refinement's threshold keep an orthogonality error of second order
-// in the FP32 eigenvectors' error (1e-5 with Jacobi rotations skipped below
-// the floor); this step takes it to the square of that, well below the
-// rounding of the stored modes to binary32.
-__device__ __noinline__ void reorth64(TileSmem& S, int n) {
-  const int tid = threadIdx.x;
+  float* R = S.G32;                             // the Gram is not needed any more
   for (int e = tid; e < NM * NM; e += kTT) {
     const int i = e / NM, j = e % NM;
     if (i < n && j < n && i <= j) {
-      double rr = 0.0;
-      for (int k = 0; k < n; ++k) rr = fma(S.X64[k * NM + i], S.X64[k * NM + j], rr);
-      rr = (i == j ? 1.0 : 0.0) - rr;
-      S.R64[i * NM + j] = rr;
-      S.R64[j * NM + i] = rr;
+      float sh = 0.0f, sl = 0.0f;
+      for (int k = 0; k < n; ++k) {
+        const float x = S.Vj[k * NM + i], y = S.Vj[k * NM + j];
+        const float ph = __fmul_rn(x, y);
+        const float pl = __fmaf_rn(x, y, -ph);  // x y = ph + pl exactly
+        const float t = __fadd_rn(sh, ph);
+        const float bv = __fsub_rn(t, sh);
+        const float er = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bv)), __fsub_rn(ph, bv));   // sh + ph = t + er
+        sh = t;
+        sl = __fadd_rn(sl, __fadd_rn(er, pl));
+      }
+      // delta_ij - (sh + sl); 1 - sh is exact for sh in [1/2, 2]
+      const float r = i == j ? __fsub_rn(__fsub_rn(1.0f, sh), sl) : -__fadd_rn(sh, sl);
+      R[i * NM + j] = r;
+      R[j * NM + i] = r;
     }
   }
   __syncthreads();
-  double xn[2] = {0.0, 0.0};
+  float xn[NM * NM / kTT];
   int cnt = 0;
   for (int e = tid; e < NM * NM; e += kTT, ++cnt) {
     const int i = e / NM, j = e % NM;
+    xn[cnt] = 0.0f;
     if (i < n && j < n) {
-      double v = S.X64[e];
-      for (int k = 0; k < n; ++k) v = fma(S.X64[i * NM + k], 0.5 * S.R64[k * NM + j], v);
-      xn[cnt] = v;
+      float c = 0.0f;
+      for (int k = 0; k < n; ++k) c = __fmaf_rn(S.Vj[i * NM + k], R[k * NM + j], c);
+      xn[cnt] = __fmaf_rn(0.5f, c, S.Vj[e]);
     }
   }
   __syncthreads();
   cnt = 0;
   for (int e = tid; e < NM * NM; e += kTT, ++cnt) {
     const int i = e / NM, j = e % NM;
-    if (i < n && j < n) S.X64[e] = xn[cnt];
+    if (i < n && j < n) S.X64[e] = (double)xn[cnt];
   }
   __syncthreads();
 }
@@ -1250,51 +1222,59 @@ __device__ __noinline__ bool pass_all_errors(const TileArgs& a, const Maps& tm, 
 // FP64 evaluation of E(r) in the fixed order of the definition (per column,
 // rows in chunks of 32, chunk sums in order, column sums in order), from the
 // input in global memory.  Used only when the FP32 estimate cannot decide.
+// Thread t takes chunk t of each group of kTT chunks: it decodes each of its
+// rows once and accumulates every column's chunk sum; the chunk sums of a
+// group wait in the staging ring (idle between passes) and thread j adds
+// column j's in chunk order.
 __device__ __noinline__ double exact_error(const TileArgs& a, TileSmem& S, const Geom& g, int r, const RowConst& rcst) {
   const int tid = threadIdx.x, n = g.n;
   const int64_t nch = cdiv(g.L, 32);
-  // kTT doubles of scratch (T64 may hold the bitmap of the encode pass)
-  double* part = reinterpret_cast<double*>(&S.red[0][0]);
-  static_assert(sizeof(S.red) >= kTT * sizeof(double), "scratch");
+  double* part = reinterpret_cast<double*>(&S.ring[0][0]);      // kTT chunks x NM columns
+  static_assert(sizeof(S.ring) >= kTT * NM * sizeof(double), "scratch");
   double colsum = 0.0;
-  for (int j = 0; j < n; ++j) {
-    for (int64_t c0 = 0; c0 < nch; c0 += kTT) {
-      const int64_t c = c0 + tid;
-      if (c < nch) {
-        double pc = 0.0;
-        const int64_t l1 = (c + 1) * 32 < g.L ? (c + 1) * 32 : g.L;
-        for (int64_t l = c * 32; l < l1; ++l) {
-          float x[NM];
+  for (int64_t c0 = 0; c0 < nch; c0 += kTT) {
+    const int64_t c = c0 + tid;
+    if (c < nch) {
+      double pc[NM];
 #pragma unroll
-          for (int jj = 0; jj < NM; ++jj) x[jj] = jj < n ? __ldg(a.in + gidx_row(a, g, l, jj)) : 0.0f;
-          float d[NM];
-          shifted(x, d);
-          int ovf = 0;
-          float acc[NM];
+      for (int j = 0; j < NM; ++j) pc[j] = 0.0;
+      const int64_t l1 = (c + 1) * 32 < g.L ? (c + 1) * 32 : g.L;
+      for (int64_t l = c * 32; l < l1; ++l) {
+        float x[NM];
 #pragma unroll
-          for (int jj = 0; jj < NM; ++jj) acc[jj] = 0.0f;
-          for (int k = 0; k < r; ++k) {
-            int32_t q;
-            const float chk = coeff_q<0>(S, d, x[0], n, k, rcst, q, ovf);
-            row_decode_step(S, k, chk, acc);
-          }
-          float aj = acc[0];
+        for (int jj = 0; jj < NM; ++jj) x[jj] = jj < n ? __ldg(a.in + gidx_row(a, g, l, jj)) : 0.0f;
+        float d[NM];
+        shifted(x, d);
+        int ovf = 0;
+        float acc[NM];
 #pragma unroll
-          for (int jj = 1; jj < NM; ++jj) aj = (jj == j) ? acc[jj] : aj;
-          const double dd = __dsub_rn((double)x[j], (double)aj);
-          pc = __fma_rn(dd, dd, pc);
+        for (int jj = 0; jj < NM; ++jj) acc[jj] = 0.0f;
+        for (int k = 0; k < r; ++k) {
+          int32_t q;
+          const float chk = coeff_q<0>(S, d, x[0], n, k, rcst, q, ovf);
+          row_decode_step(S, k, chk, acc);
         }
-        part[tid] = pc;
+#pragma unroll
+        for (int j = 0; j < NM; ++j) {
+          if (j < n) {
+            const double dd = __dsub_rn((double)x[j], (double)acc[j]);
+            pc[j] = __fma_rn(dd, dd, pc[j]);
+          }
+        }
       }
-      __syncthreads();
-      if (tid == j) {
-        const int64_t cend = (nch - c0) < kTT ? (nch - c0) : kTT;
-        for (int64_t cc = 0; cc < cend; ++cc) colsum = __dadd_rn(colsum, part[cc]);
-      }
-      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < NM; ++j) part[tid * NM + j] = pc[j];
     }
+    __syncthreads();
+    if (tid < n) {
+      const int64_t cend = (nch - c0) < kTT ? (nch - c0) : kTT;
+      for (int64_t cc = 0; cc < cend; ++cc) colsum = __dadd_rn(colsum, part[cc * NM + tid]);
+    }
+    __syncthreads();
   }
   if (tid < n) S.lam_t[tid] = colsum;           // lam_t is free once the basis is ordered
+  // the ring's next writer is the copy engine (async proxy)
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
   double E = 0.0;
   for (int j = 0; j < n; ++j) E = __dadd_rn(E, S.lam_t[j]);
@@ -1848,7 +1828,7 @@ __device__ __noinline__ void defer_record(const TileArgs& a, TileSmem& S, const 
   __syncthreads();
 }
 
-// ---------------------------------------------------------------- the kernel
+// ---------------------------------------------------------------- the kernels
 // The eigensolver out of line: inline, it would share the kernel's registers
 // with the block state the body keeps live across it.
 __device__ __noinline__ void jacobi_tile(TileSmem& S, int n, float jfloor) {
@@ -1856,39 +1836,266 @@ __device__ __noinline__ void jacobi_tile(TileSmem& S, int n, float jfloor) {
   else jacobi_cta<kTT>(S.G32, S.Vj, S.lam_t, n, jfloor, S.jp);
 }
 
-// TC: the tensor-core Gram (its instantiation alone contains tcgen05 code).
-// The arguments stay in parameter space (the passes take their address).
-template <int MINB, bool TC>
-__global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUtensorMap tmap,
-                                                    const __grid_constant__ CUtensorMap tmapg,
-                                                    const __grid_constant__ TileArgs a) {
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // TMA destinations: align the tile ring to 1024 bytes explicitly
-  const uint32_t sbase = smem_u32(smem_raw);
-  TileSmem& S = *reinterpret_cast<TileSmem*>(smem_raw + (((sbase + 1023u) & ~1023u) - sbase));
-  const Maps tm{&tmap, &tmapg};
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int32_t* qs = a.q_scr + (int64_t)blockIdx.x * NM * a.lmax;
-  int8_t* k8 = a.k8_scr + (int64_t)blockIdx.x * a.nptmax;
-  int32_t* k32 = a.k32_scr + (int64_t)blockIdx.x * a.nptmax;
-  uint32_t* bits = a.bit_scr + (int64_t)blockIdx.x * (align_up(a.nptmax, 32) / 32);
-  const Plan& P = a.P;
-  // tensor-core Gram: the lo buffer follows the shared struct (1024-aligned)
-  float* lobuf = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(&S) +
-                                          align_up((int64_t)sizeof(TileSmem), 1024));
-  (void)lobuf;
-  if (tid == 0) {
+// The compression of the tile route runs as phase kernels over all its
+// blocks:
+//   k_gram  the Gram pass and the block statistics (streams every block once);
+//   k_eig   the eigensolve, FP64 refinement, ordering and the rank prediction
+//           (no staging ring: many CTAs per SM hide its barriers and its
+//           FP64 latency);
+//   k_enc   the encode pass at the predicted rank, the exact acceptance test
+//           and the deferred record, for the blocks where all of that applies
+//           (learned or tail rank, pointwise bound, full blocks);
+//   k_tile  every other block, from a list k_enc fills (or all blocks with
+//           the bisection): the Rayleigh-Ritz pass, the search, records that
+//           cannot be deferred.  It loads the state k_gram and k_eig left, so
+//           each block's basis, and so its stored bytes, do not depend on the
+//           kernel that writes its record.
+struct FastBlock {
+  float G[NM * NM];                  // FP32 Gram, entries i, j < n
+  float VstT[NM * NM];               // stored modes, VstT[k * NM + j] = Vst[j][k]
+  double lam[NM];                    // eigenvalues, descending
+  double lam_tr;                     // their sum
+  float vsum[NM];
+  float st_min[kWarps], st_max[kWarps], st_tg[kWarps], st_xg[kWarps], st_rowmax[kWarps];
+  int32_t flags, rpred;
+  int32_t pad[2];
+};
+enum : int32_t { kFbNonfinite = 1, kFbRR = 2, kFbOverflow = 4 };
+
+// Block counters of the phase kernels and the list of blocks k_enc leaves.
+struct FastCtl {
+  unsigned long long next_gram, next_eig, next_enc, next_list;
+  unsigned long long nlist;
+  unsigned long long next_rrg, next_rre;
+  unsigned long long pad;
+};
+
+struct PhaseClock {
+  long long t;
+  __device__ void start() {
+    if (threadIdx.x == 0) t = clock64();
+  }
+  __device__ void mark(TileSmem& S, int p) {
+    if (threadIdx.x == 0) {
+      const long long now = clock64();
+      S.ph[p] += (unsigned long long)(now - t);
+      t = now;
+    }
+  }
+};
+
+// The next block of [blo, bhi) whose Gram side is time, from a counter.
+__device__ __forceinline__ int64_t grab_range(const TileArgs& a, unsigned long long* ctr) {
+  for (;;) {
+    const int64_t b = a.blo + (int64_t)atomicAdd(ctr, 1ull);
+    if (b >= a.bhi) return a.bhi;
+    if (block_geom(a.P, a.P.b0 + b).side == 0) return b;
+  }
+}
+
+// Shared-memory set-up common to the kernels that stream blocks: mbarriers,
+// counters and the abort flag (thread 0), then a CTA barrier.
+__device__ void init_stream_smem(const TileArgs& a, TileSmem& S) {
+  if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) mbar_init(&S.full[s], a.use_tma ? 1u : (unsigned)kTT);
     mbar_init(&S.mma_bar, 1u);
     S.mma_phase = 0;
     S.mma_pending = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (threadIdx.x < kPhases) S.ph[threadIdx.x] = 0;
+  if (threadIdx.x == 0) {
     S.nexact = 0;
     S.abort_flag = 0;
+    S.cvar = -1;
+  }
+}
+
+// Constants of the block's variable (thread 0 recomputes them when it changes).
+__device__ void var_consts(TileSmem& S, const Geom& g, const VarInfo& vi, bool pointwise) {
+  if (threadIdx.x == 0) {
+    S.nonfinite = 0;
+    S.ovf = 0;
+    if (S.cvar != g.v) {
+      S.cvar = g.v;
+      S.crc.delta = vi.delta;
+      S.crc.inv_delta = __double2float_rn(1.0 / vi.delta);
+      S.crc.delta_f = __double2float_rn(vi.delta);
+      S.ccc = make_corr_const(vi.eb, vi.step, pointwise);
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ double local_tol2(const Plan& P, const VarInfo& vi, const Geom& g) {
+  return (P.eb_type == DLS_EB_NRMSE) ? (vi.eb * vi.eb) * ((double)g.N / (double)P.K) : (vi.eb * vi.eb) * (double)g.N;
+}
+
+// Jacobi skip floor: rotations below 5% of the per-mode budget eb^2 L change
+// no decision worth a sweep; the decisions themselves stay exact.
+__device__ __forceinline__ float jacobi_floor(const TileArgs& a, const VarInfo& vi, const Geom& g, double el2) {
+  return (float)(a.jfloor * (a.P.eb_type == DLS_EB_NRMSE ? el2 / g.n : vi.eb * vi.eb * (double)g.L));
+}
+
+// FP32 Jacobi, orthonormalisation of its eigenvectors, ordering, trace.
+// (An FP64 Ogita-Aishima refinement step took a third of the per-block time
+// and only improved eigenvector accuracy, whose effect on the energy a mode
+// captures is second order; the orthonormality of the stored modes is what
+// the method needs, and the re-orthonormalisation alone gives it.)
+__device__ void eigen_block(TileSmem& S, int n, float jfloor, PhaseClock& pc) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // the eigensolve starts from the identity: its result depends on this
+  // block's Gram alone, whichever blocks the CTA took before
+  jacobi_tile(S, n, jfloor);
+  pc.mark(S, kPhJacobi);
+  orth_basis(S, n, false);
+  if (warp == 0) {
+    order_basis(S, n, lane);
+    __syncwarp();
+    if (lane == 0) {
+      double tr = 0.0;
+      for (int i = 0; i < n; ++i) tr += S.lam[i];
+      S.lam_tr = tr;
+    }
+  }
+  __syncthreads();
+  pc.mark(S, kPhRefine);
+}
+
+// Tight bounds need the modes an FP32 Gram cannot resolve (eigenvalues near
+// 2^-24 trace G): a Rayleigh-Ritz step on the projected data fixes them, when
+// that resolution reaches half the per-mode budget eb^2 L.
+__device__ __forceinline__ bool rr_wanted(const TileSmem& S, const Plan& P, const VarInfo& vi, const Geom& g,
+                                          double el2) {
+  const double budget = (vi.eb * vi.eb) * (double)g.L;
+  const double noise = (P.eb_type == DLS_EB_NRMSE ? el2 / g.n : budget);
+  return g.n > 1 && 4.0 * 5.9604644775390625e-8 * S.lam_tr > 0.5 * noise;
+}
+
+// |c_k| <= ||row|| (1 + 1e-4) for every column: no coefficient can reach 2^24 steps.
+__device__ __forceinline__ bool overflow_possible(const TileSmem& S, const VarInfo& vi) {
+  float rowmax = 0.0f;
+  for (int w = 0; w < kWarps; ++w) rowmax = fmaxf(rowmax, S.st_rowmax[w]);
+  return !((double)sqrtf(rowmax) * 1.0001 / vi.delta < 16777216.0 * 0.999);
+}
+
+// The predicted rank (warp 0 computes, every thread returns it).
+__device__ int predicted_rank(const TileArgs& a, TileSmem& S, const Geom& g, int64_t bi, int rcap, double el2,
+                              double delta) {
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x < 32) {
+    const int rp = predict_rank(a, S, g, bi, rcap, el2, delta, lane);
+    int rm = rp;
+    if (a.learned == kRankMlp && a.model) rm = mlp_rank_warp(a.model, S.featv, S.mh1, lane, rcap);
+    if (lane == 0) S.r_pred = rm;
+  }
+  __syncthreads();
+  return S.r_pred;
+}
+
+// k_gram -> state: the Gram and the statistics of the block.
+__device__ void store_gram(const TileSmem& S, FastBlock& f) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < NM * NM; e += kTT) f.G[e] = S.G32[e];
+  if (tid < kWarps) {
+    f.st_min[tid] = S.st_min[tid];
+    f.st_max[tid] = S.st_max[tid];
+    f.st_tg[tid] = S.st_tg[tid];
+    f.st_xg[tid] = S.st_xg[tid];
+    f.st_rowmax[tid] = S.st_rowmax[tid];
+  }
+  if (tid == 0) f.flags = S.nonfinite ? kFbNonfinite : 0;
+}
+// state -> k_eig: the Gram (and its FP64 copy) and the statistics.
+__device__ void load_gram(TileSmem& S, const FastBlock& f, int n) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < NM * NM; e += kTT) {
+    const float v = f.G[e];
+    S.G32[e] = v;
+    if (e / NM < n && e % NM < n) S.G64[e] = (double)v;
+  }
+  if (tid < kWarps) {
+    S.st_min[tid] = f.st_min[tid];
+    S.st_max[tid] = f.st_max[tid];
+    S.st_tg[tid] = f.st_tg[tid];
+    S.st_xg[tid] = f.st_xg[tid];
+    S.st_rowmax[tid] = f.st_rowmax[tid];
+  }
+  if (tid == 0) S.nonfinite = (f.flags & kFbNonfinite) ? 1 : 0;
+  __syncthreads();
+}
+// k_eig -> state: the ordered basis, eigenvalues, flags and predicted rank.
+__device__ void store_basis(const TileSmem& S, FastBlock& f, int32_t flags, int rpred) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < NM * NM; e += kTT) f.VstT[e] = S.VstT[e];
+  if (tid < NM) {
+    f.vsum[tid] = S.vsum[tid];
+    f.lam[tid] = S.lam[tid];
+  }
+  if (tid == 0) {
+    f.lam_tr = S.lam_tr;
+    f.flags = flags;
+    f.rpred = rpred;
+  }
+}
+// state -> k_enc / k_tile: everything the passes after the eigensolve read.
+__device__ void load_basis(TileSmem& S, const FastBlock& f) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < NM * NM; e += kTT) S.VstT[e] = f.VstT[e];
+  if (tid < NM) {
+    S.vsum[tid] = f.vsum[tid];
+    S.lam[tid] = f.lam[tid];
+  }
+  if (tid < kWarps) {
+    S.st_min[tid] = f.st_min[tid];
+    S.st_max[tid] = f.st_max[tid];
+    S.st_tg[tid] = f.st_tg[tid];
+    S.st_xg[tid] = f.st_xg[tid];
+    S.st_rowmax[tid] = f.st_rowmax[tid];
+  }
+  if (tid == 0) {
+    S.lam_tr = f.lam_tr;
+    S.nonfinite = (f.flags & kFbNonfinite) ? 1 : 0;
+    S.r_pred = f.rpred;
+  }
+  __syncthreads();
+}
+
+// Phase counters of a phase kernel's CTA into the workspace slot it shares
+// with others (more CTAs than slots).
+__device__ void flush_phases(const TileArgs& a, TileSmem& S) {
+  if (threadIdx.x == 0) {
+    S.ph[kCntExact] += S.nexact;
+    if (a.phase)
+      for (int i = 0; i < kPhases; ++i)
+        if (S.ph[i]) atomicAdd(&a.phase[(int64_t)(blockIdx.x % a.ctas) * kPhases + i], S.ph[i]);
+  }
+}
+
+// Leaves no copy and no product in flight, then gives back the TMEM.
+template <bool TC>
+__device__ void finish_stream(TileSmem& S, Cursor& cu) {
+  while (cu.con < cu.iss) {
+    mbar_wait(&S.full[cu.con % kStages], (cu.con / kStages) & 1u);
+    ++cu.con;
   }
   if (TC) {
-    if (warp == 0) {
+    if (threadIdx.x == 0 && S.mma_pending) mbar_wait(&S.mma_bar, S.mma_phase & 1u);
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      tc_fence_after();
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem_base), "r"(kTmemCols)
+                   : "memory");
+    }
+  }
+}
+
+template <bool TC>
+__device__ void alloc_tmem(TileSmem& S) {
+  if (TC) {
+    if (threadIdx.x < 32) {
       asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
                    "r"(kTmemCols)
                    : "memory");
@@ -1901,26 +2108,314 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
   } else {
     __syncthreads();
   }
+}
+
+__device__ __forceinline__ TileSmem& tile_smem(unsigned char* smem_raw) {
+  // TMA destinations: align the tile ring to 1024 bytes explicitly
+  const uint32_t sbase = smem_u32(smem_raw);
+  return *reinterpret_cast<TileSmem*>(smem_raw + (((sbase + 1023u) & ~1023u) - sbase));
+}
+
+// ---------------------------------------------------------------- k_gram
+// The Gram pass of every block of the launch's range: FP32 Gram (or the
+// 3xTF32 tensor-core Gram) and statistics into the block's state.
+template <int MINB, bool TC>
+__global__ void __launch_bounds__(kTT, MINB) k_gram(const __grid_constant__ CUtensorMap tmap,
+                                                    const __grid_constant__ CUtensorMap tmapg,
+                                                    const __grid_constant__ TileArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  TileSmem& S = tile_smem(smem_raw);
+  const Maps tm{&tmap, &tmapg};
+  const Plan& P = a.P;
+  float* lobuf = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(&S) +
+                                          align_up((int64_t)sizeof(TileSmem), 1024));
+  (void)lobuf;
+  init_stream_smem(a, S);
+  alloc_tmem<TC>(S);
+  PhaseClock pc;
+  Cursor cu;
+  cu.iss = 0; cu.con = 0; cu.pf_blk = -1; cu.pf_cnt = 0; cu.pf_layout = kLayoutRow;
+  if (threadIdx.x == 0) S.bnext = grab_range(a, &a.ctl->next_gram);
+  __syncthreads();
+  for (;;) {
+    const int64_t bi = S.bnext;
+    __syncthreads();
+    if (bi >= a.bhi) break;
+    if (threadIdx.x == 0) S.bnext = grab_range(a, &a.ctl->next_gram);
+    const Geom g = block_geom(P, P.b0 + bi);
+    if (threadIdx.x == 0) S.nonfinite = 0;
+    __syncthreads();
+    pc.start();
+    bool ok;
+    if (TC) ok = pass_gram_tc(a, tm, S, cu, bi, g, lobuf);
+    else ok = g.n == NM ? pass_gram<false, NM>(a, tm, S, cu, bi, g) : pass_gram<false, 0>(a, tm, S, cu, bi, g);
+    if (!ok) break;
+    // the next block's first chunks load while this one's state is written
+    {
+      const int64_t bn = S.bnext;
+      if (bn < a.bhi) prefetch(a, tm, S, cu, bn, block_geom(P, P.b0 + bn), TC ? kLayoutGram : kLayoutRow);
+    }
+    if (S.nonfinite && threadIdx.x == 0) atomicOr(&a.status->nonfinite, 1u);
+    store_gram(S, a.fb[bi]);
+    pc.mark(S, kPhGram);
+    __syncthreads();
+  }
+  if (S.abort_flag && threadIdx.x == 0) atomicOr(&a.status->timeout, 1u);
+  finish_stream<TC>(S, cu);
+  flush_phases(a, S);
+}
+
+// The next block of the range that k_eig flagged for the Rayleigh-Ritz pass.
+__device__ __forceinline__ int64_t grab_rr(const TileArgs& a, unsigned long long* ctr) {
+  for (;;) {
+    const int64_t b = grab_range(a, ctr);
+    if (b >= a.bhi || (a.fb[b].flags & kFbRR)) return b;
+  }
+}
+
+// ---------------------------------------------------------------- k_eig
+// Eigensolve, orthonormalisation, ordering and rank prediction of every block
+// of the range, from the Gram k_gram left.  Blocks whose FP32 Gram cannot
+// resolve the modes near the budget are flagged for the Rayleigh-Ritz pass,
+// blocks whose coefficients might overflow for k_tile.
+// RR: the second solve of the Rayleigh-Ritz pass, on the flagged blocks, from
+// the Gram of their rows projected on the first basis (k_rrgram): the rotated
+// basis V = Vst W in FP64, orthonormalised, ordered, and the rank predicted.
+template <bool RR>
+__global__ void __launch_bounds__(kTT, 5) k_eig(const __grid_constant__ TileArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  TileSmem& S = tile_smem(smem_raw);       // only the part before the staging ring
+  const Plan& P = a.P;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned long long* ctr = RR ? &a.ctl->next_rre : &a.ctl->next_eig;
+  auto next = [&]() { return RR ? grab_rr(a, ctr) : grab_range(a, ctr); };
   if (tid < kPhases) S.ph[tid] = 0;
-  long long tck = clock64();
-  auto mark = [&](int p) {
-    if (tid == 0) {
-      const long long now = clock64();
-      S.ph[p] += (unsigned long long)(now - tck);
-      tck = now;
+  if (tid == 0) {
+    S.nexact = 0;
+    S.bnext = next();
+  }
+  __syncthreads();
+  PhaseClock pc;
+  for (;;) {
+    const int64_t bi = S.bnext;
+    __syncthreads();
+    if (bi >= a.bhi) break;
+    if (tid == 0) S.bnext = next();
+    const Geom g = block_geom(P, P.b0 + bi);
+    const VarInfo vi = a.vars[g.v];
+    const int n = g.n;
+    const int rcap = P.rank_cap < n ? P.rank_cap : n;
+    const double el2 = local_tol2(P, vi, g);
+    FastBlock& f = a.fb[bi];
+    pc.start();
+    const int32_t flags0 = f.flags;
+    load_gram(S, f, n);
+    if (S.nonfinite) continue;                  // k_gram has set the status
+    const float jfloor = jacobi_floor(a, vi, g, el2);
+    int32_t flags = 0;
+    if (RR) {
+      load_basis(S, f);                         // the first basis
+      jacobi_tile(S, n, jfloor);
+      // V = Vst W, orthonormalised; eigenvalues from the Rayleigh-Ritz diagonal
+      orth_basis(S, n, true);
+      if (warp == 0) order_basis(S, n, lane);
+      __syncthreads();
+      pc.mark(S, kPhRR);
+      flags = flags0 & ~kFbRR;
+    } else {
+      eigen_block(S, n, jfloor, pc);
+      if (rr_wanted(S, P, vi, g, el2)) flags |= kFbRR;
+      if (overflow_possible(S, vi)) flags |= kFbOverflow;
+    }
+    int rp = 0;
+    if (!(flags & kFbRR)) rp = predicted_rank(a, S, g, bi, rcap, el2, vi.delta);
+    pc.mark(S, kPhPredict);
+    store_basis(S, f, flags, rp);
+    __syncthreads();
+  }
+  flush_phases(a, S);
+}
+
+// ---------------------------------------------------------------- k_rrgram
+// First half of the Rayleigh-Ritz pass, for the blocks k_eig flagged: the Gram
+// of the block's rows projected on its first basis (the coefficients the
+// encode pass computes), into the block's state for k_eig<true>.
+template <int MINB>
+__global__ void __launch_bounds__(kTT, MINB) k_rrgram(const __grid_constant__ CUtensorMap tmap,
+                                                      const __grid_constant__ CUtensorMap tmapg,
+                                                      const __grid_constant__ TileArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  TileSmem& S = tile_smem(smem_raw);
+  const Maps tm{&tmap, &tmapg};
+  const Plan& P = a.P;
+  init_stream_smem(a, S);
+  __syncthreads();
+  PhaseClock pc;
+  Cursor cu;
+  cu.iss = 0; cu.con = 0; cu.pf_blk = -1; cu.pf_cnt = 0; cu.pf_layout = kLayoutRow;
+  if (threadIdx.x == 0) S.bnext = grab_rr(a, &a.ctl->next_rrg);
+  __syncthreads();
+  for (;;) {
+    const int64_t bi = S.bnext;
+    __syncthreads();
+    if (bi >= a.bhi) break;
+    if (threadIdx.x == 0) S.bnext = grab_rr(a, &a.ctl->next_rrg);
+    const Geom g = block_geom(P, P.b0 + bi);
+    pc.start();
+    load_basis(S, a.fb[bi]);
+    const bool ok = g.n == NM ? pass_gram<true, NM>(a, tm, S, cu, bi, g) : pass_gram<true, 0>(a, tm, S, cu, bi, g);
+    if (!ok) break;
+    {
+      const int64_t bn = S.bnext;
+      if (bn < a.bhi) prefetch(a, tm, S, cu, bn, block_geom(P, P.b0 + bn), kLayoutRow);
+    }
+    FastBlock& f = a.fb[bi];
+    for (int e = threadIdx.x; e < NM * NM; e += kTT) f.G[e] = S.G32[e];
+    pc.mark(S, kPhRR);
+    __syncthreads();
+  }
+  if (S.abort_flag && threadIdx.x == 0) atomicOr(&a.status->timeout, 1u);
+  finish_stream<false>(S, cu);
+  flush_phases(a, S);
+}
+
+// ---------------------------------------------------------------- k_enc
+// Encode pass at the predicted rank, exact acceptance test (pass(r) and not
+// pass(r - 1), FP64 semantics) and the deferred record, for the blocks where
+// all of that applies; every other block goes to the list k_tile takes.
+template <int MINB>
+__global__ void __launch_bounds__(kTT, MINB) k_enc(const __grid_constant__ CUtensorMap tmap,
+                                                   const __grid_constant__ CUtensorMap tmapg,
+                                                   const __grid_constant__ TileArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  TileSmem& S = tile_smem(smem_raw);
+  const Maps tm{&tmap, &tmapg};
+  const Plan& P = a.P;
+  int32_t* k32 = a.k32_scr + (int64_t)blockIdx.x * a.nptmax;
+  init_stream_smem(a, S);
+  __syncthreads();
+  PhaseClock pc;
+  Cursor cu;
+  cu.iss = 0; cu.con = 0; cu.pf_blk = -1; cu.pf_cnt = 0; cu.pf_layout = kLayoutRow;
+  auto eligible = [&](int64_t b, int* rp_out) -> bool {
+    const Geom gb = block_geom(P, P.b0 + b);
+    const FastBlock& fb = a.fb[b];
+    const int rp = fb.rpred;
+    *rp_out = rp;
+    return !(fb.flags & (kFbNonfinite | kFbRR | kFbOverflow)) && gb.n == NM && bitmap_rows(a, gb) &&
+           gb.N <= (int64_t)kBitsSmem * 32 && slot_scratch(rp, gb.n, gb.L, gb.N).fits;
+  };
+  auto to_list = [&](int64_t b) {
+    if (threadIdx.x == 0) {
+      const unsigned long long i = atomicAdd(&a.ctl->nlist, 1ull);
+      a.list[i] = (int32_t)b;
     }
   };
+  const bool pointwise = P.eb_type != DLS_EB_NRMSE;
+  if (threadIdx.x == 0) S.bnext = grab_range(a, &a.ctl->next_enc);
+  __syncthreads();
+  for (;;) {
+    const int64_t bi = S.bnext;
+    __syncthreads();
+    if (bi >= a.bhi) break;
+    if (threadIdx.x == 0) S.bnext = grab_range(a, &a.ctl->next_enc);
+    const Geom g = block_geom(P, P.b0 + bi);
+    int rp = 0;
+    if (!pointwise || !eligible(bi, &rp)) {
+      if (!(a.fb[bi].flags & kFbNonfinite)) to_list(bi);
+      __syncthreads();          // thread 0 has taken the next block
+      continue;
+    }
+    const VarInfo vi = a.vars[g.v];
+    const double el2 = local_tol2(P, vi, g);
+    var_consts(S, g, vi, pointwise);
+    const RowConst rcst = S.crc;
+    const CorrConst cc = S.ccc;
+    pc.start();
+    load_basis(S, a.fb[bi]);
+    uint8_t* const slot = a.staging + align_up((g.pt_off - P.pt_base) * 4, 16) + 48 * bi;
+    const SlotScratch sc = slot_scratch(rp, g.n, g.L, g.N);
+    if (threadIdx.x == 0) {
+      S.esc_list = reinterpret_cast<uint32_t*>(slot + sc.off_esc);
+      S.esc_cap = (int)sc.esc_cap;
+    }
+    if (!pass_encode<NM, true>(a, tm, S, cu, bi, g, rp, true, rcst, cc, true,
+                               reinterpret_cast<int32_t*>(slot + sc.off_q), reinterpret_cast<int8_t*>(slot + sc.off_k8),
+                               k32, S.bitsm))
+      break;
+    pc.mark(S, kPhEncode);
+    bool accepted = false;
+    if (!S.ovf) {
+      const Chunks chk = chunks_of(a, g);
+      const double bnd = (double)(cdiv(a.rc, kTT) * chk.n * g.n + 40) * 6.6e-8;
+      const double E_rm1 = S.Ered[0], E_r = S.Ered[1];
+      const bool p_r = decide_pass(a, S, g, rp, E_r, bnd, el2, rcst);
+      bool p_rm1 = false;
+      if (rp > 0 && p_r) p_rm1 = decide_pass(a, S, g, rp - 1, E_rm1, bnd, el2, rcst);
+      accepted = p_r && !p_rm1;
+    }
+    // a deferred record has no correction beyond kDeferMaxWk bits, its
+    // escapes fit the slot's list and, when sparse, so does its entry list
+    if (accepted) {
+      const int wk = bit_width((uint32_t)S.kmax), ib = bit_width((uint32_t)(g.N - 1));
+      const bool dense = wk > 0 && (g.N * wk + 31) / 32 < ((int64_t)S.ncorr * (ib + wk) + 31) / 32;
+      if (wk > kDeferMaxWk || (!dense && S.ncorr > sc.list_cap) || S.nesc > sc.esc_cap) accepted = false;
+    }
+    pc.mark(S, kPhDecide);
+    if (!accepted) {
+      to_list(bi);
+      __syncthreads();
+      continue;
+    }
+    {
+      int rn = 0;
+      const int64_t bn = S.bnext;
+      if (bn < a.bhi && pointwise && eligible(bn, &rn)) prefetch(a, tm, S, cu, bn, block_geom(P, P.b0 + bn), kLayoutRow);
+    }
+    defer_record(a, S, g, bi, rp, S.bitsm);
+    pc.mark(S, kPhPack);
+    if (threadIdx.x == 0) S.ph[kCntAccepted] += 1;
+  }
+  if (S.abort_flag && threadIdx.x == 0) atomicOr(&a.status->timeout, 1u);
+  finish_stream<false>(S, cu);
+  flush_phases(a, S);
+}
+
+// ---------------------------------------------------------------- k_tile
+// Every block k_enc does not finish, with the block state (basis, eigenvalues,
+// statistics) k_gram and k_eig left: the Rayleigh-Ritz pass where the FP32
+// Gram cannot resolve the modes near the budget, the rank test of a
+// prediction and the bisection of Algorithm 1 when it fails (or always, with
+// the search rank mode), and records that cannot be deferred.  With
+// a.from_list the blocks come from k_enc's list, else from the launch range.
+// The arguments stay in parameter space (the passes take their address).
+template <int MINB>
+__global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUtensorMap tmap,
+                                                    const __grid_constant__ CUtensorMap tmapg,
+                                                    const __grid_constant__ TileArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  TileSmem& S = tile_smem(smem_raw);
+  const Maps tm{&tmap, &tmapg};
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int32_t* qs = a.q_scr + (int64_t)blockIdx.x * NM * a.lmax;
+  int8_t* k8 = a.k8_scr + (int64_t)blockIdx.x * a.nptmax;
+  int32_t* k32 = a.k32_scr + (int64_t)blockIdx.x * a.nptmax;
+  uint32_t* bits = a.bit_scr + (int64_t)blockIdx.x * (align_up(a.nptmax, 32) / 32);
+  const Plan& P = a.P;
+  init_stream_smem(a, S);
+  __syncthreads();
+  PhaseClock pc;
   // blocks whose Gram side is time; the others are left to k_mixed
   auto grab = [&]() -> int64_t {
-    for (;;) {
-      const int64_t b = a.blo + (int64_t)atomicAdd(&a.status->pad[1], 1ull);
-      if (b >= a.bhi) return a.bhi;
-      if (block_geom(P, P.b0 + b).side == 0) return b;
+    if (a.from_list) {
+      const unsigned long long i = atomicAdd(&a.ctl->next_list, 1ull);
+      return i < a.ctl->nlist ? (int64_t)a.list[i] : a.bhi;
     }
+    return grab_range(a, &a.status->pad[1]);
   };
   Cursor cu;
   cu.iss = 0; cu.con = 0; cu.pf_blk = -1; cu.pf_cnt = 0; cu.pf_layout = kLayoutRow;
-  if (tid == 0) { S.bnext = grab(); S.cvar = -1; }
+  if (tid == 0) S.bnext = grab();
   __syncthreads();
   for (;;) {
     const int64_t bi = S.bnext;
@@ -1932,97 +2427,35 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
     const int n = g.n;
     const int rcap = P.rank_cap < n ? P.rank_cap : n;
     const bool pointwise = P.eb_type != DLS_EB_NRMSE;
-    const double el2 = (P.eb_type == DLS_EB_NRMSE) ? (vi.eb * vi.eb) * ((double)g.N / (double)P.K)
-                                                   : (vi.eb * vi.eb) * (double)g.N;
-    if (tid == 0) {
-      S.nonfinite = 0; S.ovf = 0;
-      if (S.cvar != g.v) {
-        S.cvar = g.v;
-        S.crc.delta = vi.delta;
-        S.crc.inv_delta = __double2float_rn(1.0 / vi.delta);
-        S.crc.delta_f = __double2float_rn(vi.delta);
-        S.ccc = make_corr_const(vi.eb, vi.step, pointwise);
-      }
-    }
-    __syncthreads();
+    const double el2 = local_tol2(P, vi, g);
+    var_consts(S, g, vi, pointwise);
     const RowConst rcst = S.crc;
     const CorrConst cc = S.ccc;
 
-    if (tid == 0) tck = clock64();
+    pc.start();
     const bool full = n == NM;   // Gram order 16: the passes without per-column predicates
-    if (TC) {
-      if (!pass_gram_tc(a, tm, S, cu, bi, g, lobuf)) break;
-    } else if (!(full ? pass_gram<false, NM>(a, tm, S, cu, bi, g) : pass_gram<false, 0>(a, tm, S, cu, bi, g))) {
-      break;
-    }
-    mark(kPhGram);
-    if (S.nonfinite) {
-      if (tid == 0) atomicOr(&a.status->nonfinite, 1u);
-      __syncthreads();
-      continue;
-    }
-    // the encode pass reads the same block again: start its first chunks now
+    const float jfloor = jacobi_floor(a, vi, g, el2);
+    load_basis(S, a.fb[bi]);
+    if (S.nonfinite) continue;                  // k_gram has set the status
     prefetch(a, tm, S, cu, bi, g, kLayoutRow);
-    // rotations below 5% of the per-mode budget eb^2 L change no decision
-    // worth a sweep; the decisions themselves stay exact
-    const float jfloor = (float)(a.jfloor * (P.eb_type == DLS_EB_NRMSE ? el2 / n : vi.eb * vi.eb * (double)g.L));
-    // the eigensolve starts from the identity: its result depends on this
-    // block's Gram alone, whichever blocks the CTA took before
-    jacobi_tile(S, n, jfloor);
-    mark(kPhJacobi);
-    refine64(S, n);
-    reorth64(S, n);
-    if (warp == 0) {
-      order_basis(S, n, lane);
-      __syncwarp();
-      if (lane == 0) {
-        double tr = 0.0;
-        for (int i = 0; i < n; ++i) tr += S.lam[i];
-        S.lam_tr = tr;
-      }
+    // the Rayleigh-Ritz pass, if k_rrgram and k_eig<true> have not done it
+    bool did_rr = false;
+    if (a.fb[bi].flags & kFbRR) {
+      did_rr = true;
+      if (!(full ? pass_gram<true, NM>(a, tm, S, cu, bi, g) : pass_gram<true, 0>(a, tm, S, cu, bi, g))) break;
+      prefetch(a, tm, S, cu, bi, g, kLayoutRow);
+      jacobi_tile(S, n, jfloor);
+      // V = Vst W, orthonormalised; eigenvalues from the Rayleigh-Ritz diagonal
+      orth_basis(S, n, true);
+      if (warp == 0) order_basis(S, n, lane);
+      __syncthreads();
     }
-    __syncthreads();
-    mark(kPhRefine);
-    // Tight bounds need the modes an FP32 Gram cannot resolve (eigenvalues near
-    // 2^-24 trace G): one Rayleigh-Ritz step on the projected data fixes them,
-    // when that resolution reaches half the per-mode budget eb^2 L.
-    {
-      const double tr = S.lam_tr;
-      const double budget = (vi.eb * vi.eb) * (double)g.L;
-      const double noise = (P.eb_type == DLS_EB_NRMSE ? el2 / n : budget);
-      if (n > 1 && 4.0 * 5.9604644775390625e-8 * tr > 0.5 * noise) {
-        if (!(full ? pass_gram<true, NM>(a, tm, S, cu, bi, g) : pass_gram<true, 0>(a, tm, S, cu, bi, g))) break;
-        prefetch(a, tm, S, cu, bi, g, kLayoutRow);
-        jacobi_tile(S, n, jfloor);
-        // V = Vst W in FP64; eigenvalues from the Rayleigh-Ritz diagonal
-        for (int e = tid; e < NM * NM; e += kTT) {
-          const int i = e / NM, j = e % NM;
-          if (i < n && j < n) {
-            double v = 0.0;
-            for (int k = 0; k < n; ++k) v = fma((double)S.VstT[k * NM + i], (double)S.Vj[k * NM + j], v);
-            S.X64[e] = v;
-          }
-        }
-        __syncthreads();
-        reorth64(S, n);
-        if (warp == 0) order_basis(S, n, lane);
-        __syncthreads();
-      }
-    }
-    mark(kPhRR);
+    pc.mark(S, kPhRR);
 
-    float rowmax = 0.0f;
-    for (int w = 0; w < kWarps; ++w) rowmax = fmaxf(rowmax, S.st_rowmax[w]);
-    const bool may_overflow = !((double)sqrtf(rowmax) * 1.0001 / vi.delta < 16777216.0 * 0.999);
-
-    if (warp == 0) {
-      const int rp = predict_rank(a, S, g, bi, rcap, el2, vi.delta, lane);
-      int rm = rp;
-      if (a.learned == kRankMlp && a.model) rm = mlp_rank_warp(a.model, S.featv, S.mh1, lane, rcap);
-      if (lane == 0) S.r_pred = rm;
-    }
-    __syncthreads();
-    mark(kPhPredict);
+    const bool may_overflow = overflow_possible(S, vi);
+    // the prediction k_eig made, unless the Rayleigh-Ritz pass changed the basis
+    if (did_rr) predicted_rank(a, S, g, bi, rcap, el2, vi.delta);
+    pc.mark(S, kPhPredict);
 
     // the encode pass at rank rr; SPARSE where the bitmap carries the corrections,
     // kept in shared memory when the block has at most kBitsSmem * 32 points
@@ -2061,7 +2494,7 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
     if (a.learned != kRankSearch && !may_overflow) {
       const int rp = S.r_pred;
       if (!encode(rp, true, sparse, false)) break;
-      mark(kPhEncode);
+      pc.mark(S, kPhEncode);
       const double E_rm1 = S.Ered[0], E_r = S.Ered[1];
       if (!S.ovf) {
         const bool p_r = decide_pass(a, S, g, rp, E_r, bnd, el2, rcst);
@@ -2070,7 +2503,7 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
         accepted = p_r && !p_rm1;
         r = rp;
       }
-      mark(kPhDecide);
+      pc.mark(S, kPhDecide);
     }
     bool raw = false;
     if (!accepted) {
@@ -2097,7 +2530,7 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
         if (!pointwise && !decide_pass(a, S, g, r, Eall[r], bnd, el2, rcst)) raw = true;
         if (!raw && !encode(r, false, sparse, false)) break;
       }
-      mark(kPhSearch);
+      pc.mark(S, kPhSearch);
     }
     // a deferred record has no correction beyond kDeferMaxWk bits, its
     // escapes fit the slot's list and, when sparse, so does its entry list;
@@ -2118,31 +2551,17 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
     // the next block's first chunks load while this record is packed
     {
       const int64_t bn = S.bnext;
-      if (bn < a.bhi) prefetch(a, tm, S, cu, bn, block_geom(P, P.b0 + bn), TC ? kLayoutGram : kLayoutRow);
+      if (bn < a.bhi) prefetch(a, tm, S, cu, bn, block_geom(P, P.b0 + bn), kLayoutRow);
     }
     if (deferred) defer_record(a, S, g, bi, r, bitp);
     else write_record(a, S, g, bi, raw, r, qs, k8, k32, bitp);
-    mark(kPhPack);
+    pc.mark(S, kPhPack);
     if (tid == 0) S.ph[accepted ? kCntAccepted : kCntSearched] += 1;
   }
   if (S.abort_flag) {
     if (tid == 0) atomicOr(&a.status->timeout, 1u);
   }
-  // leave no copy and no product in flight, then give back the TMEM
-  while (cu.con < cu.iss) {
-    mbar_wait(&S.full[cu.con % kStages], (cu.con / kStages) & 1u);
-    ++cu.con;
-  }
-  if (TC) {
-    if (tid == 0 && S.mma_pending) mbar_wait(&S.mma_bar, S.mma_phase & 1u);
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) {
-      tc_fence_after();
-      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem_base), "r"(kTmemCols)
-                   : "memory");
-    }
-  }
+  finish_stream<false>(S, cu);
   if (tid == 0) {
     S.ph[kCntExact] = S.nexact;
     if (a.phase)
@@ -2283,20 +2702,20 @@ size_t tile_smem_bytes(bool tc) {
   return 1024 + (size_t)align_up((int64_t)sizeof(TileSmem), 1024) + (tc ? (size_t)kStageFloats * 4 : 0);
 }
 
+// Dynamic shared memory of k_eig: the shared struct up to the staging ring.
+size_t eig_smem_bytes() { return 1024 + (size_t)offsetof(TileSmem, ring); }
+
 // Resident CTAs per SM from the kernel's registers and shared memory and the
 // device's per-SM limits (and, with the tensor-core Gram, the TMEM columns).
 // Computed here because the occupancy query treats a kernel that contains
 // tcgen05.alloc as one CTA per SM.
-template <int MINB, bool TC>
-int ctas_per_sm_of() {
-  const bool tc = TC;
-  const size_t smem = tile_smem_bytes(tc);
-  if (cudaFuncSetAttribute(k_tile<MINB, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return 0;
+template <class K>
+int ctas_per_sm_of(K kernel, size_t smem, bool tc) {
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   cudaFuncAttributes fa;
   int dev = 0;
   cudaDeviceProp prop;
-  if (cudaFuncGetAttributes(&fa, k_tile<MINB, TC>) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
       cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
     return 0;
   // registers are allocated per warp in units of 256
@@ -2312,17 +2731,27 @@ int ctas_per_sm_of() {
   return n;
 }
 
-int tile_ctas_per_sm(int variant, bool tc) {
-  const int n = tc ? (variant == 1 ? ctas_per_sm_of<2, true>() : ctas_per_sm_of<4, true>())
-                  : (variant == 1 ? ctas_per_sm_of<2, false>() : ctas_per_sm_of<4, false>());
+int tile_ctas_per_sm(int variant) {
+  const size_t sm = tile_smem_bytes(false);
+  const int n = variant == 1 ? ctas_per_sm_of(k_tile<2>, sm, false) : ctas_per_sm_of(k_tile<4>, sm, false);
   cudaGetLastError();
   return n;
 }
 
+// Bytes of the phase kernels' state in the workspace for a plan of nb blocks.
+size_t tile_fast_bytes(int64_t nb) {
+  const int64_t n1 = nb > 0 ? nb : 1;
+  return (size_t)align_up((int64_t)sizeof(FastCtl), 256) + (size_t)align_up(n1 * (int64_t)sizeof(FastBlock), 256) +
+         (size_t)align_up(n1 * 4, 256);
+}
+
 int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, int learned, int variant,
-                         cudaStream_t s, int64_t blo, int64_t bhi) {
+                         cudaStream_t s, int64_t blo, int64_t bhi, const cudaEvent_t* pev) {
+  auto mark = [&](int i) -> bool {
+    return !pev || !pev[i] || cudaEventRecordWithFlags(pev[i], s, cudaEventRecordExternal) == cudaSuccess;
+  };
   if (bhi < 0) bhi = p.nb;
-  if (blo < 0 || blo > bhi || bhi > p.nb) return DLS_ERR_INVALID_ARG;
+  if (blo < 0 || blo > bhi || bhi > p.nb || !w.fast || !w.phase || w.ctas < 1) return DLS_ERR_INVALID_ARG;
   if (bhi == blo) return DLS_OK;
   TileArgs a;
   memset(&a, 0, sizeof(a));
@@ -2346,6 +2775,15 @@ int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, in
   a.phase = w.phase;
   a.withhold = fault_withheld_block();
   a.model = rank_model_device();
+  a.ctas = w.ctas;
+  {
+    uint8_t* f = w.fast;
+    a.ctl = reinterpret_cast<FastCtl*>(f);
+    f += align_up((int64_t)sizeof(FastCtl), 256);
+    a.fb = reinterpret_cast<FastBlock*>(f);
+    f += align_up((p.nb > 0 ? p.nb : 1) * (int64_t)sizeof(FastBlock), 256);
+    a.list = reinterpret_cast<int32_t*>(f);
+  }
   if (!tile_chunk_box(p, &a.bxb, &a.yc, &a.zc, &a.bt)) return DLS_ERR_INVALID_ARG;
   a.rc = a.bxb * a.yc * a.zc;
   auto magic = [](int d) -> uint32_t { return d <= 1 ? 0u : (uint32_t)((0x100000000ull + (uint64_t)d - 1) / (uint64_t)d); };
@@ -2392,18 +2830,70 @@ int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, in
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return DLS_ERR_CUDA;
-  const int per_sm = tile_ctas_per_sm(variant, a.tc_gram != 0);
-  if (per_sm < 1) return DLS_ERR_CUDA;
-  int ctas = sms * per_sm;
-  if (ctas > w.ctas) ctas = w.ctas;
-  if ((int64_t)ctas > bhi - blo) ctas = (int)(bhi - blo);
-  const size_t smem = tile_smem_bytes(a.tc_gram != 0);
-  if (a.tc_gram) {
-    if (variant == 1) k_tile<2, true><<<ctas, kTT, smem, s>>>(tmap, tmapg, a);
-    else k_tile<4, true><<<ctas, kTT, smem, s>>>(tmap, tmapg, a);
-  } else {
-    if (variant == 1) k_tile<2, false><<<ctas, kTT, smem, s>>>(tmap, tmapg, a);
-    else k_tile<4, false><<<ctas, kTT, smem, s>>>(tmap, tmapg, a);
+  const int64_t nblk = bhi - blo;
+  auto grid_of = [&](int per_sm, int cap) -> int {
+    int64_t c = (int64_t)sms * per_sm;
+    if (cap > 0 && c > cap) c = cap;
+    if (c > nblk) c = nblk;
+    return (int)(c > 0 ? c : 1);
+  };
+  const bool tc = a.tc_gram != 0;
+  // counters and list of this launch
+  if (cudaMemsetAsync(a.ctl, 0, sizeof(FastCtl), s) != cudaSuccess) return DLS_ERR_CUDA;
+  // 1. Gram pass (4 CTAs per SM: the staging ring and, with the tensor-core
+  //    Gram, the TMEM columns)
+  {
+    const size_t sm = tile_smem_bytes(tc);
+    const int per = tc ? ctas_per_sm_of(k_gram<4, true>, sm, true) : ctas_per_sm_of(k_gram<4, false>, sm, false);
+    cudaGetLastError();
+    if (per < 1) return DLS_ERR_CUDA;
+    const int grid = grid_of(per, w.ctas);
+    if (tc) k_gram<4, true><<<grid, kTT, sm, s>>>(tmap, tmapg, a);
+    else k_gram<4, false><<<grid, kTT, sm, s>>>(tmap, tmapg, a);
+    if (!mark(0)) return DLS_ERR_CUDA;
+  }
+  // 2. eigensolve and prediction (no staging ring: more CTAs per SM)
+  {
+    const size_t sm = eig_smem_bytes();
+    const int per = ctas_per_sm_of(k_eig<false>, sm, false);
+    cudaGetLastError();
+    if (per < 1) return DLS_ERR_CUDA;
+    k_eig<false><<<grid_of(per, 0), kTT, sm, s>>>(a);
+    if (!mark(1)) return DLS_ERR_CUDA;
+  }
+  // 2b. the Rayleigh-Ritz pass of the flagged blocks: projected Gram, second solve
+  {
+    const size_t tsm0 = tile_smem_bytes(false);
+    const int per = ctas_per_sm_of(k_rrgram<4>, tsm0, false);
+    const size_t sm = eig_smem_bytes();
+    const int pere = ctas_per_sm_of(k_eig<true>, sm, false);
+    cudaGetLastError();
+    if (per < 1 || pere < 1) return DLS_ERR_CUDA;
+    k_rrgram<4><<<grid_of(per, w.ctas), kTT, tsm0, s>>>(tmap, tmapg, a);
+    k_eig<true><<<grid_of(pere, 0), kTT, sm, s>>>(a);
+    if (!mark(2)) return DLS_ERR_CUDA;
+  }
+  // 3. encode pass and deferred record at the predicted rank
+  const size_t tsm = tile_smem_bytes(false);
+  if (learned != kRankSearch) {
+    const int per = variant == 1 ? ctas_per_sm_of(k_enc<2>, tsm, false) : ctas_per_sm_of(k_enc<4>, tsm, false);
+    cudaGetLastError();
+    if (per < 1) return DLS_ERR_CUDA;
+    const int grid = grid_of(per, w.ctas);
+    if (variant == 1) k_enc<2><<<grid, kTT, tsm, s>>>(tmap, tmapg, a);
+    else k_enc<4><<<grid, kTT, tsm, s>>>(tmap, tmapg, a);
+    a.from_list = 1;
+  }
+  if (!mark(3)) return DLS_ERR_CUDA;
+  // 4. the other blocks (all of them with the bisection)
+  {
+    const int per = tile_ctas_per_sm(variant);
+    if (per < 1) return DLS_ERR_CUDA;
+    int ctas = sms * per;
+    if (ctas > w.ctas) ctas = w.ctas;
+    if ((int64_t)ctas > nblk) ctas = (int)nblk;
+    if (variant == 1) k_tile<2><<<ctas, kTT, tsm, s>>>(tmap, tmapg, a);
+    else k_tile<4><<<ctas, kTT, tsm, s>>>(tmap, tmapg, a);
   }
   return cudaGetLastError() == cudaSuccess ? DLS_OK : DLS_ERR_CUDA;
 }

@@ -104,6 +104,7 @@ _SIGS = {
     "dls_plan_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
     "dls_plan_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_int32)]),
     "dls_plan_destroy": (C.c_int, [C.c_void_p]),
+    "dls_plan_phase_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int32]),
     "dls_phase_cycles": (C.c_int, [C.POINTER(Params), C.c_void_p, C.POINTER(C.c_ulonglong), C.c_int32]),
     "dls_stage_quantize": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dls_stage_correct": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_void_p]),
@@ -411,6 +412,17 @@ class CompressPlan:
         if st != OK:
             raise DlsError(st, "dls_plan_timing")
         return ms.value, nk.value
+
+    PHASES = ("gram", "eig", "rr", "enc", "tile", "pack")
+
+    def phase_timing(self) -> dict:
+        """Device ms of each stage of the last execute (k_gram, k_eig, the
+        Rayleigh-Ritz kernels, k_enc, k_tile / k_mixed, scan + record packing)."""
+        ms = (C.c_float * 6)()
+        st = lib().dls_plan_phase_timing(self.handle, ms, 6)
+        if st != OK:
+            raise DlsError(st, "dls_plan_phase_timing")
+        return {k: ms[i] for i, k in enumerate(self.PHASES)}
 
     def close(self):
         if self.handle:
