@@ -39,11 +39,12 @@ SEED = 2
 FORMS = {"plain": (0, 0), "fp32": (3, 0), "learned": (3, 1), "tail": (3, 2)}
 FORM_TEXT = {
     "plain": "plain FP64 (Gram, Jacobi, projection, bisection, correction in FP64)",
-    "fp32": "FP32 products, FP32 Jacobi + FP64 refinement, bisection on E(r) for all r, FP64-semantics decisions",
-    "learned": "FP32 products, FP32 Jacobi + FP64 refinement, MLP-predicted rank checked exactly (bisection "
-               "fallback), FP64-semantics decisions",
-    "tail": "FP32 products, FP32 Jacobi + FP64 refinement, eigenvalue-tail rank estimate checked exactly "
-            "(bisection fallback), FP64-semantics decisions",
+    "fp32": "FP32 products, FP32 Jacobi + orthonormalisation (error-free FP32 transforms), bisection on E(r) for "
+            "all r, FP64-semantics decisions",
+    "learned": "FP32 products, FP32 Jacobi + orthonormalisation (error-free FP32 transforms), MLP-predicted rank "
+               "checked exactly (bisection fallback), FP64-semantics decisions",
+    "tail": "FP32 products, FP32 Jacobi + orthonormalisation (error-free FP32 transforms), eigenvalue-tail rank "
+            "estimate checked exactly (bisection fallback), FP64-semantics decisions",
 }
 
 
@@ -212,7 +213,11 @@ KERNEL_SOURCES = {
     "plain": ["k_plain.cu", "dls_internal.cuh"],
     "mixed": ["k_tile.cu", "mixed_common.cuh", "dls_device.cuh", "dls_internal.cuh"],
 }
-PROFILE = {"plain": "profiles/k_plain_fp64_modes3d.md", "mixed": "profiles/k_tile_modes3d.md"}
+PROFILE = {"plain": "profiles/k_plain_fp64_modes3d.md", "mixed": "profiles/k_enc_modes3d.md"}
+# stage of a mixed-form plan -> (kernel, what its algorithmic bytes are)
+PHASE_KERNEL = {"gram": ("k_gram", "input, read once"), "eig": ("k_eig", None), "rr": ("k_rrgram", None),
+                "enc": ("k_enc", "input, read once (records: deferred packer)"), "tile": ("k_tile", None),
+                "pack": ("k_pack_tile", "stream written")}
 
 
 def _sources_sha(kind):
@@ -242,23 +247,34 @@ def _profile_traffic(kind, blocks):
     return float(vals["dram_bytes_per_block"]) * blocks
 
 
-def _roofline(form, in_bytes, out_bytes, kernel_ms, hbm, peak_kind, dims):
-    """Dominant kernel: the per-block compression kernel(s), timed by events
-    inside the captured graph.  Algorithmic bytes per launch: the plain form
-    reads the field once and writes the records (about the stream size); the
-    mixed forms' per-block kernel reads the field once and leaves the records
-    of full blocks to the deferred packer (k_pack_tile)."""
-    kind = "plain" if form == "plain" else "mixed"
+def _roofline(form, in_bytes, out_bytes, kernel_ms, hbm, peak_kind, dims, phases=None):
+    """Dominant kernel, timed by CUDA events inside the captured graph.  The
+    plain form has one per-block kernel (k_plain): algorithmic bytes = the field
+    read once + the records written.  The mixed forms run as stages (k_gram,
+    k_eig, the Rayleigh-Ritz kernels, k_enc, k_tile, scan + k_pack_tile); the
+    dominant one is the stage with the largest share of the step, and its
+    algorithmic bytes are those of PHASE_KERNEL (k_gram and k_enc: the field
+    read once; k_pack_tile: the stream written)."""
     blocks = 1
     for d, b in zip(dims, BLOCK):
         blocks *= -(-d // b)
-    alg = in_bytes + out_bytes if kind == "plain" else in_bytes
-    ach = alg / (kernel_ms * 1e-3) / 1e9
-    what = "input + records" if kind == "plain" else "input (records: deferred packer)"
-    return {"bound": "hbm", "kernel": "k_plain" if kind == "plain" else "k_tile", "achieved": ach, "peak": hbm,
-            "unit": "GB/s", "frac": ach / hbm, "traffic": _profile_traffic(kind, blocks),
-            "algorithmic_bytes": alg, "kernel_ms": kernel_ms,
-            "note": f"peak = {peak_kind} HBM copy bandwidth; algorithmic bytes = {what}"}
+    if form == "plain":
+        alg = in_bytes + out_bytes
+        ach = alg / (kernel_ms * 1e-3) / 1e9
+        return {"bound": "hbm", "kernel": "k_plain", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": _profile_traffic("plain", blocks), "algorithmic_bytes": alg,
+                "kernel_ms": kernel_ms,
+                "note": f"peak = {peak_kind} HBM copy bandwidth; algorithmic bytes = input + records"}
+    top = max(phases, key=phases.get)
+    kern, what = PHASE_KERNEL[top]
+    alg = out_bytes if top == "pack" else in_bytes
+    ms = phases[top]
+    ach = alg / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": kern, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "traffic": _profile_traffic("mixed", blocks) if kern == "k_enc" else None,
+            "algorithmic_bytes": alg, "kernel_ms": ms,
+            "note": f"peak = {peak_kind} HBM copy bandwidth; algorithmic bytes = {what or 'n/a'}; "
+                    f"share of the step {ms / sum(phases.values()):.2f}"}
 
 
 def _config(form="learned"):
@@ -283,6 +299,7 @@ def main():
     ap.add_argument("--dims", default=None, help="nx,ny,nz,nt override (profiling on a small case)")
     ap.add_argument("--form", default="learned", choices=sorted(FORMS))
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP64 form beside")
+    ap.add_argument("--no-forms", action="store_true", help="skip timing the search and tail rank modes beside")
     ap.add_argument("--rel", type=float, default=1e-3,
                     help="absolute bound as a fraction of the value range (1e-2, 1e-3, 1e-4 in the at-scale config)")
     args = ap.parse_args()
@@ -312,10 +329,11 @@ def main():
     field = make_field(dev, seed=SEED + 1000 * rank)
     rng = float(field.max() - field.min())
     eb = REL_BOUND * rng
-    if args.form == "learned":
-        from paper_2601_20113_gb300 import train_rank
-        if not os.path.exists(train_rank.DEFAULT_MODEL):
-            raise SystemExit("learned form needs paper_2601_20113_gb300/rank_model.bin (train_rank.py)")
+    from paper_2601_20113_gb300 import train_rank
+    have_model = os.path.exists(train_rank.DEFAULT_MODEL)
+    if args.form == "learned" and not have_model:
+        raise SystemExit("learned form needs paper_2601_20113_gb300/rank_model.bin (train_rank.py)")
+    if have_model:
         dls.set_rank_model(train_rank.load_model())
     form = FORMS[args.form]
     p = dls.make_params(tuple(field.shape), torch.float32, BLOCK, eb, dls.EB_ABS, RANK_CAP,
@@ -339,15 +357,20 @@ def main():
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     kms = []
+    phs = []
     e0.record(stream)
     for _ in range(args.steps):
         nb = plan.execute(stream)
         kms.append(plan.timing()[0])
+        if args.form != "plain":
+            phs.append(plan.phase_timing())
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     clk = clocks.stop()
     kernel_ms = sum(kms) / len(kms)
+    phases = {k: sum(d[k] for d in phs) / len(phs) for k in phs[0]} if phs else None
+    counters = dls.phase_cycles(p, ws) if args.form != "plain" else None
     graph_kernels = plan.timing()[1]
     variant, tune_ms = plan.info()
     plan.close()
@@ -394,7 +417,10 @@ def main():
         "data": "synthetic", "config": _config(args.form),
         "ratio": ratio, "max_abs_err": rep["max_abs_err"], "eb": eb, "n_over_bound": rep["n_over_bound"],
         "mean_rank": rep["mean_rank"], "decompress_gbs": in_bytes / (dms * 1e-3) / 1e9,
-        "roofline": _roofline(args.form, in_bytes, nb, kernel_ms, hbm, peak_kind, DIMS),
+        "roofline": _roofline(args.form, in_bytes, nb, kernel_ms, hbm, peak_kind, DIMS, phases),
+        "phases_ms": phases,
+        "rank_selection": ({"accepted": counters["n_accepted"], "searched": counters["n_searched"],
+                            "exact_fp64_fallbacks": counters["n_exact_fallback"]} if counters else None),
         "e2e": {"value": in_bytes * world / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": in_bytes,
                 "d2h_bytes_per_step": enb},
         "gpu_launches": graph_kernels * args.steps,
@@ -417,6 +443,33 @@ def main():
         line["plain_fp64"] = {"value": in_bytes / (pms * 1e-3) / 1e9, "unit": "GB/s", "ratio": in_bytes / pnb,
                               "ms_per_step": pms, "speedup_of_headline": pms / ms}
         del wsp
+    if args.form != "plain" and not args.no_forms:
+        # the same field through the other rank modes of the FP32 form, each
+        # with its own captured plan: what the network buys over the search
+        # and over the eigenvalue-tail heuristic it is fed
+        line["forms"] = {}
+        for fname in ("fp32", "tail", "learned") if have_model else ("fp32", "tail"):
+            fp = dls.make_params(tuple(field.shape), torch.float32, BLOCK, eb, dls.EB_ABS, RANK_CAP,
+                                 precision=FORMS[fname][0], rank_mode=FORMS[fname][1])
+            fws = torch.empty(dls.workspace_size(fp), dtype=torch.uint8, device=dev)
+            fplan = dls.CompressPlan(fp, field, out, fws, stream)
+            for _ in range(2):
+                fplan.execute(stream)
+            torch.cuda.synchronize()
+            q0 = torch.cuda.Event(enable_timing=True)
+            q1 = torch.cuda.Event(enable_timing=True)
+            q0.record(stream)
+            for _ in range(args.steps):
+                fnb = fplan.execute(stream)
+            q1.record(stream)
+            torch.cuda.synchronize()
+            fms = q0.elapsed_time(q1) / args.steps
+            fc = dls.phase_cycles(fp, fws)
+            line["forms"][fname] = {"ms_per_step": fms, "value": in_bytes / (fms * 1e-3) / 1e9, "unit": "GB/s",
+                                    "ratio": in_bytes / fnb, "n_accepted": fc["n_accepted"],
+                                    "n_searched": fc["n_searched"], "phases_ms": fplan.phase_timing()}
+            fplan.close()
+            del fws
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         fcpu = field[:, :16, :16].cpu().numpy()
         v, cores, desc, el = oracle_sample_bench(fcpu, eb)
