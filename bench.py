@@ -289,6 +289,76 @@ def _config(form="learned"):
             "l2": "inputs 4 GiB > 129 MB L2 (no flush)"}
 
 
+PRECISIONS = {"bf16": 5, "tf32": 4, "bf16x3": 2, "tf32x3": 1, "fp32": 3}
+
+
+def run_precision_sweep(args):
+    """Every precision mode of the Gram (BF16, TF32, BF16x3, 3xTF32, FP32) at
+    bounds 1e-2 .. 1e-5 x range on the at-scale field, against the FP64 oracle
+    (compressed and decompressed on the host cores): ratio, max pointwise error
+    over the bound, NRMSE, the reconstruction difference from the oracle's, and
+    GB/s of each mode's captured plan (search rank mode, so that the modes
+    differ in the Gram alone)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2601_20113_gb300 import build, dls
+
+    build.build()
+    oracle.build()
+    dev = torch.device("cuda", 0)
+    field = make_field(dev)
+    fh = field.cpu().numpy()
+    x = fh.astype(np.float64)
+    xnorm = float(np.linalg.norm(x))
+    rng = float(field.max() - field.min())
+    in_bytes = field.numel() * 4
+    rows = []
+    for rel in (1e-2, 1e-3, 1e-4, 1e-5):
+        eb = rel * rng
+        cfg = oracle.Config(DIMS, BLOCK, oracle.F32, eb=eb, rank_cap=RANK_CAP)
+        ts = time.time()
+        st, ref, _ = oracle.compress(cfg, fh)
+        assert st == 0
+        st, xo = oracle.decompress(ref)
+        assert st == 0
+        o_s = time.time() - ts
+        xo = xo.astype(np.float64)
+        o_nrmse = 100 * float(np.linalg.norm(xo - x)) / xnorm
+        for name, prec in PRECISIONS.items():
+            p = dls.make_params(tuple(field.shape), torch.float32, BLOCK, eb, dls.EB_ABS, RANK_CAP, precision=prec,
+                                rank_mode=dls.RANK_SEARCH)
+            out = torch.empty(dls.compress_bound(p), dtype=torch.uint8, device=dev)
+            ws = torch.empty(dls.workspace_size(p), dtype=torch.uint8, device=dev)
+            plan = dls.CompressPlan(p, field, out, ws)
+            nb = plan.execute()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                nb = plan.execute()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 3
+            ntc = dls.phase_cycles(p, ws)["n_tensor_core_gram"]
+            plan.close()
+            rec = dls.decompress(out[:nb]).cpu().numpy().astype(np.float64)
+            rows.append({"precision": name, "rel_bound": rel, "ratio": in_bytes / nb,
+                         "ratio_vs_oracle": (in_bytes / nb) / (in_bytes / ref.size) - 1.0,
+                         "max_err_over_eb": float(np.abs(rec - x).max()) / eb,
+                         "nrmse_pct": 100 * float(np.linalg.norm(rec - x)) / xnorm, "oracle_nrmse_pct": o_nrmse,
+                         "recon_diff_vs_oracle": float(np.linalg.norm(rec - xo)) / xnorm,
+                         "gbs": in_bytes / (ms * 1e-3) / 1e9, "tensor_core_gram_blocks": ntc,
+                         "oracle_ratio": in_bytes / ref.size, "oracle_s": o_s})
+            del out, ws, rec
+            torch.cuda.empty_cache()
+    print(json.dumps({"precision_sweep": rows, "config": _config("fp32"),
+                      "note": "Gram precision modes; projection, quantizer, rank test and corrections are FP32 with "
+                              "FP64-semantics decisions in every mode; oracle = plain FP64 CPU implementation"}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -302,6 +372,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip timing the search and tail rank modes beside")
     ap.add_argument("--rel", type=float, default=1e-3,
                     help="absolute bound as a fraction of the value range (1e-2, 1e-3, 1e-4 in the at-scale config)")
+    ap.add_argument("--sweep-precision", action="store_true",
+                    help="every Gram precision mode at bounds 1e-2..1e-5 against the FP64 oracle (one JSON line)")
     args = ap.parse_args()
     global DIMS, REL_BOUND
     if args.dims:
@@ -309,6 +381,8 @@ def main():
     REL_BOUND = args.rel
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep_precision:
+        return run_precision_sweep(args)
 
     import numpy as np
     import torch

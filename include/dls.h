@@ -52,15 +52,24 @@ enum { DLS_EB_ABS = 0, DLS_EB_REL_RANGE = 1, DLS_EB_NRMSE = 2 };
  *           below the rounding of the stored modes); every stored decision
  *           (quantized coefficient, rank test, correction, escape) keeps FP64
  *           semantics.
- *   TF32X3: as FP32, with the block Gram on the tensor cores (tcgen05) as a
- *           3-term TF32 split product (hi hi + hi lo + lo hi, FP32
- *           accumulation) for 16 x 16 x bz x 16 blocks of a field whose x
- *           extent is a multiple of 4; other blocks use the FP32 Gram.  The
- *           projection stays on the CUDA cores.
- *   BF16X3: reserved (rejected with DLS_ERR_INVALID_ARG).
- * Non-FP64 modes apply to float32 fields with a Gram order <= 16; other
- * fields take the FP64 form whatever the mode. */
-enum { DLS_PREC_FP64 = 0, DLS_PREC_TF32X3 = 1, DLS_PREC_BF16X3 = 2, DLS_PREC_FP32 = 3 };
+ *   TF32X3: as FP32, with the block Gram on the tensor cores (tcgen05,
+ *           kind::tf32) as a 3-term TF32 split product (hi hi + hi lo + lo hi,
+ *           FP32 accumulation; about 21 bits of each value) for
+ *           16 x 16 x bz x 16 blocks of a field whose x extent is a multiple
+ *           of 4; other blocks use the FP32 Gram.
+ *   TF32:   as TF32X3 with the one product hi hi (10-bit mantissas).
+ *   BF16X3: as TF32X3 with the Gram as the three-product BF16 split of
+ *           Henry, Tang and Heinecke (2019) on tcgen05 kind::f16:
+ *           b0 b0 + b0 b1 + b1 b0 with b0 = bf16(x), b1 = bf16(x - b0)
+ *           (relative error about 2^-16).
+ *   BF16:   as BF16X3 with the one product b0 b0 (8-bit mantissas).
+ * In every non-FP64 mode the projection, the quantizer, the rank test and
+ * the corrections are those of FP32 (CUDA cores, FP64-semantics decisions):
+ * the modes differ in the Gram, and so in the basis, only.  Non-FP64 modes
+ * apply to float32 fields with a Gram order <= 16; other fields take the
+ * FP64 form whatever the mode. */
+enum { DLS_PREC_FP64 = 0, DLS_PREC_TF32X3 = 1, DLS_PREC_BF16X3 = 2, DLS_PREC_FP32 = 3, DLS_PREC_TF32 = 4,
+       DLS_PREC_BF16 = 5 };
 /* Rank selection.  SEARCH: bisection of Algorithm 1.  LEARNED: the loaded
  * block-rank MLP (dls_set_rank_model) predicts the rank r; it is accepted
  * only if pass(r) holds and pass(r-1) does not (the smallest passing rank next

@@ -62,10 +62,12 @@ def record_of(s, h, i):
     return s[h["payp"] + o0:h["payp"] + o1]
 
 
-def check_modes(A, Vst):
+def check_modes(A, Vst, u_prod=0.0):
     """Orthonormality of the stored modes and their Rayleigh quotients on the
-    block's FP64 Gram matrix against the oracle's eigenvalues.  Returns
-    (orthonormality error, worst eigenvalue error / bound)."""
+    block's FP64 Gram matrix against the oracle's eigenvalues.  u_prod: the
+    relative error of each Gram product's operands (0 for binary32 operands;
+    2^-21, 2^-11, 2^-16, 2^-9 for the 3xTF32, TF32, BF16x3 and BF16 tensor-core
+    Grams).  Returns (orthonormality error, worst eigenvalue error / bound)."""
     L, n = A.shape
     r = Vst.shape[1]
     if r == 0:
@@ -74,17 +76,19 @@ def check_modes(A, Vst):
     lam, _, _ = jacobi(G)
     orth = float(np.abs(Vst.T @ Vst - np.eye(r)).max())
     # A binary32 Gram summed along chains of at most L + 32 terms is G + dG with
-    # |dG_ij| <= gamma sqrt(G_ii G_jj), gamma = (L + 32) u: ||dG||_2 <= gamma
+    # |dG_ij| <= gamma sqrt(G_ii G_jj), gamma = (L + 32) u (+ 2 u_prod when the
+    # products' operands carry a relative error u_prod): ||dG||_2 <= gamma
     # trace(G).  An exact eigenvector v of G + dG then has
     # |v^T G v - lambda_k| <= 2 ||dG||_2 (Weyl), and rounding v to binary32
     # moves the quotient by at most 4 n u lambda_0 more.
-    gamma = (L + 32) * U32
+    gamma = (L + 32) * U32 + 2.0 * u_prod
     bound = 2.0 * gamma * float(np.trace(G)) + 4.0 * n * U32 * float(lam[0]) + 1e-300
     rq = np.einsum("jk,ji,ik->k", Vst, G, Vst)
     return orth, float(np.abs(rq - lam[:r]).max() / bound)
 
 
-def replay_block(cfg: Config, field, b: int, rec, eb: float, delta: float, step: float, coeff: str = "f32"):
+def replay_block(cfg: Config, field, b: int, rec, eb: float, delta: float, step: float, coeff: str = "f32",
+                 u_prod: float = 0.0):
     """Checks one record; returns a dict of findings (empty 'errors' when
     everything holds).  coeff: 'f32' (the FP32 form's coefficient definition,
     codes compared exactly) or 'f64' (the oracle's own FP64 projection)."""
@@ -149,7 +153,7 @@ def replay_block(cfg: Config, field, b: int, rec, eb: float, delta: float, step:
     if rec_o != bytes(rec):
         out["errors"].append("record bytes differ from the oracle packer's")
     # the stored modes against the oracle's eigenproblem
-    orth, lam_err = check_modes(A, Vst)
+    orth, lam_err = check_modes(A, Vst, u_prod)
     out["orth"], out["lam_err"] = orth, lam_err
     # modes orthonormal in exact arithmetic, each component rounded once to the
     # dtype (relative error u): |v_i^T v_j - delta_ij| <= 2u + u^2 by
@@ -162,7 +166,7 @@ def replay_block(cfg: Config, field, b: int, rec, eb: float, delta: float, step:
     return out
 
 
-def replay_stream(cfg: Config, field, stream, blocks=None, coeff: str = "f32"):
+def replay_stream(cfg: Config, field, stream, blocks=None, coeff: str = "f32", u_prod: float = 0.0):
     """Replays the records of `blocks` (all by default).  Returns (findings,
     stream-level errors)."""
     s, h = parse_stream(stream)
@@ -182,5 +186,5 @@ def replay_stream(cfg: Config, field, stream, blocks=None, coeff: str = "f32"):
         b = h["block_begin"] + i
         v = block_geom(cfg, b).v
         out.append(replay_block(cfg, field, b, rec, float(h["eb"][v]), float(h["delta"][v]), float(h["step"][v]),
-                                coeff))
+                                coeff, u_prod))
     return out, errs

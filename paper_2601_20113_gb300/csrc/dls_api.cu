@@ -20,9 +20,7 @@ int make_plan(const dls_params* p, Plan* out) {
   if (!p || p->nvars < 1 || p->nvars > kMaxVars || !p->eb) return DLS_ERR_INVALID_ARG;
   if (p->dtype != DLS_F32 && p->dtype != DLS_F64) return DLS_ERR_INVALID_ARG;
   if (p->eb_type < 0 || p->eb_type > 2 || p->rank_cap < 0) return DLS_ERR_INVALID_ARG;
-  if (p->precision < 0 || p->precision > 3 || p->rank_mode < 0 || p->rank_mode > 2) return DLS_ERR_INVALID_ARG;
-  // the 3-term BF16 split is reserved (TF32X3 serves the tensor-core Gram)
-  if (p->precision == DLS_PREC_BF16X3) return DLS_ERR_INVALID_ARG;
+  if (p->precision < 0 || p->precision > 5 || p->rank_mode < 0 || p->rank_mode > 2) return DLS_ERR_INVALID_ARG;
   for (int a = 0; a < 4; ++a)
     if (p->dims[a] < 1 || p->block[a] < 1 || p->block[a] > p->dims[a]) return DLS_ERR_INVALID_ARG;
   const int64_t M = (int64_t)p->block[0] * p->block[1] * p->block[2];

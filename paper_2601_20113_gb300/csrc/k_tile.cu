@@ -65,7 +65,7 @@ struct TileArgs {
   int bxb, yc, zc, bt;     // chunk box (x, y, z, t)
   int rc;                  // rows per chunk = bxb * yc * zc
   uint32_t mbx, myc;       // ceil(2^32 / bxb), ceil(2^32 / yc) (0 for a divisor of 1)
-  int tc_gram;             // 1: Gram pass on the tensor cores (3xTF32), chunk box 16 x 16 x 1 x 16
+  int tc_gram;             // Gram pass on the tensor cores (chunk box 16 x 16 x 1 x 16): a TcMode, 0 for none
   double jfloor;           // Jacobi skip floor as a fraction of the per-mode budget
   int64_t blo, bhi;        // the blocks [blo, bhi) of the plan this launch compresses
   int64_t withhold;        // test hook: the first chunk of this block is never copied (-1: none)
@@ -188,6 +188,11 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
 }
 __device__ __forceinline__ void tc_mma_tf32(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
   asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+               "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+               : "memory");
+}
+__device__ __forceinline__ void tc_mma_f16(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
                : "memory");
 }
@@ -597,27 +602,40 @@ __device__ __noinline__ bool pass_gram(const TileArgs& a, const Maps& tm, TileSm
 }
 
 // ---------------------------------------------------------------- tensor-core Gram
-// Gram pass on the tensor cores (3xTF32), for chunk boxes of 16 x 16 x 1 x 16.
+// Gram pass on the tensor cores, for chunk boxes of 16 x 16 x 1 x 16.
 // The Gram map stages a chunk as [t / 8][y][x / 4][t % 8][x % 4]: each y-pair
 // is a subset s of 32 spatial rows, and the tile is the K-major operand of a
 // 128-row matrix A whose row m = (t / 8, s, t % 8) holds time step t over the
 // 32 rows of subset s (8-row groups 1024 B apart, 4-row K steps 128 B apart,
 // no swizzle).  D = A A^T accumulates in TMEM over the chunks of the block;
 // the Gram is the sum of its eight diagonal 16 x 16 blocks (one per subset).
-// Split precision: the staged x is replaced by hi = x with its 13 low mantissa
-// bits cleared and lo = x - hi, also truncated to TF32, goes to a second
-// buffer; D += hi hi^T + hi lo^T + lo hi^T.  Both operands are exact TF32
-// values, so the products do not depend on how the tensor cores read FP32;
-// the split keeps about 21 bits of each x (relative error 2^-21).
+// Modes (the operands of each product are exact in the MMA's input type, so
+// the products do not depend on how the tensor cores convert FP32):
+//   3xTF32  hi = x with its 13 low mantissa bits cleared (in place), lo = x - hi
+//           truncated to TF32 (second buffer); D += hi hi^T + hi lo^T + lo hi^T
+//           (about 21 bits of each x kept: relative error 2^-21);
+//   TF32    D += hi hi^T (10-bit mantissas, relative error 2^-11);
+//   BF16X3  x = b0 + b1 + ..., b0 = bf16(x), b1 = bf16(x - b0) (round to
+//           nearest even), written as a K-major bf16 operand [t / 8][s][k / 8]
+//           [t % 8][k % 8] (core matrices 128 B, K neighbours 128 B apart,
+//           8-row groups 512 B apart); D += b0 b0^T + b0 b1^T + b1 b0^T
+//           (kind::f16), the three-product split of Henry, Tang and Heinecke
+//           (2019): relative error about 2^-16;
+//   BF16    D += b0 b0^T (8-bit mantissas, relative error 2^-9).
+enum TcMode : int { kTcNone = 0, kTcTf32x3 = 1, kTcTf32 = 2, kTcBf16x3 = 3, kTcBf16 = 4 };
 __device__ __forceinline__ float tf32_trunc(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
 
 __device__ __noinline__ bool pass_gram_tc(const TileArgs& a, const Maps& tm, TileSmem& S, Cursor& cu, int64_t bi,
                                           const Geom& g, float* lo) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = g.n;
+  const int mode = a.tc_gram;
+  const bool bf = mode == kTcBf16x3 || mode == kTcBf16;
   float mn = INFINITY, mx = -INFINITY, xg = 0.0f;
-  // D FP32; A, B TF32, K-major; N = 128 (bits 17-22: N/8), M = 128 (bits 24-28: M/16)
-  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+  // D FP32; N = 128 (bits 17-22: N/8), M = 128 (bits 24-28: M/16); A, B TF32
+  // (kind::tf32, format 2) or BF16 (kind::f16, format 1), K-major
+  const uint32_t fmt = bf ? 1u : 2u;
+  const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
   uint32_t accum = 0;
   const bool ok = stream_block(a, tm, S, cu, bi, g, kLayoutGram, [&](int c, const Chunks& ch, const float* tile_c) {
     float* tile = const_cast<float*>(tile_c);
@@ -643,32 +661,72 @@ __device__ __noinline__ bool pass_gram_tc(const TileArgs& a, const Maps& tm, Til
       }
     }
     __syncthreads();
-    // split into hi (in place) and lo
-    for (int gi = tid; gi < 1024; gi += kTT) {
-      const float4 v = reinterpret_cast<const float4*>(tile)[gi];
-      float4 h, l;
-      h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u); l.x = tf32_trunc(__fsub_rn(v.x, h.x));
-      h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u); l.y = tf32_trunc(__fsub_rn(v.y, h.y));
-      h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u); l.z = tf32_trunc(__fsub_rn(v.z, h.z));
-      h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u); l.w = tf32_trunc(__fsub_rn(v.w, h.w));
-      reinterpret_cast<float4*>(tile)[gi] = h;
-      reinterpret_cast<float4*>(lo)[gi] = l;
+    if (!bf) {
+      // split into hi (in place) and, for 3xTF32, lo
+      for (int gi = tid; gi < 1024; gi += kTT) {
+        const float4 v = reinterpret_cast<const float4*>(tile)[gi];
+        float4 h, l;
+        h.x = tf32_trunc(v.x); l.x = tf32_trunc(__fsub_rn(v.x, h.x));
+        h.y = tf32_trunc(v.y); l.y = tf32_trunc(__fsub_rn(v.y, h.y));
+        h.z = tf32_trunc(v.z); l.z = tf32_trunc(__fsub_rn(v.z, h.z));
+        h.w = tf32_trunc(v.w); l.w = tf32_trunc(__fsub_rn(v.w, h.w));
+        reinterpret_cast<float4*>(tile)[gi] = h;
+        if (mode == kTcTf32x3) reinterpret_cast<float4*>(lo)[gi] = l;
+      }
+    } else {
+      // bf16 operands: output row (h, s, kc, tr) holds x = 8 (kc % 2) .. + 7 of
+      // y = 2 s + kc / 2 at t = 8 h + tr; b0 in lo[0, 8 KiB), b1 after it
+      for (int o = tid; o < 512; o += kTT) {
+        const int tr = o & 7, kc = (o >> 3) & 3, sub = (o >> 5) & 7, h = o >> 8;
+        const int y = 2 * sub + (kc >> 1), xq = 2 * (kc & 1);
+        const int gi = ((h * 16 + y) * 4 + xq) * 8 + tr;
+        const float4 v0 = reinterpret_cast<const float4*>(tile)[gi];
+        const float4 v1 = reinterpret_cast<const float4*>(tile)[gi + 8];
+        const float xv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+        uint32_t p0[4], p1[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const __nv_bfloat16 a0 = __float2bfloat16_rn(xv[2 * i]), c0 = __float2bfloat16_rn(xv[2 * i + 1]);
+          const __nv_bfloat16 a1 = __float2bfloat16_rn(__fsub_rn(xv[2 * i], __bfloat162float(a0)));
+          const __nv_bfloat16 c1 = __float2bfloat16_rn(__fsub_rn(xv[2 * i + 1], __bfloat162float(c0)));
+          p0[i] = (uint32_t)__bfloat16_as_ushort(a0) | ((uint32_t)__bfloat16_as_ushort(c0) << 16);
+          p1[i] = (uint32_t)__bfloat16_as_ushort(a1) | ((uint32_t)__bfloat16_as_ushort(c1) << 16);
+        }
+        reinterpret_cast<uint4*>(lo)[o] = make_uint4(p0[0], p0[1], p0[2], p0[3]);
+        if (mode == kTcBf16x3) reinterpret_cast<uint4*>(lo)[512 + o] = make_uint4(p1[0], p1[1], p1[2], p1[3]);
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor core reads
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
-      const uint32_t ha = smem_u32(tile), la = smem_u32(lo);
+      if (!bf) {
+        const uint32_t ha = smem_u32(tile), la = smem_u32(lo);
 #pragma unroll
-      for (int ks = 0; ks < 4; ++ks) {
-        const uint64_t dh = sdesc(ha + ks * 256, 128, 1024), dl = sdesc(la + ks * 256, 128, 1024);
-        tc_mma_tf32(S.tmem_base, dh, dh, idesc, accum);
-        accum = 1;
-        tc_mma_tf32(S.tmem_base, dh, dl, idesc, 1);
-        tc_mma_tf32(S.tmem_base, dl, dh, idesc, 1);
+        for (int ks = 0; ks < 4; ++ks) {
+          const uint64_t dh = sdesc(ha + ks * 256, 128, 1024), dl = sdesc(la + ks * 256, 128, 1024);
+          tc_mma_tf32(S.tmem_base, dh, dh, idesc, accum);
+          accum = 1;
+          if (mode == kTcTf32x3) {
+            tc_mma_tf32(S.tmem_base, dh, dl, idesc, 1);
+            tc_mma_tf32(S.tmem_base, dl, dh, idesc, 1);
+          }
+        }
+      } else {
+        const uint32_t b0 = smem_u32(lo), b1 = b0 + 8192;
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+          const uint64_t d0 = sdesc(b0 + ks * 256, 128, 512), d1 = sdesc(b1 + ks * 256, 128, 512);
+          tc_mma_f16(S.tmem_base, d0, d0, idesc, accum);
+          accum = 1;
+          if (mode == kTcBf16x3) {
+            tc_mma_f16(S.tmem_base, d0, d1, idesc, 1);
+            tc_mma_f16(S.tmem_base, d1, d0, idesc, 1);
+          }
+        }
       }
       tc_commit(&S.mma_bar);
-      // the stage and the lo buffer are reused next: wait for the products
+      // the stage and the operand buffer are reused next: wait for the products
       if (mbar_wait(&S.mma_bar, S.mma_phase & 1u)) {
         ++S.mma_phase;
       } else {
@@ -2814,7 +2872,12 @@ int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, in
   CUtensorMap tmapg;
   memset(&tmapg, 0, sizeof(tmapg));
   a.tc_gram = 0;
-  if (p.precision == DLS_PREC_TF32X3 && a.use_tma && a.bxb == 16 && a.yc == 16 && a.zc == 1 && a.bt == 16) {
+  const int tc_mode = p.precision == DLS_PREC_TF32X3 ? kTcTf32x3
+                      : p.precision == DLS_PREC_TF32  ? kTcTf32
+                      : p.precision == DLS_PREC_BF16X3 ? kTcBf16x3
+                      : p.precision == DLS_PREC_BF16  ? kTcBf16
+                                                      : kTcNone;
+  if (tc_mode != kTcNone && a.use_tma && a.bxb == 16 && a.yc == 16 && a.zc == 1 && a.bt == 16) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     const cuuint64_t dims[5] = {4, (cuuint64_t)(p.dims[3] * p.nvars), (cuuint64_t)(p.dims[0] / 4), (cuuint64_t)p.dims[1],
                                 (cuuint64_t)p.dims[2]};
@@ -2825,7 +2888,7 @@ int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, in
     if (enc && enc(&tmapg, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void*>(d_in), dims, strides, box, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
-      a.tc_gram = 1;
+      a.tc_gram = tc_mode;
   }
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)

@@ -17,7 +17,7 @@ from . import build as _build
 
 F32, F64 = 0, 1
 EB_ABS, EB_REL_RANGE, EB_NRMSE = 0, 1, 2
-PREC_FP64, PREC_TF32X3, PREC_BF16X3, PREC_FP32 = 0, 1, 2, 3
+PREC_FP64, PREC_TF32X3, PREC_BF16X3, PREC_FP32, PREC_TF32, PREC_BF16 = 0, 1, 2, 3, 4, 5
 RANK_SEARCH, RANK_LEARNED, RANK_TAIL = 0, 1, 2
 MLP_NPARAM, MLP_NFEAT = 6401, 32
 OK = 0
