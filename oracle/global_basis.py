@@ -1,17 +1,20 @@
-"""Oracle of the global-basis mode: Algorithm 1 as the paper states it.
+"""Oracle of the global-basis mode (one basis per variable for all patches).
 
 Test infrastructure: only the tests (and the benchmark's CPU baseline) may
-import it.  Plain numpy in FP64, one function per step, no blocking or fusion;
-numpy's SVD and matrix-vector product serve as library steps.
+import it.  Plain numpy in FP64, one function per definition, no blocking or
+fusion; numpy's SVD and matrix-vector product serve as library steps.
 
-- learn_basis: one orthonormal basis per variable from random patches of the
-  first snapshot (Algorithm 1 step 1; Sec. 2.3, Eq. 2-3): the right singular
-  vectors of the sample matrix, by decreasing singular value.
-- local_tolerance: the per-patch L2 budget (Sec. 2.4, Eq. 4).
-- compress_patch: projection on the basis (Sec. 2.5, Eq. 5), coefficients
-  ordered by decreasing magnitude, and the smallest prefix meeting the
-  tolerance found by bisection (Eq. 6; Algorithm 1 step 3).
-- compress / decompress: every patch of every snapshot, and back.
+What it computes, by definition:
+- the modes (Sec. 2.3, Eq. 2-3): the right singular vectors, by decreasing
+  singular value, of a sample matrix whose rows are patches of the first
+  snapshot (``learn_basis``);
+- the per-patch L2 budget eps_l from the global target (Sec. 2.4, Eq. 4;
+  ``local_tolerance``);
+- the coefficients of a patch on the modes, alpha = Phi^T u (Sec. 2.5, Eq. 5),
+  and the smallest set of largest-magnitude coefficients whose reconstruction
+  meets eps_l (Eq. 6), the set size found by bisection (``compress_patch``);
+- every patch of every snapshot through that map and back (``compress`` /
+  ``decompress``).
 
 Readings where the paper is silent or loose:
 - G1 patches tile each snapshot from the origin (x fastest within a patch);
@@ -61,9 +64,9 @@ def gather_patch(snap: np.ndarray, origin, patch) -> np.ndarray:
 
 
 def learn_basis(snap0: np.ndarray, origins: np.ndarray, patch):
-    """Algorithm 1 step 1: Q (S x M) from the sampled patches of the first
-    snapshot, Q = U Sigma V^T, Phi = V (M x M, column k = mode k), with the
-    singular values (zero beyond the rank of Q) and the sign rule G3."""
+    """The modes of Sec. 2.3 (Eq. 2-3): Q (S x M) from the sampled patches of
+    the first snapshot, Q = U Sigma V^T, Phi = V (M x M, column k = mode k),
+    with the singular values (zero beyond the rank of Q) and the sign rule G3."""
     Q = np.stack([gather_patch(snap0, o, patch) for o in origins])
     _, s, vt = np.linalg.svd(Q, full_matrices=True)
     phi = vt.T.copy()
@@ -95,9 +98,9 @@ def reconstruct(phi: np.ndarray, idx: np.ndarray, q: np.ndarray, delta: float) -
 
 
 def compress_patch(u: np.ndarray, phi: np.ndarray, eps_l2: float, delta: float):
-    """Algorithm 1 step 3 for one patch: alpha = Phi^T u, the coefficients
-    ranked by decreasing magnitude (G5), quantized (G6), and the smallest n
-    with pass(n) by bisection over [0, M].  Returns (kept mode indices in kept
+    """One patch: alpha = Phi^T u (Eq. 5), the coefficients ranked by
+    decreasing magnitude (G5), quantized (G6), and the smallest n with pass(n)
+    (Eq. 6) by bisection over [0, M].  Returns (kept mode indices in kept
     order, their q, the squared error at n)."""
     u = np.asarray(u, dtype=np.float64)
     if delta == 0.0:

@@ -7,7 +7,7 @@ Prints, for modes3d fields:
   with deflate (zlib 1 / 6 / 9) over the whole stream; the share of each record
   section and how much deflate shrinks it (the plain form's GPU streams are
   byte-identical to these);
-- the global-basis form (Algorithm 1 as printed, m = 4) against the block-local
+- the global-basis form (one basis per variable, m = 4) against the block-local
   NRMSE form at the same NRMSE targets.
 """
 from __future__ import annotations

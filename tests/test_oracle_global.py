@@ -1,4 +1,4 @@
-"""Pins of the global-basis oracle (Algorithm 1 as printed: one basis per
+"""Pins of the global-basis oracle (the global-basis mode: one basis per
 variable from random patches of the first snapshot; per patch, the smallest
 magnitude-ordered prefix of its coefficients meeting the local tolerance).
 
