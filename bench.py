@@ -359,6 +359,135 @@ def run_precision_sweep(args):
     return 0
 
 
+def _plan_run(p, field, steps, stream=None):
+    """Times a captured plan of params p on field: (ms per step, nbytes, stages,
+    counters, stream bytes on the host)."""
+    import torch
+
+    from paper_2601_20113_gb300 import dls
+    out = torch.empty(dls.compress_bound(p), dtype=torch.uint8, device=field.device)
+    ws = torch.empty(dls.workspace_size(p), dtype=torch.uint8, device=field.device)
+    plan = dls.CompressPlan(p, field, out, ws, stream)
+    for _ in range(3):
+        nb = plan.execute(stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    phs = []
+    for _ in range(steps):
+        nb = plan.execute(stream)
+        phs.append(plan.phase_timing())
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    counters = dls.phase_cycles(p, ws)
+    plan.close()
+    stages = {k: sum(d[k] for d in phs) / len(phs) for k in phs[0]}
+    comp = out[:nb].clone()
+    del out, ws
+    torch.cuda.empty_cache()
+    return ms, nb, stages, counters, comp
+
+
+def run_config(args):
+    """The other at-scale configurations, one JSON line each:
+    4 -- five float32 variables (u, v, w, p, T: vortex + mode mixtures) on
+         250 x 190 x 130 x 50 with edge blocks on every axis (mixed block
+         shapes up to 16^3 x 16), bounds 1e-3 / 1e-3 / 1e-3 / 1e-4 / 1e-4 x each
+         variable's range, one captured plan; the oracle's ratio on sampled
+         block ranges of every variable beside the GPU's on the same blocks;
+    5 -- the learned-rank evaluation field: 512^3 x 32 float32 (16 GiB), abs
+         bound 1e-3 x range, learned rank with the search fallback, beside the
+         tail and search rank modes."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from oracle import replay
+    from paper_2601_20113_gb300 import build, dls, synth, train_rank
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    dls.set_rank_model(train_rank.load_model())
+    line = {"metric": METRIC, "unit": "GB/s", "n_gpus": 1, "steps": args.steps, "data": "synthetic"}
+    if args.config == 4:
+        dims = (250, 190, 130, 50)
+        field = synth.multivar(*dims, device=dev)
+        rels = [1e-3, 1e-3, 1e-3, 1e-4, 1e-4]
+        in_bytes = field.numel() * 4
+        modes = {}
+        comp = None
+        for name, rm in (("learned", dls.RANK_LEARNED), ("tail", dls.RANK_TAIL), ("search", dls.RANK_SEARCH)):
+            p = dls.make_params(tuple(field.shape), torch.float32, BLOCK, rels, dls.EB_REL_RANGE, RANK_CAP,
+                                precision=dls.PREC_FP32, rank_mode=rm)
+            ms, nb, stages, c, cs = _plan_run(p, field, args.steps)
+            modes[name] = {"value": in_bytes / (ms * 1e-3) / 1e9, "ms_per_step": ms, "ratio": in_bytes / nb,
+                           "n_accepted": c["n_accepted"], "n_searched": c["n_searched"], "phases_ms": stages}
+            if name == "learned":
+                comp = cs
+        rec = dls.decompress(comp)
+        rep = dls.verify(field, rec, comp)
+        del rec
+        # the oracle on sampled block ranges of every variable
+        cfg_all = oracle.Config(dims, BLOCK, oracle.F32, eb=rels, eb_type=oracle.EB_REL_RANGE, rank_cap=RANK_CAP,
+                                nvars=5)
+        nbv = oracle.num_blocks(cfg_all) // 5
+        fh = field.cpu().numpy()
+        s_g, h_g = replay.parse_stream(comp.cpu().numpy())
+        samp = []
+        for v in range(5):
+            for start in (0, nbv // 2, nbv - 64):
+                b0 = v * nbv + start
+                cfg = oracle.Config(dims, BLOCK, oracle.F32, eb=rels, eb_type=oracle.EB_REL_RANGE,
+                                    rank_cap=RANK_CAP, nvars=5, block_begin=b0, block_end=b0 + 64)
+                st, so, _ = oracle.compress(cfg, fh)
+                assert st == 0
+                s_o, h_o = replay.parse_stream(so)
+                samp.append((int(h_o["offsets"][-1]), int(h_g["offsets"][b0 + 64] - h_g["offsets"][b0])))
+        o_bytes = sum(a for a, _ in samp)
+        g_bytes = sum(b for _, b in samp)
+        line.update({
+            "value": modes["learned"]["value"], "ms_per_step": modes["learned"]["ms_per_step"],
+            "config": {"workload": "multivar 5 x 250x190x130 x 50 float32 (5.75 GiB), blocks up to 16^3x16 "
+                                   f"({oracle.num_blocks(cfg_all)}, mixed shapes), rel bounds {rels}, rank cap 16, "
+                                   "FP32 form, one captured plan"},
+            "ratio": in_bytes / comp.numel(), "max_err_over_bound": [rep["var_max_abs_err"][v] / rep["var_eb"][v]
+                                                                    for v in range(5)],
+            "n_over_bound": rep["n_over_bound"], "forms": modes,
+            "oracle_sample": {"blocks": 5 * 3 * 64, "oracle_record_bytes": o_bytes, "gpu_record_bytes": g_bytes,
+                              "ratio_gpu_over_oracle_bytes": g_bytes / o_bytes,
+                              "what": "64-block ranges at the start, middle and end of each variable"}})
+    else:
+        dims = (512, 512, 512, 32)
+        field = synth.modes3d(*dims, seed=5, count=64, device=dev)
+        eb = 1e-3 * float(field.max() - field.min())
+        in_bytes = field.numel() * 4
+        modes = {}
+        comp = None
+        for name, rm in (("learned", dls.RANK_LEARNED), ("tail", dls.RANK_TAIL), ("search", dls.RANK_SEARCH)):
+            p = dls.make_params(tuple(field.shape), torch.float32, BLOCK, eb, dls.EB_ABS, RANK_CAP,
+                                precision=dls.PREC_FP32, rank_mode=rm)
+            ms, nb, stages, c, cs = _plan_run(p, field, args.steps)
+            modes[name] = {"value": in_bytes / (ms * 1e-3) / 1e9, "ms_per_step": ms, "ratio": in_bytes / nb,
+                           "n_accepted": c["n_accepted"], "n_searched": c["n_searched"], "phases_ms": stages}
+            if name == "learned":
+                comp = cs
+            else:
+                del cs
+        rec = dls.decompress(comp)
+        err = float((rec - field).abs().max())
+        del rec
+        line.update({
+            "value": modes["learned"]["value"], "ms_per_step": modes["learned"]["ms_per_step"],
+            "config": {"workload": "modes3d 512^3 x 32 float32 (16 GiB), 64 modes |k|<=8, k^-5/3, N(0,1e-3^2) "
+                                   "noise, blocks 16^3x16 (65536), abs bound 1e-3 x range, rank cap 16, FP32 form, "
+                                   "learned rank with the search fallback"},
+            "ratio": in_bytes / comp.numel(), "max_err_over_eb": err / eb, "forms": modes})
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -374,6 +503,8 @@ def main():
                     help="absolute bound as a fraction of the value range (1e-2, 1e-3, 1e-4 in the at-scale config)")
     ap.add_argument("--sweep-precision", action="store_true",
                     help="every Gram precision mode at bounds 1e-2..1e-5 against the FP64 oracle (one JSON line)")
+    ap.add_argument("--config", type=int, default=2, choices=(2, 4, 5),
+                    help="4: five-variable uneven field; 5: 512^3 x 32 learned-rank evaluation (one JSON line each)")
     args = ap.parse_args()
     global DIMS, REL_BOUND
     if args.dims:
@@ -383,6 +514,8 @@ def main():
         return run_reference(args)
     if args.sweep_precision:
         return run_precision_sweep(args)
+    if args.config != 2:
+        return run_config(args)
 
     import numpy as np
     import torch

@@ -65,6 +65,8 @@ struct TileArgs {
   int bxb, yc, zc, bt;     // chunk box (x, y, z, t)
   int rc;                  // rows per chunk = bxb * yc * zc
   uint32_t mbx, myc;       // ceil(2^32 / bxb), ceil(2^32 / yc) (0 for a divisor of 1)
+  uint32_t mrc;            // ceil(2^32 / rc) (0 for rc = 1)
+  int cp_pairs;            // cp.async path: copy x-pairs of 8 bytes (even field and block widths)
   int tc_gram;             // Gram pass on the tensor cores (chunk box 16 x 16 x 1 x 16): a TcMode, 0 for none
   double jfloor;           // Jacobi skip floor as a fraction of the per-mode budget
   int64_t blo, bhi;        // the blocks [blo, bhi) of the plan this launch compresses
@@ -172,6 +174,10 @@ __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, u
 }
 __device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 8 : 0)
                : "memory");
 }
 __device__ __forceinline__ void cp_async_arrive(unsigned long long* b) {
@@ -302,15 +308,23 @@ __device__ void issue_chunk(const TileArgs& a, const Maps& tm, TileSmem& S, int6
                   g.v);
     }
   } else {
+    // element e of the tile is (t, r) = (e / rc, e % rc), r = (t2, x) with
+    // t2 = (zl, yl); divisions by multiply-high (the divisors are below 2^13)
     const Plan& P = a.P;
     const int tot = a.rc * a.bt;
-    for (int e = threadIdx.x; e < tot; e += kTT) {
-      const int t = e / a.rc, r = e - t * a.rc;
-      const int x = r % a.bxb, t2 = r / a.bxb;
-      const int64_t gx = g.x0 + x, gy = g.y0 + yb + t2 % a.yc, gz = g.z0 + zb + t2 / a.yc, gt = g.t0 + t;
+    const int64_t vbase = (int64_t)g.v * P.K;
+    const int step = a.cp_pairs ? 2 : 1;
+    for (int e = threadIdx.x * step; e < tot; e += kTT * step) {
+      const int t = fdiv(e, a.mrc), r = e - t * a.rc;
+      const int t2 = fdiv(r, a.mbx), x = r - t2 * a.bxb;
+      const int zl = fdiv(t2, a.myc), yl = t2 - zl * a.yc;
+      const int64_t gx = g.x0 + x, gy = g.y0 + yb + yl, gz = g.z0 + zb + zl, gt = g.t0 + t;
       const bool ok = gx < P.dims[0] && gy < P.dims[1] && gz < P.dims[2] && gt < P.dims[3];
-      const float* src = ok ? a.in + (int64_t)g.v * P.K + gt * P.P + (gz * P.dims[1] + gy) * P.dims[0] + gx : a.in;
-      cp_async4(&S.ring[stage][e], src, ok);
+      const float* src = ok ? a.in + vbase + gt * P.P + (gz * P.dims[1] + gy) * P.dims[0] + gx : a.in;
+      // pairs: x even and the field's x extent even, so x + 1 is in the field
+      // whenever x is, and both addresses are 8-byte aligned
+      if (a.cp_pairs) cp_async8(&S.ring[stage][e], src, ok);
+      else cp_async4(&S.ring[stage][e], src, ok);
     }
     cp_async_arrive(&S.full[stage]);
   }
@@ -2847,6 +2861,8 @@ int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, in
   auto magic = [](int d) -> uint32_t { return d <= 1 ? 0u : (uint32_t)((0x100000000ull + (uint64_t)d - 1) / (uint64_t)d); };
   a.mbx = magic(a.bxb);
   a.myc = magic(a.yc);
+  a.mrc = magic(a.rc);
+  a.cp_pairs = (p.dims[0] % 2 == 0) && (a.bxb % 2 == 0) && (((uintptr_t)d_in & 7) == 0);
   a.jfloor = 5e-2;
   CUtensorMap tmap;
   memset(&tmap, 0, sizeof(tmap));
