@@ -118,6 +118,18 @@ typedef struct {
    * it once, at dls_plan_create, into its workspace. */
   const double* basis;
   int32_t basis_n;
+  /* Statistics of the whole field, for a call that compresses one part of it
+   * (a rank's z-slab; Sec. 2.7.1 data distribution).  Null: the field passed
+   * is the whole field.  Otherwise a host array of nvars x 4 doubles, per
+   * variable {min, max, sum of squares, number of points} of the whole field
+   * (an all-reduce of the parts' own statistics): REL_RANGE takes the range,
+   * NRMSE the norm and the point count (Sec. 2.4 Eq. 4: eps and the points K
+   * of eps_l^2 = eps^2 N / K) from it instead of from the part, so that every
+   * part resolves the same bound and the parts' records are those of the
+   * whole field.  Points must be >= 1 and equal across variables, min <= max,
+   * the sum >= 0, all finite, the count integral (else DLS_ERR_INVALID_ARG).  Copied on each call
+   * (plans: once, at dls_plan_create). */
+  const double* global_stats;
 } dls_params;
 
 /* Worst-case stream size for these parameters (each record is at most the
@@ -137,6 +149,20 @@ size_t dls_workspace_size(const dls_params* p);
  * Synchronizes `stream` once to read the stream size. */
 int dls_compress(const dls_params* p, const void* d_in, void* d_out, size_t out_cap,
                  size_t* out_bytes, void* d_workspace, size_t ws_bytes, dls_stream_t stream);
+
+/* Statistics of the field d_in (one part of a larger field, or all of it),
+ * per variable {min, max, sum of squares, number of points} into h_stats
+ * (host, nvars x 4 doubles), by the statistics pass a compression runs for
+ * the relative and NRMSE bounds (Sec. 2.4): the sum of squares in the same
+ * fixed order, so a single part's result given back as p->global_stats
+ * resolves the bound the part resolves on its own.  A data-distributed
+ * field (Sec. 2.7.1: each rank a z-slab) combines its parts' results --
+ * min of mins, max of maxes, sums of the rest -- into the global_stats of
+ * every part's compression.  p->global_stats is ignored here.  d_workspace
+ * as for dls_compress.  DLS_ERR_NONFINITE if the part holds a NaN or an
+ * infinity.  Synchronizes `stream`. */
+int dls_field_stats(const dls_params* p, const void* d_in, double* h_stats, void* d_workspace, size_t ws_bytes,
+                    dls_stream_t stream);
 
 /* Reusable compression plan for fixed parameters and buffers (a time series
  * of snapshots written into the same buffers, for example).  Creation

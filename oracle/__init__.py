@@ -56,6 +56,7 @@ class Params(C.Structure):
         ("basis", C.POINTER(C.c_double)),
         ("basis_n", C.c_int32),
         ("corr_codec", C.c_int32),
+        ("global_stats", C.POINTER(C.c_double)),
     ]
 
 
@@ -149,7 +150,7 @@ class Config:
     bound type and rank cap."""
 
     def __init__(self, dims, block, dtype, eb, eb_type=EB_ABS, rank_cap=32, nvars=1,
-                 block_begin=0, block_end=-1, basis=None, corr_codec=0):
+                 block_begin=0, block_end=-1, basis=None, corr_codec=0, global_stats=None):
         self.dims = tuple(int(d) for d in dims)
         self.block = tuple(int(b) for b in block)
         self.dtype = int(dtype)
@@ -164,6 +165,10 @@ class Config:
         self.basis = None if basis is None else np.ascontiguousarray(basis, dtype=np.float64)
         if self.basis is not None and (self.basis.ndim != 2 or self.basis.shape[0] != self.basis.shape[1]):
             raise ValueError("basis must be a square matrix")
+        # whole-field statistics (nvars x 4: min, max, sum of squares, points)
+        # when the field passed is one part of it (Sec. 2.7.1 data distribution)
+        self.global_stats = (None if global_stats is None else
+                             np.ascontiguousarray(np.asarray(global_stats, dtype=np.float64).reshape(self.nvars, 4)))
 
     def c(self) -> Params:
         p = Params()
@@ -181,6 +186,8 @@ class Config:
             p.basis = _p(self.basis, C.c_double)
             p.basis_n = self.basis.shape[0]
         p.corr_codec = self.corr_codec
+        if self.global_stats is not None:
+            p.global_stats = _p(self.global_stats, C.c_double)
         return p
 
 

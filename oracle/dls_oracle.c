@@ -111,6 +111,18 @@ int or_validate(const or_params* p) {
         if (fabs(d - (i == j ? 1.0 : 0.0)) > 1e-12) return OR_ERR_INVALID_ARG;
       }
   }
+  if (p->global_stats) {
+    /* whole-field statistics: finite, min <= max, sum >= 0, one point count
+       (>= 1, integral) shared by every variable */
+    const double pts = p->global_stats[3];
+    for (int v = 0; v < p->nvars; ++v) {
+      const double* g = p->global_stats + 4 * v;
+      for (int i = 0; i < 4; ++i)
+        if (!isfinite(g[i])) return OR_ERR_INVALID_ARG;
+      if (!(g[0] <= g[1]) || g[2] < 0.0 || g[3] < 1.0 || g[3] != pts || g[3] != floor(g[3]))
+        return OR_ERR_INVALID_ARG;
+    }
+  }
   return OR_OK;
 }
 
@@ -132,9 +144,18 @@ int or_resolve(const or_params* p, const void* field, or_var* vars) {
       if (x > mx) mx = x;
       s2 = fma(x, x, s2);
     }
+    int64_t Kb = K;
+    if (p->global_stats) {
+      /* the whole field's statistics replace the part's own */
+      const double* g = p->global_stats + 4 * v;
+      mn = g[0];
+      mx = g[1];
+      s2 = g[2];
+      Kb = (int64_t)g[3];
+    }
     or_var* o = &vars[v];
     o->eb_user = p->eb[v];
-    o->K = K;
+    o->K = Kb;
     o->norm2 = s2;
     if (p->eb_type == OR_EB_ABS) {
       o->eb = p->eb[v];
@@ -145,7 +166,7 @@ int or_resolve(const or_params* p, const void* field, or_var* vars) {
       o->eb = p->eb[v] * sqrt(s2) / 100.0;
     }
     if (p->eb_type == OR_EB_NRMSE) {
-      o->delta = o->eb > 0.0 ? o->eb / sqrt((double)K) : 1.0;
+      o->delta = o->eb > 0.0 ? o->eb / sqrt((double)Kb) : 1.0;
       o->step = 0.0;
     } else {
       o->delta = o->eb;

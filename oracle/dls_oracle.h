@@ -61,6 +61,12 @@ typedef struct {
      writes); 1: a Rice-coded section too, wherever it is smaller (a proposed
      format, see or_pack_record). */
   int32_t corr_codec;
+  /* Statistics of the whole field when `field` is one part of it (a z-slab
+     of a data-distributed field, Sec. 2.7.1): nvars x 4 doubles, per variable
+     {min, max, sum of squares, number of points}.  Bound resolution takes the
+     range, the norm and K from here instead of from the part, so the part's
+     records are those of the whole field.  Null: the field is whole. */
+  const double* global_stats;
 } or_params;
 
 /* Geometry of one block. */

@@ -46,6 +46,17 @@ int make_plan(const dls_params* p, Plan* out) {
       }
     }
   }
+  if (p->global_stats) {
+    // statistics of the whole field, for a call on one part of it
+    const double pts = p->global_stats[3];
+    for (int v = 0; v < p->nvars; ++v) {
+      const double* g = p->global_stats + 4 * v;
+      for (int i = 0; i < 4; ++i)
+        if (!isfinite(g[i])) return DLS_ERR_INVALID_ARG;
+      if (!(g[0] <= g[1]) || !(g[2] >= 0.0) || !(g[3] >= 1.0) || g[3] != pts || g[3] != floor(g[3]))
+        return DLS_ERR_INVALID_ARG;
+    }
+  }
   Plan P;
   memset(&P, 0, sizeof(P));
   P.basis_n = p->basis ? p->basis_n : 0;
@@ -68,6 +79,8 @@ int make_plan(const dls_params* p, Plan* out) {
   P.nb = e - p->block_begin;
   P.P = p->dims[0] * p->dims[1] * p->dims[2];
   P.K = P.P * p->dims[3];
+  P.has_gstats = p->global_stats ? 1 : 0;
+  P.kbound = p->global_stats ? p->global_stats[3] : (double)P.K;
   P.nmax = (int32_t)(M < T ? M : T);
   P.lmax = (int32_t)(M < T ? T : M);
   P.nmax_full = P.nmax;
@@ -88,6 +101,7 @@ struct Layout {
   size_t meta, vst, q, kc, offsets, vars, status, partial, basis, total;
   // mixed-precision form
   size_t staging, q_scr, k8_scr, k32_scr, bit_scr, feat, ranks, phase, fast;
+  size_t gstats;        // nvars x 4 doubles when the caller gives the whole field's statistics
   int ctas;
   bool mixed;
 };
@@ -177,6 +191,7 @@ static Layout work_layout(const Plan& P) {
     L.ranks = take(sizeof(int32_t) * (size_t)nb1);
     L.phase = take(sizeof(unsigned long long) * (size_t)L.ctas * kMixedPhases);
     L.fast = take(tile_fast_bytes(P.nb));
+    L.gstats = P.has_gstats ? take(sizeof(double) * 4 * (size_t)P.nvars) : 0;
     L.total = off;
     return L;
   }
@@ -189,6 +204,7 @@ static Layout work_layout(const Plan& P) {
   L.status = take(sizeof(Status));
   L.partial = take(sizeof(double) * (size_t)stats_partial_doubles(P));
   L.basis = P.basis_n > 0 ? take(sizeof(double) * (size_t)P.basis_n * P.basis_n) : 0;
+  L.gstats = P.has_gstats ? take(sizeof(double) * 4 * (size_t)P.nvars) : 0;
   L.total = off;
   return L;
 }
@@ -204,12 +220,19 @@ static Work carve(const Layout& L, void* ws) {
   w.vars = (VarInfo*)(b + L.vars);
   w.status = (Status*)(b + L.status);
   w.basis = L.basis ? (const double*)(b + L.basis) : nullptr;
+  w.gstats = L.gstats ? (const double*)(b + L.gstats) : nullptr;
   return w;
 }
 
 // Copies the fixed basis (if any) into its workspace region, stream-ordered;
 // the host array may be freed once this returns.
 static int upload_basis(const dls_params* p, const Plan& P, const Layout& L, void* d_ws, cudaStream_t s) {
+  if (P.has_gstats) {
+    // the whole field's statistics (small; copied with the basis, before any kernel reads them)
+    if (cudaMemcpyAsync((uint8_t*)d_ws + L.gstats, p->global_stats, sizeof(double) * 4 * (size_t)P.nvars,
+                        cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return DLS_ERR_CUDA;
+  }
   if (P.basis_n == 0) return DLS_OK;
   const size_t bytes = sizeof(double) * (size_t)P.basis_n * P.basis_n;
   return cudaMemcpyAsync((uint8_t*)d_ws + L.basis, p->basis, bytes, cudaMemcpyHostToDevice, s) == cudaSuccess
@@ -580,6 +603,7 @@ int dls_compress_host(const dls_params* p, const void* h_in, void* h_out, size_t
   const Layout L = work_layout(P);
   if (host_pipelined(P, L)) {
     if (L.mixed && P.rank_mode == DLS_RANK_LEARNED && !rank_model_loaded()) return DLS_ERR_NO_MODEL;
+    if ((st = upload_basis(p, P, L, base + in + out, s)) != DLS_OK) return st;
     st = compress_host_pipelined(P, L, h_in, base, base + in, bound, base + in + out, s, &nb);
   } else {
     CK(cudaMemcpyAsync(base, h_in, inb, cudaMemcpyHostToDevice, s));
@@ -614,6 +638,25 @@ int dls_decompress(const void* d_comp, size_t comp_bytes, void* d_out, size_t ou
   return hs.corrupt ? DLS_ERR_CORRUPT : DLS_OK;
 }
 
+int dls_field_stats(const dls_params* p, const void* d_in, double* h_stats, void* d_workspace, size_t ws_bytes,
+                    dls_stream_t stream) {
+  Plan P;
+  int st = make_plan(p, &P);
+  if (st != DLS_OK) return st;
+  if (!d_in || !h_stats || ((uintptr_t)d_in & (esize(P.dtype) - 1))) return DLS_ERR_INVALID_ARG;
+  const Layout L = work_layout(P);
+  if (!d_workspace || ws_bytes < L.total || ((uintptr_t)d_workspace & 255)) return DLS_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  Work w = carve(L, d_workspace);
+  CK(cudaMemsetAsync(w.status, 0, sizeof(Status), s));
+  if ((st = launch_field_stats(P, d_in, w, (double*)((uint8_t*)d_workspace + L.partial), h_stats, s)) != DLS_OK)
+    return st;
+  Status hs;
+  CK(cudaMemcpyAsync(&hs, w.status, sizeof(Status), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return hs.nonfinite ? DLS_ERR_NONFINITE : DLS_OK;
+}
+
 int dls_block_features(const dls_params* p, const void* d_in, float* d_feat, int32_t* d_rank, void* d_workspace,
                        size_t ws_bytes, dls_stream_t stream) {
   Plan P;
@@ -625,6 +668,7 @@ int dls_block_features(const dls_params* p, const void* d_in, float* d_feat, int
   cudaStream_t s = (cudaStream_t)stream;
   Work w = carve(L, d_workspace);
   uint8_t* b = (uint8_t*)d_workspace;
+  if ((st = upload_basis(p, P, L, d_workspace, s)) != DLS_OK) return st;
   CK(cudaMemsetAsync(w.status, 0, sizeof(Status), s));
   if ((st = launch_stats_resolve(P, d_in, w, (double*)(b + L.partial), s)) != DLS_OK) return st;
   // the workspace as a compression uses it, with the caller's feature and rank arrays
@@ -750,7 +794,7 @@ int dls_plan_create(const dls_params* p, const void* d_in, void* d_out, size_t o
   if (cudaHostAlloc((void**)&pl->h_status, sizeof(Status), cudaHostAllocDefault) != cudaSuccess) return fail(DLS_ERR_CUDA);
   // the fixed basis goes into the workspace once, outside the captured graph
   if ((st = upload_basis(p, P, L, d_workspace, s)) != DLS_OK) return fail(st);
-  if (P.basis_n > 0 && cudaStreamSynchronize(s) != cudaSuccess) return fail(DLS_ERR_CUDA);
+  if ((P.basis_n > 0 || P.has_gstats) && cudaStreamSynchronize(s) != cudaSuccess) return fail(DLS_ERR_CUDA);
   // autotune: time each occupancy variant of the per-block kernel on the real work
   if (L.mixed) {
     const std::string key = tune_key(P);

@@ -47,6 +47,8 @@ struct Plan {
   int64_t offsets_pos, payload_pos;   // byte positions in the stream
   int64_t pt_base, pt_count;          // point range of the processed blocks (workspace indexing)
   int32_t basis_n;                    // Gram order of the fixed basis (0: none)
+  int32_t has_gstats;                 // bound statistics given by the caller (a part of a field)
+  double kbound;                      // points per variable the bound refers to (K, or the whole field's)
   double eb_user[kMaxVars];
 };
 
@@ -135,6 +137,7 @@ struct Work {
   VarInfo* vars;        // nvars
   Status* status;
   const double* basis;  // basis_n x basis_n fixed modes (null: none)
+  const double* gstats; // nvars x 4 statistics of the whole field (null: from the field passed)
 };
 
 // ordered key for doubles (monotone map to unsigned)
@@ -270,6 +273,8 @@ int launch_plain_compress(const Plan& p, const void* d_in, const Work& w, cudaSt
 int launch_scan(const Plan& p, const Work& w, size_t out_cap, void* d_out, cudaStream_t s);
 int launch_pack(const Plan& p, const void* d_in, const Work& w, void* d_out, size_t out_cap, cudaStream_t s);
 int launch_stats_resolve(const Plan& p, const void* d_in, const Work& w, double* partial, cudaStream_t s);
+int launch_field_stats(const Plan& p, const void* d_in, const Work& w, double* partial, double* h_stats,
+                       cudaStream_t s);
 int stats_partial_doubles(const Plan& p);
 int launch_decode(const Plan& p, const void* d_comp, unsigned long long comp_bytes, void* d_out, Status* st,
                   cudaStream_t s);

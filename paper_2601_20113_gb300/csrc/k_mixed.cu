@@ -817,7 +817,7 @@ __device__ __forceinline__ void mixed_body(const MxArgs& a) {
     cc.inv_step_f = pointwise ? __double2float_rn(1.0 / vi.step) : 0.0f;
     cc.eb_lo_f = __double2float_rd(vi.eb * (1.0 - 1e-6));
     cc.eb_hi_f = __double2float_ru(vi.eb * (1.0 + 1e-6));
-    const double el2 = (P.eb_type == DLS_EB_NRMSE) ? (vi.eb * vi.eb) * ((double)g.N / (double)P.K)
+    const double el2 = (P.eb_type == DLS_EB_NRMSE) ? (vi.eb * vi.eb) * ((double)g.N / P.kbound)
                                                    : (vi.eb * vi.eb) * (double)g.N;
     if (tid == 0) { S.nonfinite = 0; S.ovf = 0; }
     prepare_block(a, S, g);

@@ -237,6 +237,13 @@ __global__ void __launch_bounds__(256) k_stats(Plan P, const T* __restrict__ in,
   }
 }
 
+// A variable's sum of squares: the CTAs' partial sums added in CTA order.
+__device__ double stats_sumsq(const double* partial, int v) {
+  double s2 = 0.0;
+  for (int c = 0; c < kStatCtas; ++c) s2 = __dadd_rn(s2, partial[(int64_t)v * kStatCtas + c]);
+  return s2;
+}
+
 __global__ void k_resolve(Plan P, Work W, const double* partial, int have_stats) {
   const int v = threadIdx.x + blockIdx.x * blockDim.x;
   if (v >= P.nvars) return;
@@ -244,24 +251,44 @@ __global__ void k_resolve(Plan P, Work W, const double* partial, int have_stats)
   const double ebu = P.eb_user[v];
   o.eb_user = ebu;
   double s2 = 0.0;
-  if (have_stats)
-    for (int c = 0; c < kStatCtas; ++c) s2 = __dadd_rn(s2, partial[(int64_t)v * kStatCtas + c]);
+  double vmin = 0.0, vmax = 0.0;
+  if (W.gstats) {
+    // the whole field's statistics, given by the caller of a part of it
+    vmin = W.gstats[4 * v + 0];
+    vmax = W.gstats[4 * v + 1];
+    s2 = W.gstats[4 * v + 2];
+  } else if (have_stats) {
+    s2 = stats_sumsq(partial, v);
+    vmin = dunkey(o.minkey);
+    vmax = dunkey(o.maxkey);
+  }
   o.sumsq = s2;
   if (P.eb_type == DLS_EB_ABS) {
     o.eb = ebu;
   } else if (P.eb_type == DLS_EB_REL_RANGE) {
-    const double range = __dsub_rn(dunkey(o.maxkey), dunkey(o.minkey));
+    const double range = __dsub_rn(vmax, vmin);
     o.eb = range > 0.0 ? __dmul_rn(ebu, range) : ebu;
   } else {
     o.eb = __ddiv_rn(__dmul_rn(ebu, __dsqrt_rn(s2)), 100.0);
   }
   if (P.eb_type == DLS_EB_NRMSE) {
-    o.delta = o.eb > 0.0 ? __ddiv_rn(o.eb, __dsqrt_rn((double)P.K)) : 1.0;
+    o.delta = o.eb > 0.0 ? __ddiv_rn(o.eb, __dsqrt_rn(P.kbound)) : 1.0;
     o.step = 0.0;
   } else {
     o.delta = o.eb;
     o.step = __dmul_rn(2.0, o.eb);
   }
+}
+
+// The part's own statistics, per variable {min, max, sum of squares, points}.
+__global__ void k_stats_export(Plan P, Work W, const double* partial, double* out) {
+  const int v = threadIdx.x;
+  if (v >= P.nvars) return;
+  const VarInfo& o = W.vars[v];
+  out[4 * v + 0] = dunkey(o.minkey);
+  out[4 * v + 1] = dunkey(o.maxkey);
+  out[4 * v + 2] = stats_sumsq(partial, v);
+  out[4 * v + 3] = (double)P.K;
 }
 
 __global__ void k_init_vars(Plan P, Work W) {
@@ -289,7 +316,7 @@ int launch_pack(const Plan& p, const void* d_in, const Work& w, void* d_out, siz
 // Statistics pass (only REL_RANGE / NRMSE need it) followed by resolution.
 // `partial` scratch: nvars * kStatCtas doubles, carved from the workspace by the caller.
 int launch_stats_resolve(const Plan& p, const void* d_in, const Work& w, double* partial, cudaStream_t s) {
-  const bool need = p.eb_type != DLS_EB_ABS;
+  const bool need = p.eb_type != DLS_EB_ABS && !w.gstats;
   if (need) {
     k_init_vars<<<1, 64, 0, s>>>(p, w);
     dim3 grid(kStatCtas, p.nvars);
@@ -300,6 +327,24 @@ int launch_stats_resolve(const Plan& p, const void* d_in, const Work& w, double*
   return cudaGetLastError() == cudaSuccess ? DLS_OK : DLS_ERR_CUDA;
 }
 
-int stats_partial_doubles(const Plan& p) { return p.nvars * kStatCtas; }
+// The statistics pass alone, its result (nvars x 4 doubles, written to the
+// last 4 * nvars doubles of `partial`) copied to h_stats on `s`.
+int launch_field_stats(const Plan& p, const void* d_in, const Work& w, double* partial, double* h_stats,
+                       cudaStream_t s) {
+  double* d_stats = partial + (int64_t)p.nvars * kStatCtas;
+  k_init_vars<<<1, 64, 0, s>>>(p, w);
+  dim3 grid(kStatCtas, p.nvars);
+  if (p.dtype == DLS_F32) k_stats<float><<<grid, 256, 0, s>>>(p, (const float*)d_in, w, partial);
+  else k_stats<double><<<grid, 256, 0, s>>>(p, (const double*)d_in, w, partial);
+  k_stats_export<<<1, 64, 0, s>>>(p, w, partial, d_stats);
+  if (cudaGetLastError() != cudaSuccess) return DLS_ERR_CUDA;
+  return cudaMemcpyAsync(h_stats, d_stats, sizeof(double) * 4 * (size_t)p.nvars, cudaMemcpyDeviceToHost, s) ==
+                 cudaSuccess
+             ? DLS_OK
+             : DLS_ERR_CUDA;
+}
+
+// CTA partial sums of squares, then the field_stats output (4 per variable).
+int stats_partial_doubles(const Plan& p) { return p.nvars * kStatCtas + 4 * p.nvars; }
 
 }  // namespace dls

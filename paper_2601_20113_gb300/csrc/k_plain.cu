@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(kThreads) k_plain(Plan P, const T* __restrict_
 
   // ---- 4. rank: bisection on pass(r) <=> E(r) <= eps_l^2
   const double el2 = (P.eb_type == DLS_EB_NRMSE)
-                         ? dmul(dmul(vi.eb, vi.eb), ddiv((double)N, (double)P.K))
+                         ? dmul(dmul(vi.eb, vi.eb), ddiv((double)N, P.kbound))
                          : dmul(dmul(vi.eb, vi.eb), (double)N);
   int r = 0, nprobes = 0;
   bool raw = overflow;

@@ -2001,7 +2001,7 @@ __device__ void var_consts(TileSmem& S, const Geom& g, const VarInfo& vi, bool p
 }
 
 __device__ __forceinline__ double local_tol2(const Plan& P, const VarInfo& vi, const Geom& g) {
-  return (P.eb_type == DLS_EB_NRMSE) ? (vi.eb * vi.eb) * ((double)g.N / (double)P.K) : (vi.eb * vi.eb) * (double)g.N;
+  return (P.eb_type == DLS_EB_NRMSE) ? (vi.eb * vi.eb) * ((double)g.N / P.kbound) : (vi.eb * vi.eb) * (double)g.N;
 }
 
 // Jacobi skip floor: rotations below 5% of the per-mode budget eb^2 L change

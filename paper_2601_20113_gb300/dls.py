@@ -47,6 +47,7 @@ class Params(C.Structure):
         ("block_end", C.c_int64),
         ("basis", C.POINTER(C.c_double)),
         ("basis_n", C.c_int32),
+        ("global_stats", C.POINTER(C.c_double)),
     ]
 
 
@@ -94,6 +95,8 @@ _SIGS = {
     "dls_set_rank_model": (C.c_int, [C.c_void_p, C.c_size_t]),
     "dls_block_features": (C.c_int, [C.POINTER(Params), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
                                      C.c_void_p]),
+    "dls_field_stats": (C.c_int, [C.POINTER(Params), C.c_void_p, C.POINTER(C.c_double), C.c_void_p, C.c_size_t,
+                                  C.c_void_p]),
     "dls_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "dls_mlp_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dls_mlp_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
@@ -148,9 +151,12 @@ def _dtype_code(t: torch.dtype) -> int:
 
 
 def make_params(shape, dtype, block, eb, eb_type=EB_ABS, rank_cap=32, precision=PREC_FP64,
-                rank_mode=RANK_SEARCH, block_begin=0, block_end=-1, basis=None):
+                rank_mode=RANK_SEARCH, block_begin=0, block_end=-1, basis=None, global_stats=None):
     """shape = (nvars, nt, nz, ny, nx) of the field tensor; basis: optional
-    n x n orthonormal modes (column k = mode k) for the blocks of Gram order n."""
+    n x n orthonormal modes (column k = mode k) for the blocks of Gram order n;
+    global_stats: optional nvars x 4 (min, max, sum of squares, point count) of
+    the whole field when the tensor is one part of it (a z-slab): the relative
+    bounds and the NRMSE tolerance then come from the whole field."""
     nvars, nt, nz, ny, nx = shape
     p = Params()
     p.nvars = nvars
@@ -177,6 +183,13 @@ def make_params(shape, dtype, block, eb, eb_type=EB_ABS, rank_cap=32, precision=
         p.basis = b.ctypes.data_as(C.POINTER(C.c_double))
         p.basis_n = b.shape[0]
         p._basis_keep = b
+    if global_stats is not None:
+        import numpy as np
+        g = np.ascontiguousarray(np.asarray(global_stats, dtype=np.float64))
+        if g.shape != (nvars, 4):
+            raise ValueError("global_stats must be nvars x 4")
+        p.global_stats = g.ctypes.data_as(C.POINTER(C.c_double))
+        p._gstats_keep = g
     return p
 
 
@@ -333,6 +346,20 @@ def set_rank_model(params) -> None:
     st = lib().dls_set_rank_model(arr.ctypes.data_as(C.c_void_p), arr.size)
     if st != OK:
         raise DlsError(st, "dls_set_rank_model")
+
+
+def field_stats(p: Params, field: torch.Tensor, workspace: torch.Tensor | None = None):
+    """Per-variable (min, max, sum of squares, points) of a CUDA field as an
+    nvars x 4 float64 numpy array (the library's statistics pass)."""
+    import numpy as np
+    ws = workspace if workspace is not None else torch.empty(workspace_size(p), dtype=torch.uint8,
+                                                             device=field.device)
+    out = np.zeros((p.nvars, 4), dtype=np.float64)
+    st = lib().dls_field_stats(C.byref(p), _ptr(field), out.ctypes.data_as(C.POINTER(C.c_double)), _ptr(ws),
+                               ws.numel(), _stream(None))
+    if st != OK:
+        raise DlsError(st, "dls_field_stats")
+    return out
 
 
 def block_features(field: torch.Tensor, block, eb, eb_type=EB_ABS, rank_cap=16):
