@@ -654,10 +654,14 @@ def main():
         # the same field through the other rank modes of the FP32 form, each
         # with its own captured plan: what the network buys over the search
         # and over the eigenvalue-tail heuristic it is fed
+        # (and, last, the learned form with the Rice-coded correction sections:
+        # what the lossless stage costs and gains)
         line["forms"] = {}
-        for fname in ("fp32", "tail", "learned") if have_model else ("fp32", "tail"):
+        names = ("fp32", "tail", "learned") if have_model else ("fp32", "tail")
+        for fname in names + (names[-1] + "_rice",):
+            base, codec = (fname[:-5], 1) if fname.endswith("_rice") else (fname, 0)
             fp = dls.make_params(tuple(field.shape), torch.float32, BLOCK, eb, dls.EB_ABS, RANK_CAP,
-                                 precision=FORMS[fname][0], rank_mode=FORMS[fname][1])
+                                 precision=FORMS[base][0], rank_mode=FORMS[base][1], corr_codec=codec)
             fws = torch.empty(dls.workspace_size(fp), dtype=torch.uint8, device=dev)
             fplan = dls.CompressPlan(fp, field, out, fws, stream)
             for _ in range(2):

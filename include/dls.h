@@ -130,6 +130,16 @@ typedef struct {
    * the sum >= 0, all finite, the count integral (else DLS_ERR_INVALID_ARG).  Copied on each call
    * (plans: once, at dls_plan_create). */
   const double* global_stats;
+  /* Correction section codec (the lossless stage after the lossy map, Sec.
+   * 2.5 and Algorithm 1 step 3; undone first in Sec. 2.6).  0: dense or
+   * entry-list corrections only.  1: also the Rice-coded form (record flag 8)
+   * wherever it is strictly smaller: the corrections in chunks of 1024
+   * elements, each nonzero as the Rice code (parameter kr in [0, 20], the
+   * fewest bits) of the zeros before it and zigzag(k) - 1 in wv bits, one more
+   * code for the zeros to the chunk end; the section holds the word count,
+   * kr | wv << 8, the chunks' bit offsets and the coded words.  Other values:
+   * DLS_ERR_INVALID_ARG.  The decoder reads both. */
+  int32_t corr_codec;
 } dls_params;
 
 /* Worst-case stream size for these parameters (each record is at most the

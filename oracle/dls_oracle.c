@@ -1194,7 +1194,9 @@ int or_parse_record(const uint8_t* rec, int64_t nbytes, int side, int n, int64_t
     for (int64_t e = 0; e < N; ++e) escval[e] = get_val(rec + 16 + e * es, dtype);
     return OR_OK;
   }
-  if ((flags & ~(OR_FLAG_SPATIAL | OR_FLAG_DENSE)) != 0) return OR_ERR_CORRUPT;   /* no Rice here */
+  if ((flags & ~(OR_FLAG_SPATIAL | OR_FLAG_DENSE | OR_FLAG_RICE)) != 0) return OR_ERR_CORRUPT;
+  const int rice = (flags & OR_FLAG_RICE) ? 1 : 0;
+  if (rice && (wk == 0 || (flags & OR_FLAG_DENSE))) return OR_ERR_CORRUPT;
   if (r > n || wk > 32 || ib != nbits((uint32_t)(N - 1)) || ncorr > N || nesc > N) return OR_ERR_CORRUPT;
   const uint8_t* wq = rec + 16;
   const int64_t off_v = 16 + al(r, 8);
@@ -1205,8 +1207,16 @@ int or_parse_record(const uint8_t* rec, int64_t nbytes, int side, int n, int64_t
     qwords += (L * wq[c] + 31) / 32;
   }
   const int dense = (flags & OR_FLAG_DENSE) ? 1 : 0;
-  const int64_t corr_w = wk == 0 ? 0 : (dense ? (N * wk + 31) / 32 : (ncorr * (ib + wk) + 31) / 32);
   const int64_t off_c = off_q + al(qwords * 4, 8);
+  const int64_t nchunks = (N + OR_RICE_CHUNK - 1) / OR_RICE_CHUNK;
+  int64_t rice_words = 0;
+  if (rice) {
+    if (off_c + 8 > nbytes) return OR_ERR_CORRUPT;
+    rice_words = rd32(rec + off_c);
+  }
+  const int64_t corr_w = wk == 0 ? 0
+                         : rice ? 2 + nchunks + rice_words
+                                : (dense ? (N * wk + 31) / 32 : (ncorr * (ib + wk) + 31) / 32);
   const int64_t off_ei = off_c + al(corr_w * 4, 8);
   const int64_t off_ev = off_ei + al(nesc * 4, 8);
   if (al(off_ev + al(nesc * es, 8), 16) != nbytes) return OR_ERR_CORRUPT;
@@ -1222,7 +1232,22 @@ int or_parse_record(const uint8_t* rec, int64_t nbytes, int side, int n, int64_t
     wbase += (L * wq[c] + 31) / 32;
   }
   const uint32_t* cw = (const uint32_t*)(rec + off_c);
-  if (wk > 0 && dense) {
+  if (rice) {
+    /* the Rice section: its decoder, then the counts the header claims */
+    const int kr = (int)(cw[1] & 0xFFu), wv = (int)((cw[1] >> 8) & 0xFFu);
+    if ((cw[1] >> 16) != 0 || kr > 20 || wv > 32) return OR_ERR_CORRUPT;
+    if (or_rice_decode(cw + 2 + nchunks, rice_words, cw + 2, N, OR_RICE_CHUNK, kr, wv, k) != 0)
+      return OR_ERR_CORRUPT;
+    int64_t nz = 0;
+    uint32_t kmx = 0;
+    for (int64_t e = 0; e < N; ++e)
+      if (k[e] != 0) {
+        ++nz;
+        const uint32_t z = ((uint32_t)k[e] << 1) ^ (uint32_t)(k[e] >> 31);
+        if (z > kmx) kmx = z;
+      }
+    if (nz != ncorr || nbits(kmx) != wk) return OR_ERR_CORRUPT;
+  } else if (wk > 0 && dense) {
     for (int64_t e = 0; e < N; ++e) {
       const uint32_t z = get_bits(cw, (uint64_t)e * wk, wk);
       k[e] = (int32_t)((z >> 1) ^ (0u - (z & 1u)));

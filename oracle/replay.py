@@ -23,7 +23,8 @@ definition the oracle evaluates exactly:
   3. reconstruction (Sec. 2.6, Algorithm 2): the decode contract in binary32;
   4. pointwise corrections and escapes: equal, element for element;
   5. the record (Sec. 2.7.2 layout): the oracle's packer given (r, V^st, q, k,
-     escapes, the block's raw values) must write the same bytes.
+     escapes, the block's raw values) and the configuration's correction codec
+     (Rice-coded sections where smaller, when asked) must write the same bytes.
 
 The stored modes themselves are checked against the oracle's FP64 eigenproblem
 of the same block: orthonormal to binary32 rounding, and their Rayleigh
@@ -149,7 +150,7 @@ def replay_block(cfg: Config, field, b: int, rec, eb: float, delta: float, step:
     out["dense"] = bool(p["flags"] & 4)
     out["sparse"] = (not out["dense"]) and bool(np.any(p["k"] != 0))
     # 5. the record, repacked by the oracle
-    rec_o = pack_record(r, g.side, n, L, M, cfg.dtype, Vst, q, k, esc, A)
+    rec_o = pack_record(r, g.side, n, L, M, cfg.dtype, Vst, q, k, esc, A, cfg.corr_codec)
     if rec_o != bytes(rec):
         out["errors"].append("record bytes differ from the oracle packer's")
     # the stored modes against the oracle's eigenproblem

@@ -21,6 +21,7 @@ int make_plan(const dls_params* p, Plan* out) {
   if (p->dtype != DLS_F32 && p->dtype != DLS_F64) return DLS_ERR_INVALID_ARG;
   if (p->eb_type < 0 || p->eb_type > 2 || p->rank_cap < 0) return DLS_ERR_INVALID_ARG;
   if (p->precision < 0 || p->precision > 5 || p->rank_mode < 0 || p->rank_mode > 2) return DLS_ERR_INVALID_ARG;
+  if (p->corr_codec != 0 && p->corr_codec != 1) return DLS_ERR_INVALID_ARG;
   for (int a = 0; a < 4; ++a)
     if (p->dims[a] < 1 || p->block[a] < 1 || p->block[a] > p->dims[a]) return DLS_ERR_INVALID_ARG;
   const int64_t M = (int64_t)p->block[0] * p->block[1] * p->block[2];
@@ -80,6 +81,7 @@ int make_plan(const dls_params* p, Plan* out) {
   P.P = p->dims[0] * p->dims[1] * p->dims[2];
   P.K = P.P * p->dims[3];
   P.has_gstats = p->global_stats ? 1 : 0;
+  P.corr_codec = p->corr_codec;
   P.kbound = p->global_stats ? p->global_stats[3] : (double)P.K;
   P.nmax = (int32_t)(M < T ? M : T);
   P.lmax = (int32_t)(M < T ? T : M);
@@ -102,6 +104,8 @@ struct Layout {
   // mixed-precision form
   size_t staging, q_scr, k8_scr, k32_scr, bit_scr, feat, ranks, phase, fast;
   size_t gstats;        // nvars x 4 doubles when the caller gives the whole field's statistics
+  size_t rice_tmp, rice_info, rice_chunks;   // Rice stage: the packers' stream (bound bytes), per-block
+                                             // choices, per-chunk run counts
   int ctas;
   bool mixed;
 };
@@ -163,6 +167,8 @@ static int launch_mixed_all(const Plan& P, const void* d_in, const MixedWork& mw
   return DLS_OK;
 }
 
+static int64_t bound_bytes(const Plan& P);
+
 static Layout work_layout(const Plan& P) {
   Layout L;
   memset(&L, 0, sizeof(L));
@@ -171,6 +177,12 @@ static Layout work_layout(const Plan& P) {
     size_t o = off;
     off = (size_t)align_up((int64_t)(off + bytes), 256);
     return o;
+  };
+  auto take_rice = [&](Layout& l) {
+    if (!P.corr_codec) return;
+    l.rice_tmp = take((size_t)bound_bytes(P));
+    l.rice_info = take(sizeof(RiceInfo) * (size_t)(P.nb > 0 ? P.nb : 1));
+    l.rice_chunks = take(sizeof(RiceChunk) * (size_t)(P.nb > 0 ? P.nb : 1) * (size_t)rice_chunks_per_block(P));
   };
   if (use_mixed(P)) {
     const int64_t nb1 = P.nb > 0 ? P.nb : 1;
@@ -192,6 +204,7 @@ static Layout work_layout(const Plan& P) {
     L.phase = take(sizeof(unsigned long long) * (size_t)L.ctas * kMixedPhases);
     L.fast = take(tile_fast_bytes(P.nb));
     L.gstats = P.has_gstats ? take(sizeof(double) * 4 * (size_t)P.nvars) : 0;
+    take_rice(L);
     L.total = off;
     return L;
   }
@@ -205,6 +218,7 @@ static Layout work_layout(const Plan& P) {
   L.partial = take(sizeof(double) * (size_t)stats_partial_doubles(P));
   L.basis = P.basis_n > 0 ? take(sizeof(double) * (size_t)P.basis_n * P.basis_n) : 0;
   L.gstats = P.has_gstats ? take(sizeof(double) * 4 * (size_t)P.nvars) : 0;
+  take_rice(L);
   L.total = off;
   return L;
 }
@@ -353,6 +367,10 @@ static int enqueue_compress(const Plan& P, const Layout& L, const void* d_in, vo
   int st;
   Work w = carve(L, d_ws);
   CK(cudaMemsetAsync(w.status, 0, sizeof(Status), s));
+  // with the Rice stage the packers write into its staging stream, which the
+  // stage then rewrites into d_out
+  void* out1 = P.corr_codec ? (void*)((uint8_t*)d_ws + L.rice_tmp) : d_out;
+  const size_t cap1 = P.corr_codec ? (size_t)bound_bytes(P) : out_cap;
   double* partial = (double*)((uint8_t*)d_ws + L.partial);
   if ((st = launch_stats_resolve(P, d_in, w, partial, s)) != DLS_OK) return st;
   if (L.mixed) {
@@ -362,17 +380,21 @@ static int enqueue_compress(const Plan& P, const Layout& L, const void* d_in, vo
     if (ev0) CK(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
     if ((st = launch_mixed_all(P, d_in, mw, mode, variant, s, pev)) != DLS_OK) return st;
     if (ev1) CK(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
-    if ((st = launch_scan(P, w, out_cap, d_out, s)) != DLS_OK) return st;
-    if ((st = launch_compact(P, mw, d_out, s)) != DLS_OK) return st;
-    if ((st = launch_pack_tile(P, mw, d_in, d_out, s)) != DLS_OK) return st;
-    if (pev && pev[4]) CK(cudaEventRecordWithFlags(pev[4], s, cudaEventRecordExternal));
+    if ((st = launch_scan(P, w, cap1, out1, s)) != DLS_OK) return st;
+    if ((st = launch_compact(P, mw, out1, s)) != DLS_OK) return st;
+    if ((st = launch_pack_tile(P, mw, d_in, out1, s)) != DLS_OK) return st;
   } else {
     if (ev0) CK(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
     if ((st = launch_plain_compress(P, d_in, w, s)) != DLS_OK) return st;
     if (ev1) CK(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
-    if ((st = launch_scan(P, w, out_cap, d_out, s)) != DLS_OK) return st;
-    if ((st = launch_pack(P, d_in, w, d_out, out_cap, s)) != DLS_OK) return st;
+    if ((st = launch_scan(P, w, cap1, out1, s)) != DLS_OK) return st;
+    if ((st = launch_pack(P, d_in, w, out1, cap1, s)) != DLS_OK) return st;
   }
+  if (P.corr_codec &&
+      (st = launch_rice(P, w, (const uint8_t*)out1, (RiceInfo*)((uint8_t*)d_ws + L.rice_info),
+                        (RiceChunk*)((uint8_t*)d_ws + L.rice_chunks), out_cap, d_out, s)) != DLS_OK)
+    return st;
+  if (L.mixed && pev && pev[4]) CK(cudaEventRecordWithFlags(pev[4], s, cudaEventRecordExternal));
   return DLS_OK;
 }
 
@@ -428,9 +450,13 @@ static int compress_host_pipelined(const Plan& P, const Layout& L, const void* h
       return done(DLS_ERR_CUDA);
     if ((st = launch_tile_compress(P, d_in, mw, mode, 2, s, k * nbs, (k + 1) * nbs)) != DLS_OK) return done(st);
   }
-  if ((st = launch_scan(P, w, bound, d_out, s)) != DLS_OK) return done(st);
-  if ((st = launch_compact(P, mw, d_out, s)) != DLS_OK) return done(st);
-  if ((st = launch_pack_tile(P, mw, d_in, d_out, s)) != DLS_OK) return done(st);
+  uint8_t* out1 = P.corr_codec ? d_ws + L.rice_tmp : d_out;
+  if ((st = launch_scan(P, w, bound, out1, s)) != DLS_OK) return done(st);
+  if ((st = launch_compact(P, mw, out1, s)) != DLS_OK) return done(st);
+  if ((st = launch_pack_tile(P, mw, d_in, out1, s)) != DLS_OK) return done(st);
+  if (P.corr_codec && (st = launch_rice(P, w, out1, (RiceInfo*)(d_ws + L.rice_info),
+                                        (RiceChunk*)(d_ws + L.rice_chunks), bound, d_out, s)) != DLS_OK)
+    return done(st);
   Status hs;
   if (cudaMemcpyAsync(&hs, w.status, sizeof(Status), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)

@@ -19,6 +19,10 @@ constexpr uint32_t kVersion = 1u;
 constexpr int kHdr = 128;
 constexpr int kVarRec = 32;
 constexpr uint32_t kFlagRaw = 1u, kFlagSpatial = 2u, kFlagDense = 4u;
+// Rice-coded correction section (the lossless stage, corr_codec = 1): see k_rice.cu.
+constexpr uint32_t kFlagRice = 8u;
+constexpr int kRiceChunk = 1024;           // elements per independently decodable chunk
+constexpr int kRiceMaxKr = 20;             // Rice parameters tried: 0..20
 // Block metadata only (never in a record): the record waits in its staging
 // slot for the deferred packer, which writes it at its stream offset.
 constexpr uint32_t kFlagDeferred = 1u << 8;
@@ -48,6 +52,7 @@ struct Plan {
   int64_t pt_base, pt_count;          // point range of the processed blocks (workspace indexing)
   int32_t basis_n;                    // Gram order of the fixed basis (0: none)
   int32_t has_gstats;                 // bound statistics given by the caller (a part of a field)
+  int32_t corr_codec;                 // 1: Rice-coded correction sections where smaller
   double kbound;                      // points per variable the bound refers to (K, or the whole field's)
   double eb_user[kMaxVars];
 };
@@ -140,6 +145,23 @@ struct Work {
   const double* gstats; // nvars x 4 statistics of the whole field (null: from the field passed)
 };
 
+// Per block, the Rice stage's choice: on, parameter kr, value width wv and
+// the coded words (the section is 2 + chunks + words words).
+struct RiceInfo {
+  uint32_t words;
+  int32_t kr, wv, on;
+};
+// Per chunk of a record's corrections: c[i] = runs of zeros with bit i set,
+// and the nonzeros, so that the chunk's code length is known for every kr.
+struct RiceChunk {
+  uint16_t c[11];
+  uint16_t nnz;
+  uint32_t first;   // entry-list sources: the chunk's first entry
+};
+__host__ __device__ inline int64_t rice_chunks_per_block(const Plan& p) {
+  return cdiv((int64_t)p.block[0] * p.block[1] * p.block[2] * p.block[3], kRiceChunk);
+}
+
 // ordered key for doubles (monotone map to unsigned)
 __host__ __device__ inline unsigned long long dbits(double x) {
 #ifdef __CUDA_ARCH__
@@ -204,6 +226,16 @@ __host__ __device__ inline RecLayout rec_layout(int r, int n, int64_t L, int64_t
   return o;
 }
 __host__ __device__ inline int64_t raw_record_bytes(int64_t N, int es) { return align_up(16 + N * es, 16); }
+// The layout of the same record with a Rice-coded correction section of
+// `rice_words` coded words: [count, kr | wv << 8, chunk bit offsets, words].
+__host__ __device__ inline RecLayout rice_layout(RecLayout o, int64_t N, int64_t rice_words, int64_t nesc, int es) {
+  o.dense = 0;
+  o.corr_words = 2 + cdiv(N, kRiceChunk) + rice_words;
+  o.off_ei = o.off_c + align_up(o.corr_words * 4, 8);
+  o.off_ev = o.off_ei + align_up(nesc * 4, 8);
+  o.size = align_up(o.off_ev + align_up(nesc * es, 8), 16);
+  return o;
+}
 
 // Workspace of the mixed-precision form.
 struct MixedWork {
@@ -272,6 +304,8 @@ int launch_stage_correct(const float* x, const float* xh, int64_t n, double eb, 
 int launch_plain_compress(const Plan& p, const void* d_in, const Work& w, cudaStream_t s);
 int launch_scan(const Plan& p, const Work& w, size_t out_cap, void* d_out, cudaStream_t s);
 int launch_pack(const Plan& p, const void* d_in, const Work& w, void* d_out, size_t out_cap, cudaStream_t s);
+int launch_rice(const Plan& p, const Work& w, const uint8_t* s0, RiceInfo* info, RiceChunk* chunks, size_t out_cap,
+                void* d_out, cudaStream_t s);
 int launch_stats_resolve(const Plan& p, const void* d_in, const Work& w, double* partial, cudaStream_t s);
 int launch_field_stats(const Plan& p, const void* d_in, const Work& w, double* partial, double* h_stats,
                        cudaStream_t s);

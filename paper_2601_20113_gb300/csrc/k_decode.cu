@@ -89,9 +89,9 @@ __global__ void __launch_bounds__(kDecThreads, kDecMinBlocks) k_decode(Plan P, c
   const uint32_t* rec32 = reinterpret_cast<const uint32_t*>(rec);
   const int r = rec[0], flags = rec[1], wk = rec[2], ib = rec[3];
   const int64_t ncorr = rec32[1], nesc = rec32[2], nbytes = rec32[3];
-  // a flag outside raw / spatial side / dense corrections (a record section
-  // this decoder does not read, such as Rice-coded corrections) is refused
-  if (nbytes != (int64_t)(o1 - o0) || nbytes < 16 || (flags & ~(int)(kFlagRaw | kFlagSpatial | kFlagDense)) != 0) {
+  // a flag outside raw / spatial side / dense / Rice-coded corrections is refused
+  if (nbytes != (int64_t)(o1 - o0) || nbytes < 16 ||
+      (flags & ~(int)(kFlagRaw | kFlagSpatial | kFlagDense | kFlagRice)) != 0) {
     if (tid == 0) atomicOr(&st->corrupt, 1u);
     return;
   }
@@ -119,8 +119,23 @@ __global__ void __launch_bounds__(kDecThreads, kDecMinBlocks) k_decode(Plan P, c
     }
     wbase[r] = acc;
     if (!bad) {
-      const RecLayout lay = rec_layout(r, n, L, N, es, wq, wk, ib, ncorr, nesc);
-      if (lay.size != nbytes || (lay.dense ? 1 : 0) != ((flags & kFlagDense) ? 1 : 0)) bad = 1;
+      RecLayout lay = rec_layout(r, n, L, N, es, wq, wk, ib, ncorr, nesc);
+      if (flags & kFlagRice) {
+        // [coded words, kr | wv << 8, chunk bit offsets, coded words]
+        if (wk == 0 || (flags & kFlagDense) || lay.off_c + 8 > nbytes) {
+          bad = 1;
+        } else {
+          const uint32_t* cw = reinterpret_cast<const uint32_t*>(rec + lay.off_c);
+          if ((cw[1] >> 16) != 0u || (int)(cw[1] & 0xFFu) > kRiceMaxKr || (int)((cw[1] >> 8) & 0xFFu) > 32 ||
+              (int64_t)cw[0] > nbytes)
+            bad = 1;
+          else
+            lay = rice_layout(lay, N, cw[0], nesc, es);
+        }
+        if (!bad && lay.size != nbytes) bad = 1;
+      } else if (lay.size != nbytes || (lay.dense ? 1 : 0) != ((flags & kFlagDense) ? 1 : 0)) {
+        bad = 1;
+      }
     }
   }
   __syncthreads();
@@ -128,7 +143,9 @@ __global__ void __launch_bounds__(kDecThreads, kDecMinBlocks) k_decode(Plan P, c
     if (tid == 0) atomicOr(&st->corrupt, 1u);
     return;
   }
-  const RecLayout lay = rec_layout(r, n, L, N, es, wq, wk, ib, ncorr, nesc);
+  const bool rice = (flags & kFlagRice) != 0;
+  RecLayout lay = rec_layout(r, n, L, N, es, wq, wk, ib, ncorr, nesc);
+  if (rice) lay = rice_layout(lay, N, reinterpret_cast<const uint32_t*>(rec + lay.off_c)[0], nesc, es);
   const int v = g.v;
   const double delta = reinterpret_cast<const double*>(comp + kHdr + kVarRec * v)[2];
   const double step = reinterpret_cast<const double*>(comp + kHdr + kVarRec * v)[3];
@@ -229,7 +246,52 @@ __global__ void __launch_bounds__(kDecThreads, kDecMinBlocks) k_decode(Plan P, c
       break;
   }
   __syncthreads();
-  if (!dense && wk > 0) {
+  if (rice) {
+    // chunk by chunk, one thread each: a Rice code gives the zeros before
+    // the next nonzero (or the chunk's end), then wv bits give zigzag(k) - 1
+    const int kr = (int)(cw[1] & 0xFFu), wv = (int)((cw[1] >> 8) & 0xFFu);
+    const int64_t nch = cdiv(N, kRiceChunk);
+    const uint32_t* rw = cw + 2 + nch;
+    const uint64_t nbits = (uint64_t)cw[0] * 32;
+    for (int64_t ch = tid; ch < nch; ch += kDecThreads) {
+      const int64_t c1 = (ch + 1) * kRiceChunk < N ? (ch + 1) * kRiceChunk : N;
+      int64_t e = ch * kRiceChunk;
+      uint64_t pos = cw[2 + ch];
+      bool ok = true;
+      for (;;) {
+        // the unary part: ones up to a zero
+        uint64_t q = 0;
+        for (;;) {
+          if (pos >= nbits) { ok = false; break; }
+          const int avail = (nbits - pos) < 32 ? (int)(nbits - pos) : 32;
+          const uint32_t w = get_bits(rw, pos, avail);
+          const int t = (~w == 0u) ? 32 : __ffs(~w) - 1;
+          if (t >= avail) {
+            q += (uint64_t)avail;
+            pos += (uint64_t)avail;
+            if (q > (uint64_t)kRiceChunk) { ok = false; break; }
+            continue;
+          }
+          q += (uint64_t)t;
+          pos += (uint64_t)t + 1;
+          break;
+        }
+        if (!ok || pos + (uint64_t)kr > nbits) { ok = false; break; }
+        const uint64_t run = (q << kr) | get_bits(rw, pos, kr);
+        pos += (uint64_t)kr;
+        if (run > (uint64_t)(c1 - e)) { ok = false; break; }
+        e += (int64_t)run;
+        if (e == c1) break;
+        if (pos + (uint64_t)wv > nbits) { ok = false; break; }
+        const int32_t kv = unzigzag(get_bits(rw, pos, wv) + 1u);
+        pos += (uint64_t)wv;
+        const int64_t gi = elem_off(P, g, e);
+        out[gi] = tf<T>((T)kv, step_t, out[gi]);
+        ++e;
+      }
+      if (!ok) atomicOr(&st->corrupt, 1u);
+    }
+  } else if (!dense && wk > 0) {
 #pragma unroll 4
     for (int64_t i = tid; i < ncorr; i += kDecThreads) {
       const uint64_t pos = (uint64_t)i * (uint64_t)(ib + wk);
@@ -306,7 +368,9 @@ __global__ void k_verify_stream(Plan P, const uint8_t* comp, unsigned long long 
     atomicAdd(&t[8], (double)rec32[3]);
     return;
   }
-  const RecLayout lay = rec_layout(r, g.n, g.L, g.N, es, rec + 16, rec[2], rec[3], rec32[1], rec32[2]);
+  RecLayout lay = rec_layout(r, g.n, g.L, g.N, es, rec + 16, rec[2], rec[3], rec32[1], rec32[2]);
+  if ((flags & kFlagRice) && lay.off_c + 4 <= (int64_t)(o1 - o0))
+    lay = rice_layout(lay, g.N, reinterpret_cast<const uint32_t*>(rec + lay.off_c)[0], rec32[2], es);
   atomicAdd(&t[1], (double)r);
   atomicAdd(&t[2], (double)rec32[1]);
   atomicAdd(&t[3], (double)rec32[2]);

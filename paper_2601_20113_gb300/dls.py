@@ -21,6 +21,7 @@ PREC_FP64, PREC_TF32X3, PREC_BF16X3, PREC_FP32, PREC_TF32, PREC_BF16 = 0, 1, 2, 
 RANK_SEARCH, RANK_LEARNED, RANK_TAIL = 0, 1, 2
 MLP_NPARAM, MLP_NFEAT = 6401, 32
 OK = 0
+ERR_CORRUPT = -4
 ERR_TIMEOUT = -6
 ERR = {-1: "INVALID_ARG", -2: "CAPACITY", -3: "NONFINITE", -4: "CORRUPT", -5: "CUDA", -6: "TIMEOUT",
        -7: "BOUND_VIOLATED", -8: "WORKSPACE", -9: "NO_MODEL"}
@@ -48,6 +49,7 @@ class Params(C.Structure):
         ("basis", C.POINTER(C.c_double)),
         ("basis_n", C.c_int32),
         ("global_stats", C.POINTER(C.c_double)),
+        ("corr_codec", C.c_int32),
     ]
 
 
@@ -151,12 +153,13 @@ def _dtype_code(t: torch.dtype) -> int:
 
 
 def make_params(shape, dtype, block, eb, eb_type=EB_ABS, rank_cap=32, precision=PREC_FP64,
-                rank_mode=RANK_SEARCH, block_begin=0, block_end=-1, basis=None, global_stats=None):
+                rank_mode=RANK_SEARCH, block_begin=0, block_end=-1, basis=None, global_stats=None, corr_codec=0):
     """shape = (nvars, nt, nz, ny, nx) of the field tensor; basis: optional
     n x n orthonormal modes (column k = mode k) for the blocks of Gram order n;
     global_stats: optional nvars x 4 (min, max, sum of squares, point count) of
     the whole field when the tensor is one part of it (a z-slab): the relative
-    bounds and the NRMSE tolerance then come from the whole field."""
+    bounds and the NRMSE tolerance then come from the whole field; corr_codec:
+    1 adds the Rice-coded correction section where it is smaller."""
     nvars, nt, nz, ny, nx = shape
     p = Params()
     p.nvars = nvars
@@ -175,6 +178,7 @@ def make_params(shape, dtype, block, eb, eb_type=EB_ABS, rank_cap=32, precision=
     p.rank_mode = rank_mode
     p.block_begin = block_begin
     p.block_end = block_end
+    p.corr_codec = int(corr_codec)
     if basis is not None:
         import numpy as np
         b = np.ascontiguousarray(np.asarray(basis, dtype=np.float64))

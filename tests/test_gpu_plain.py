@@ -143,23 +143,6 @@ def test_gpu_decoder_on_oracle_streams():
         assert torch.equal(rec.cpu(), torch.from_numpy(rref))
 
 
-def test_decoder_refuses_rice_coded_records():
-    """A stream whose records carry the Rice-coded correction section (flag 8,
-    written by the oracle with corr_codec = 1) has a record section this
-    decoder does not read: dls_decompress reports DLS_ERR_CORRUPT instead of
-    reading the section as another one."""
-    dims = (32, 32, 16, 16)
-    f = synth.modes3d(*dims, seed=12, count=16).numpy()
-    eb = 1e-4 * float(f.max() - f.min())
-    cfg = oracle.Config(dims, (16, 16, 16, 16), oracle.F32, eb=eb, rank_cap=16, corr_codec=1)
-    st, s, _ = oracle.compress(cfg, f)
-    assert st == oracle.OK
-    payp = int(s[112:120].view(np.uint64)[0])
-    assert s[payp + 1] & 8, "the first record should take the Rice section"
-    out = torch.zeros((1, dims[3], dims[2], dims[1], dims[0]), dtype=torch.float32, device="cuda")
-    assert dls.decompress_into(torch.from_numpy(s).cuda(), out) == -4
-
-
 def test_errors_capacity_nonfinite_corrupt():
     dims = (16, 16, 8, 16)
     f = synth.modes3d(*dims, seed=9, count=8)

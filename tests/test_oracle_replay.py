@@ -164,3 +164,44 @@ def test_fp32_coefficients_match_binary32_evaluation():
         # and it is the FP64 projection up to binary32 evaluation error
         C64 = oracle.project(A, V)
         assert np.abs(got - C64).max() <= 1e-4 * np.abs(A).max() * np.abs(V).sum(0).max()
+
+
+def test_replay_reads_rice_coded_records():
+    """With the Rice-coded correction section asked for, the oracle's own
+    stream (Rice where smaller) parses and replays; the parser recovers the
+    corrections the plain stream carries, record for record."""
+    dims = (48, 48, 32, 32)
+    f = synth.modes3d(*dims, seed=2, count=64).numpy()
+    eb = 1e-3 * float(f.max() - f.min())
+    cfg = oracle.Config(dims, (16, 16, 16, 16), oracle.F32, eb=eb, rank_cap=16)
+    cfg_r = oracle.Config(dims, (16, 16, 16, 16), oracle.F32, eb=eb, rank_cap=16, corr_codec=1)
+    st, s, trs = oracle.compress(cfg, f, traces=True)
+    assert st == oracle.OK
+    st, sr, _ = oracle.compress(cfg_r, f)
+    assert st == oracle.OK and sr.size < s.size
+    res, errs = replay.replay_stream(cfg_r, f, sr, coeff="f64")
+    assert errs == [] and all(r["errors"] == [] for r in res)
+    a, ha = replay.parse_stream(s)
+    b, hb = replay.parse_stream(sr)
+    nrice = 0
+    for i in range(len(trs)):
+        g = oracle.block_geom(cfg, i)
+        pa = oracle.parse_record(replay.record_of(a, ha, i), g.side, g.n, g.L, g.M, cfg.dtype)
+        pb = oracle.parse_record(replay.record_of(b, hb, i), g.side, g.n, g.L, g.M, cfg.dtype)
+        nrice += bool(pb["flags"] & 8)
+        np.testing.assert_array_equal(pa["k"], pb["k"])
+        np.testing.assert_array_equal(pa["q"], pb["q"])
+    assert nrice > 0
+    # a Rice record with a flipped bit in its coded words does not parse
+    i = next(j for j in range(len(trs)) if replay.record_of(b, hb, j)[1] & 8)
+    g = oracle.block_geom(cfg, i)
+    rec = bytearray(bytes(replay.record_of(b, hb, i)))
+    bad = 0
+    for pos in range(200, len(rec) - 64, 97):
+        r2 = bytearray(rec)
+        r2[pos] ^= 0x10
+        p2 = oracle.parse_record(bytes(r2), g.side, g.n, g.L, g.M, cfg.dtype)
+        pa = oracle.parse_record(bytes(rec), g.side, g.n, g.L, g.M, cfg.dtype)
+        if p2 is None or not np.array_equal(p2["k"], pa["k"]) or not np.array_equal(p2["q"], pa["q"]):
+            bad += 1
+    assert bad > 0
