@@ -16,7 +16,10 @@ constexpr int kDecThreads = 256;
 // Shared-memory words for a record's coefficient and correction sections
 // (72 KB: three CTAs per SM, as the launch bounds ask of the registers).
 constexpr int kDecStageWords = 18432;
+// Resident CTAs asked of the registers: 3 (80 registers) or 2 (128, no
+// spills; faster where records are small, the unrolled rows dominating).
 constexpr int kDecMinBlocks = 3;
+constexpr int kDecSmallRecord = 32768;     // mean record bytes up to which the 2-CTA form runs
 
 template <typename T> __device__ __forceinline__ T dq(int32_t q, T d);
 template <> __device__ __forceinline__ float dq<float>(int32_t q, float d) { return __fmul_rn(__int2float_rn(q), d); }
@@ -49,6 +52,7 @@ __device__ __forceinline__ uint32_t get_bits32(const uint32_t* w, uint32_t pos, 
 }
 
 template <int V> struct RankC { static constexpr int value = V; };
+template <bool V> struct BoolC { static constexpr bool value = V; };
 
 // Field offset of a block's spatial point ls (x fastest) without the time
 // step: 32-bit division (a block's extents are small), once per point.
@@ -64,8 +68,8 @@ __device__ __forceinline__ int64_t elem_off(const Plan& p, const Geom& g, int64_
   return spatial_off(p, g, (int)(e - lt * g.M)) + (g.t0 + lt) * p.P;
 }
 
-template <typename T, int NM>
-__global__ void __launch_bounds__(kDecThreads, kDecMinBlocks) k_decode(Plan P, const uint8_t* __restrict__ comp,
+template <typename T, int NM, int MINB>
+__global__ void __launch_bounds__(kDecThreads, MINB) k_decode(Plan P, const uint8_t* __restrict__ comp,
                                                         unsigned long long comp_bytes, T* __restrict__ out,
                                                         Status* st) {
   extern __shared__ __align__(16) uint32_t stage_sm[];   // kDecStageWords
@@ -202,7 +206,51 @@ __global__ void __launch_bounds__(kDecThreads, kDecMinBlocks) k_decode(Plan P, c
       }
     }
   };
-  switch (r) {
+  // Time-side blocks of order 16 (the full 16^3 x 16 blocks) at ranks 1-4: the
+  // 16 outputs of a row unrolled, dense corrections read with 32-bit bit
+  // positions one time plane (M wk bits) apart (N wk < 2^32 here), blocks
+  // without dense corrections compiled without their test.
+  auto rows_t16 = [&](auto RK, auto DK) {
+    constexpr int R = decltype(RK)::value;
+    constexpr bool D = decltype(DK)::value;
+    int wqc[R];
+    const uint32_t* qc[R];
+#pragma unroll
+    for (int c = 0; c < R; ++c) { wqc[c] = wq[c]; qc[c] = qw + wbase[c]; }
+    const uint32_t pstep = (uint32_t)g.M * (uint32_t)wk;
+    for (int l = tid; l < (int)L; l += kDecThreads) {
+      T ch[R];
+#pragma unroll
+      for (int c = 0; c < R; ++c) ch[c] = dq<T>(unzigzag(get_bits32(qc[c], (uint32_t)l * (uint32_t)wqc[c], wqc[c])), delta_t);
+      T* o = out + spatial_off(P, g, l) + g.t0 * P.P;
+      uint32_t pos = (uint32_t)l * (uint32_t)wk;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        T acc = T(0);
+#pragma unroll
+        for (int c = 0; c < R; ++c) acc = tf<T>(ch[c], vst[j * NM + c], acc);
+        if (D) {
+          const int32_t kv = unzigzag(get_bits32(cw, pos, wk));
+          pos += pstep;
+          if (kv != 0) acc = tf<T>((T)kv, step_t, acc);
+        }
+        *o = acc;
+        o += P.P;
+      }
+    }
+  };
+  auto rows_t16_d = [&](auto RK) {
+    if (dense) rows_t16(RK, BoolC<true>());
+    else rows_t16(RK, BoolC<false>());
+  };
+  if (NM == 16 && g.side == 0 && n == 16 && r >= 1 && r <= 4) {
+    switch (r) {
+      case 1: rows_t16_d(RankC<1>()); break;
+      case 2: rows_t16_d(RankC<2>()); break;
+      case 3: rows_t16_d(RankC<3>()); break;
+      default: rows_t16_d(RankC<4>()); break;
+    }
+  } else switch (r) {
     case 1: rows_fixed(RankC<1>()); break;
     case 2: rows_fixed(RankC<2>()); break;
     case 3: rows_fixed(RankC<3>()); break;
@@ -396,10 +444,18 @@ int launch_decode(const Plan& p, const void* d_comp, unsigned long long comp_byt
     return true;
   };
   bool ok;
-  if (p.dtype == DLS_F32)
-    ok = p.nmax <= 16 ? go(k_decode<float, 16>, (float*)d_out) : go(k_decode<float, 32>, (float*)d_out);
-  else
-    ok = p.nmax <= 16 ? go(k_decode<double, 16>, (double*)d_out) : go(k_decode<double, 32>, (double*)d_out);
+  // measured on 16^3 x 16 float32 blocks: 2 CTAs per SM 1.78 ms against 2.13 at
+  // 1e-3 (21 KB records), 3 CTAs 3.52 against 3.79 at 1e-4 (52 KB records)
+  const bool small = comp_bytes / (unsigned long long)p.nb <= (unsigned long long)kDecSmallRecord;
+  if (p.dtype == DLS_F32) {
+    if (p.nmax <= 16)
+      ok = small ? go(k_decode<float, 16, 2>, (float*)d_out) : go(k_decode<float, 16, kDecMinBlocks>, (float*)d_out);
+    else
+      ok = go(k_decode<float, 32, kDecMinBlocks>, (float*)d_out);
+  } else {
+    ok = p.nmax <= 16 ? go(k_decode<double, 16, kDecMinBlocks>, (double*)d_out)
+                      : go(k_decode<double, 32, kDecMinBlocks>, (double*)d_out);
+  }
   return ok && cudaGetLastError() == cudaSuccess ? DLS_OK : DLS_ERR_CUDA;
 }
 
