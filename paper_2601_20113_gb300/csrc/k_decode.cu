@@ -399,6 +399,113 @@ __global__ void __launch_bounds__(256) k_verify_points(Plan P, const T* __restri
   }
 }
 
+// float32 fields: the same report with the FP64 pipe kept for what needs it.
+// A point's difference is s = fl32(x - y) and its rounding error e (TwoSum,
+// s + e = x - y exactly); the bound test decides in FP32 outside a relative
+// 2^-20 band around eb and in FP64 inside it; the maximum is taken in FP64 on
+// the points whose |s| reaches the thread's running maximum (rounding is
+// monotone, so the point of the largest |x - y| is among them); the sums of
+// squares run as unevaluated float pairs (x^2 = p + fma(x, x, -p) exactly,
+// d^2 = s^2 + 2 s e to within e^2 <= 2^-48 s^2) per batch of 1024 points of a
+// thread, each batch then added in FP64.  Values beyond 2^60 take the FP64
+// path.  Loads are float4 when the field allows (4 | K, 16-byte pointers).
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float a, float ae) {
+  const float s = __fadd_rn(hi, a);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(a, bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, ae));
+}
+
+// The FP64 work of a point, out of line so that it runs only when taken
+// (inlined, it would be predicated and issued for every point).
+__device__ __noinline__ double fp64_diff(float x, float y) { return fabs((double)x - (double)y); }
+
+__global__ void __launch_bounds__(256) k_verify_points_f32(Plan P, const float* __restrict__ a,
+                                                           const float* __restrict__ b, const uint8_t* comp,
+                                                           double* acc, int vec4) {
+  const int v = blockIdx.y;
+  const double eb = reinterpret_cast<const double*>(comp + kHdr + kVarRec * v)[1];
+  const bool pointwise = P.eb_type != DLS_EB_NRMSE;
+  const float eb_lo = __double2float_rd(eb * (1.0 - 0x1p-20)), eb_hi = __double2float_ru(eb * (1.0 + 0x1p-20));
+  const float big = 0x1p60f;
+  double mx = 0.0, se = 0.0, sx = 0.0;
+  float mx32 = 0.0f;
+  unsigned long long over = 0;
+  float eh = 0.0f, el = 0.0f, xh = 0.0f, xl = 0.0f;
+  auto point = [&](float x, float y) {
+    const float sd = __fsub_rn(x, y);
+    const float bb = __fsub_rn(sd, x);
+    const float e = __fadd_rn(__fsub_rn(x, __fsub_rn(sd, bb)), __fsub_rn(-y, bb));
+    const float ad = fabsf(sd);
+    if (!(fabsf(x) < big) || !(fabsf(y) < big) || !(ad < big)) {
+      // far out of range (or not finite): this point in FP64
+      const double d = fp64_diff(x, y);
+      mx = fmax(mx, d);
+      if (pointwise && d > eb) ++over;
+      se = fma(d, d, se);
+      sx = fma((double)x, (double)x, sx);
+      return;
+    }
+    if (ad >= mx32 && ad > 0.0f) {
+      mx32 = ad;
+      mx = fmax(mx, fp64_diff(x, y));
+    }
+    if (pointwise) {
+      if (ad > eb_hi) ++over;
+      else if (ad >= eb_lo && fp64_diff(x, y) > eb) ++over;
+    }
+    const float p = __fmul_rn(sd, sd);
+    ff_add(eh, el, p, __fmaf_rn(__fmul_rn(2.0f, sd), e, __fmaf_rn(sd, sd, -p)));
+    const float q = __fmul_rn(x, x);
+    ff_add(xh, xl, q, __fmaf_rn(x, x, -q));
+  };
+  auto flush = [&]() {
+    se += (double)eh + (double)el;
+    sx += (double)xh + (double)xl;
+    eh = el = xh = xl = 0.0f;
+  };
+  const int64_t base = (int64_t)v * P.K;
+  const int64_t stride = (int64_t)gridDim.x * 256;
+  if (vec4) {
+    // four points a load; batches of 256 loads (1024 points) per float pair
+    const float4* a4 = reinterpret_cast<const float4*>(a + base);
+    const float4* b4 = reinterpret_cast<const float4*>(b + base);
+    const int64_t K4 = P.K / 4;
+    int64_t i = blockIdx.x * 256ll + threadIdx.x;
+    while (i < K4) {
+#pragma unroll 4
+      for (int n = 0; n < 256 && i < K4; ++n, i += stride) {
+        const float4 x = a4[i], y = b4[i];
+        point(x.x, y.x);
+        point(x.y, y.y);
+        point(x.z, y.z);
+        point(x.w, y.w);
+      }
+      flush();
+    }
+  } else {
+    int64_t i = blockIdx.x * 256ll + threadIdx.x;
+    while (i < P.K) {
+      for (int n = 0; n < 1024 && i < P.K; ++n, i += stride) point(a[base + i], b[base + i]);
+      flush();
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    se += __shfl_xor_sync(0xffffffffu, se, o);
+    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+    over += __shfl_xor_sync(0xffffffffu, over, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    unsigned long long* u = reinterpret_cast<unsigned long long*>(acc + 16 * v);
+    atomicMax(&u[0], dkey(mx));
+    atomicAdd(&u[1], over);
+    atomicAdd(&acc[16 * v + 2], se);
+    atomicAdd(&acc[16 * v + 3], sx);
+  }
+}
+
 __global__ void k_verify_stream(Plan P, const uint8_t* comp, unsigned long long comp_bytes, int es, double* acc) {
   const int64_t bi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (bi >= P.nb) return;
@@ -463,7 +570,9 @@ int launch_verify(const Plan& p, const void* d_orig, const void* d_recon, const 
                   unsigned long long comp_bytes, double* acc, cudaStream_t s) {
   dim3 grid(1024, p.nvars);
   if (p.dtype == DLS_F32)
-    k_verify_points<float><<<grid, 256, 0, s>>>(p, (const float*)d_orig, (const float*)d_recon, (const uint8_t*)d_comp, acc);
+    k_verify_points_f32<<<grid, 256, 0, s>>>(p, (const float*)d_orig, (const float*)d_recon, (const uint8_t*)d_comp, acc,
+                                             (p.K % 4 == 0 && ((uintptr_t)d_orig & 15) == 0 &&
+                                              ((uintptr_t)d_recon & 15) == 0) ? 1 : 0);
   else
     k_verify_points<double><<<grid, 256, 0, s>>>(p, (const double*)d_orig, (const double*)d_recon, (const uint8_t*)d_comp, acc);
   if (p.nb > 0)
