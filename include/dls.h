@@ -400,6 +400,55 @@ int dls_set_fault_hook(int32_t kind, int64_t arg);
 /* Static text for a DLS_* status ("unknown status" for other values). */
 const char* dls_status_string(int status);
 
+/* ------------------------------------------------------------------------
+ * Global-basis mode: the method as Algorithm 1 states it (Sec. 2.3 Eq. 2-3,
+ * Sec. 2.4 Eq. 4, Sec. 2.5 Eq. 5-6, Sec. 2.6), one basis per variable for
+ * every patch of every snapshot, beside the block-local mode above.
+ *   step 1: Q (S x M) holds S patches of the first snapshot (rows, x fastest
+ *           within a patch) at the caller's origins; the modes Phi are the
+ *           eigenvectors of Q^T Q by decreasing eigenvalue (the right singular
+ *           vectors of Q), each signed so that its largest-magnitude
+ *           component is positive (the lowest index on ties);
+ *   step 2: eps = eps_t ||u|| / 100 over the variable (all snapshots),
+ *           eps_l^2 = eps^2 M / K, delta = eps / sqrt(K);
+ *   step 3: per patch of every snapshot (tiling from the origin): alpha =
+ *           Phi^T u, q = rint(alpha / delta), the coefficients ranked by
+ *           decreasing |alpha| (index order on ties), and the smallest kept
+ *           count n by bisection over [0, M] with pass(n) := ||u - sum_{s<n}
+ *           q_s delta phi_s||^2 <= eps_l^2 (the kept modes added in kept order).
+ * Everything in FP64.  Patches are m x m x m (m x m when nz == 1), M <= 128;
+ * the extents must be multiples of the patch.  One float32 variable per call,
+ * laid out (nt, nz, ny, nx).
+ * Stream ("DLSG", little-endian): header of 80 bytes (magic, u32 version 1,
+ * M, px, py, pz, u64 nx, ny, nz, nt, f64 eps_l^2, f64 delta, u64 records),
+ * the basis M x M float64 mode after mode, (records + 1) u64 offsets (an
+ * exclusive scan of the record sizes), then the records in (t, z, y, x) patch
+ * order: u32 n, u8 wv, three zero bytes, n mode indices of bit_width(M - 1)
+ * bits then n zigzag(q) of wv bits, LSB first in 32-bit words, padded to 8
+ * bytes. */
+typedef struct {
+  int64_t dims[4];      /* nx, ny, nz, nt */
+  int32_t m;            /* patch edge */
+  double eps_t;         /* NRMSE target in percent (> 0) */
+  int64_t nsample;      /* S: rows of the sample matrix (>= 1) */
+} dls_gb_params;
+
+/* Worst-case stream bytes; 0 for invalid parameters. */
+size_t dls_gb_bound(const dls_gb_params* p);
+/* Device workspace bytes dls_gb_compress needs (256-byte aligned). */
+size_t dls_gb_workspace_size(const dls_gb_params* p);
+/* d_in: the variable (nt, nz, ny, nx) float32 on the device; d_origins: S x 3
+ * int64 (x, y, z) patch origins in the first snapshot, each patch inside it
+ * (else DLS_ERR_INVALID_ARG, checked on the device).  On success *out_bytes
+ * is the stream size; DLS_ERR_CAPACITY sets it to the size needed.
+ * Synchronizes `stream`. */
+int dls_gb_compress(const dls_gb_params* p, const float* d_in, const int64_t* d_origins, void* d_out, size_t out_cap,
+                    size_t* out_bytes, void* d_workspace, size_t ws_bytes, dls_stream_t stream);
+/* The variable from a DLSG stream, in FP64 (each patch rebuilt as the sum of
+ * its kept modes in kept order, Sec. 2.6): d_out holds nt*nz*ny*nx doubles.
+ * DLS_ERR_CORRUPT for a stream that fails validation.  Synchronizes `stream`. */
+int dls_gb_decompress(const void* d_comp, size_t comp_bytes, double* d_out, size_t out_count, dls_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -53,6 +53,11 @@ class Params(C.Structure):
     ]
 
 
+class GbParams(C.Structure):
+    """dls_gb_params: the global-basis mode's problem (one float32 variable)."""
+    _fields_ = [("dims", C.c_int64 * 4), ("m", C.c_int32), ("eps_t", C.c_double), ("nsample", C.c_int64)]
+
+
 class Report(C.Structure):
     _fields_ = [
         ("max_abs_err", C.c_double), ("n_over_bound", C.c_int64), ("nrmse", C.c_double), ("ratio", C.c_double),
@@ -117,6 +122,11 @@ _SIGS = {
                                          C.c_void_p]),
     "dls_set_fault_hook": (C.c_int, [C.c_int32, C.c_int64]),
     "dls_status_string": (C.c_char_p, [C.c_int]),
+    "dls_gb_bound": (C.c_size_t, [C.POINTER(GbParams)]),
+    "dls_gb_workspace_size": (C.c_size_t, [C.POINTER(GbParams)]),
+    "dls_gb_compress": (C.c_int, [C.POINTER(GbParams), C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
+                                  C.POINTER(C.c_size_t), C.c_void_p, C.c_size_t, C.c_void_p]),
+    "dls_gb_decompress": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t, C.c_void_p]),
 }
 
 
@@ -478,3 +488,54 @@ def phase_cycles(p: Params, workspace: torch.Tensor) -> dict:
     if st != OK:
         raise DlsError(st, "dls_phase_cycles")
     return {k: int(arr[i]) for i, k in enumerate(PHASES)}
+
+
+# ---------------------------------------------------------------- global-basis mode
+def gb_params(shape, m, eps_t, nsample) -> GbParams:
+    """shape = (nt, nz, ny, nx) of one variable."""
+    nt, nz, ny, nx = shape
+    p = GbParams()
+    for a, d in enumerate((nx, ny, nz, nt)):
+        p.dims[a] = int(d)
+    p.m = int(m)
+    p.eps_t = float(eps_t)
+    p.nsample = int(nsample)
+    return p
+
+
+def gb_compress(field: torch.Tensor, m: int, eps_t: float, origins) -> torch.Tensor:
+    """Global-basis compression of a float32 CUDA variable (nt, nz, ny, nx) with
+    the sample patches at `origins` (S x 3 int64, x y z): the DLSG stream as a
+    uint8 CUDA tensor."""
+    import numpy as np
+    if not field.is_cuda or field.dtype != torch.float32 or field.dim() != 4 or not field.is_contiguous():
+        raise ValueError("field must be a contiguous float32 CUDA tensor (nt, nz, ny, nx)")
+    o = torch.from_numpy(np.ascontiguousarray(np.asarray(origins, dtype=np.int64))).to(field.device)
+    p = gb_params(tuple(field.shape), m, eps_t, o.shape[0])
+    cap = lib().dls_gb_bound(C.byref(p))
+    if cap == 0:
+        raise DlsError(-1, "dls_gb_bound")
+    out = torch.empty(cap, dtype=torch.uint8, device=field.device)
+    ws = torch.empty(lib().dls_gb_workspace_size(C.byref(p)), dtype=torch.uint8, device=field.device)
+    nb = C.c_size_t(0)
+    st = lib().dls_gb_compress(C.byref(p), _ptr(field), _ptr(o), _ptr(out), out.numel(), C.byref(nb), _ptr(ws),
+                               ws.numel(), _stream(None))
+    if st != OK:
+        raise DlsError(st, "dls_gb_compress")
+    return out[:nb.value].clone()
+
+
+def gb_decompress_into(comp: torch.Tensor, out: torch.Tensor) -> int:
+    return lib().dls_gb_decompress(_ptr(comp), comp.numel(), _ptr(out), out.numel(), _stream(None))
+
+
+def gb_decompress(comp: torch.Tensor) -> torch.Tensor:
+    """The variable (nt, nz, ny, nx) in float64 from a DLSG stream."""
+    import numpy as np
+    h = comp[:80].cpu().numpy()
+    nx, ny, nz, nt = (int(v) for v in h[24:56].view(np.uint64))
+    out = torch.empty((nt, nz, ny, nx), dtype=torch.float64, device=comp.device)
+    st = gb_decompress_into(comp, out)
+    if st != OK:
+        raise DlsError(st, "dls_gb_decompress")
+    return out

@@ -80,6 +80,7 @@ def test_struct_layouts_match_the_header(tmp_path):
     cases = [("dls_params", dls.Params, "dls.h", os.path.join(ROOT, "include")),
              ("dls_report", dls.Report, "dls.h", os.path.join(ROOT, "include")),
              ("dls_stream_info", dls.StreamInfo, "dls.h", os.path.join(ROOT, "include")),
+             ("dls_gb_params", dls.GbParams, "dls.h", os.path.join(ROOT, "include")),
              ("or_params", oracle.Params, "dls_oracle.h", os.path.join(ROOT, "oracle"))]
     for cname, py, hdr, inc in cases:
         lines = [f'#include "{hdr}"', "#include <stdio.h>", "#include <stddef.h>", "int main(void) {",
