@@ -390,6 +390,39 @@ def _plan_run(p, field, steps, stream=None):
     return ms, nb, stages, counters, comp
 
 
+def run_global_basis(dev):
+    """The global-basis mode (one FP64 basis per variable from 4 m^3 random
+    patches of the first snapshot, magnitude-ordered coefficients by
+    bisection): modes3d 128^3 x 16 float32 (128 MiB), patches of 4^3, NRMSE
+    target 1%; compression and decompression timed with CUDA events around the
+    calls (each synchronizes once), three runs after one warm-up."""
+    import torch
+
+    from paper_2601_20113_gb300 import dls, synth
+    dims, m, eps_t = (128, 128, 128, 16), 4, 1.0
+    f = synth.modes3d(*dims, seed=2, count=64, device=dev)[0].contiguous()
+    origins = synth.patch_origins(dims[:3], (m, m, m), 4 * m ** 3, seed=3)
+    comp = dls.gb_compress(f, m, eps_t, origins)
+    rec = dls.gb_decompress(comp)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(3):
+        comp = dls.gb_compress(f, m, eps_t, origins)
+    e1.record()
+    for _ in range(3):
+        rec = dls.gb_decompress(comp)
+    e2.record()
+    torch.cuda.synchronize()
+    nb = f.numel() * 4
+    cms, dms = e0.elapsed_time(e1) / 3, e1.elapsed_time(e2) / 3
+    nrmse = 100.0 * ((rec - f.double()).norm() / f.double().norm()).item()
+    return {"workload": "modes3d 128x128x128 x 16 float32 (128 MiB), patches 4^3 (M = 64), S = 256, "
+                        "NRMSE target 1%", "value": nb / (cms * 1e-3) / 1e9, "unit": "GB/s", "ms": cms,
+            "decompress_gbs": nb / (dms * 1e-3) / 1e9, "ratio": nb / comp.numel(), "nrmse_percent": nrmse,
+            "dtype": "f64"}
+
+
 def run_config(args):
     """The other at-scale configurations, one JSON line each:
     4 -- five float32 variables (u, v, w, p, T: vortex + mode mixtures) on
@@ -681,6 +714,8 @@ def main():
                                     "n_searched": fc["n_searched"], "phases_ms": fplan.phase_timing()}
             fplan.close()
             del fws
+    if not args.no_forms:
+        line["global_basis"] = run_global_basis(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         fcpu = field[:, :16, :16].cpu().numpy()
         v, cores, desc, el = oracle_sample_bench(fcpu, eb)

@@ -7,8 +7,8 @@
 // steps are
 //   k_gb_sample   the sample matrix Q (S x M) from the first snapshot,
 //   k_gb_gram     G = Q^T Q, each entry a sequential sum over the samples,
-//   k_gb_jacobi   the eigenvectors of G by cyclic Jacobi in one CTA (G in
-//                 shared memory, V in global memory), sorted by decreasing
+//   k_gb_jacobi   the eigenvectors of G by cyclic Jacobi in one CTA (G and,
+//                 when they fit, V in shared memory), sorted by decreasing
 //                 eigenvalue and signed (largest component positive),
 //   k_gb_norm     ||u||^2 of the variable, then eps_l^2 and delta,
 //   k_gb_patch    a warp per patch: alpha = Phi^T u, q = rint(alpha / delta),
@@ -156,15 +156,16 @@ __device__ __forceinline__ void gb_pair(int round, int i, int m, int& p, int& q)
 // columns of V by decreasing eigenvalue (index order on ties), each signed so
 // that its largest-magnitude component (the first on ties) is positive.
 constexpr int kJacThreads = 1024;
-__global__ void __launch_bounds__(kJacThreads, 1) k_gb_jacobi(GbPlan g, const double* __restrict__ G, double* V,
-                                                               double* phi, double* lam_out) {
-  extern __shared__ double A[];               // m x m
+__global__ void __launch_bounds__(kJacThreads, 1) k_gb_jacobi(GbPlan g, const double* __restrict__ G, double* Vg,
+                                                               double* phi, double* lam_out, int v_shared) {
+  extern __shared__ double A[];               // m x m, then V (m x m) when v_shared
   __shared__ int pq[kGbMaxM / 2];
   __shared__ double jc[kGbMaxM / 2], js[kGbMaxM / 2], jt[kGbMaxM / 2];
   __shared__ double lam[kGbMaxM];
   __shared__ int order[kGbMaxM];
   const int tid = threadIdx.x;
   const int M = g.M, m = M + (M & 1), h = m / 2;
+  double* V = v_shared ? A + m * m : Vg;
   for (int e = tid; e < m * m; e += kJacThreads) {
     const int i = e / m, j = e - i * m;
     A[e] = (i < M && j < M) ? G[i * M + j] : 0.0;
@@ -363,11 +364,14 @@ __global__ void __launch_bounds__(kGbWarps * 32) k_gb_patch(GbPlan g, const floa
       W.qd[k] = __dmul_rn((double)q, delta);
     }
     __syncwarp();
+    // ranks by |alpha| (descending, index order on ties) on the magnitudes'
+    // bit patterns: for non-negative doubles their order is the integers'
+    // order, and the comparisons leave the FP64 pipe to the arithmetic
     for (int k = lane; k < M; k += 32) {
-      const double ak = fabs(W.al[k]);
+      const unsigned long long ak = (unsigned long long)__double_as_longlong(W.al[k]) & 0x7FFFFFFFFFFFFFFFull;
       int rank = 0;
       for (int j = 0; j < M; ++j) {
-        const double aj = fabs(W.al[j]);
+        const unsigned long long aj = (unsigned long long)__double_as_longlong(W.al[j]) & 0x7FFFFFFFFFFFFFFFull;
         rank += (aj > ak || (aj == ak && j < k)) ? 1 : 0;
       }
       W.ord[rank] = k;
@@ -609,11 +613,13 @@ int dls_gb_compress(const dls_gb_params* p, const float* d_in, const int64_t* d_
   if (cudaMemsetAsync(gs, 0, sizeof(GbStatus), s) != cudaSuccess) return DLS_ERR_CUDA;
   k_gb_sample<<<(unsigned)g.S, 128, 0, s>>>(g, d_in, d_origins, Q, gs);
   k_gb_gram<<<(unsigned)cdiv((int64_t)g.M * g.M, 256), 256, 0, s>>>(g, Q, G);
+  // V beside A in shared memory when both fit (M <= 90), else in global memory
   const int me = g.M + (g.M & 1);
-  const size_t jsm = sizeof(double) * (size_t)me * me;
+  const int v_shared = 2 * sizeof(double) * (size_t)me * me <= 200 * 1024 ? 1 : 0;
+  const size_t jsm = sizeof(double) * (size_t)me * me * (v_shared ? 2 : 1);
   if (cudaFuncSetAttribute(k_gb_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm) != cudaSuccess)
     return DLS_ERR_CUDA;
-  k_gb_jacobi<<<1, kJacThreads, jsm, s>>>(g, G, V, phi, lam);
+  k_gb_jacobi<<<1, kJacThreads, jsm, s>>>(g, G, V, phi, lam, v_shared);
   k_gb_norm<<<kGbStatCtas, 256, 0, s>>>(g, d_in, partial, gs);
   k_gb_resolve<<<1, 1, 0, s>>>(g, partial, gs);
   const size_t psm = gb_patch_smem(g.M);
