@@ -1027,9 +1027,9 @@ int or_decompress(const void* stream, int64_t bytes, void* out, int64_t out_cap,
 
 /* ------------------------------------------------------------------ */
 /* Rice-coded corrections: a record section that or_pack_record takes  */
-/* with corr_codec = 1 (flag 8) where it is smaller; the CUDA packers   */
-/* and decoder do not write or read it.  The corrections k[0..N) of a   */
-/* block, in element order,                                             */
+/* with corr_codec = 1 (flag 8) where it is smaller (the lossless      */
+/* stage of the stream format).  The corrections k[0..N) of a block,   */
+/* in element order,                                                    */
 /* are cut into chunks of `chunk` elements.  Within a chunk every       */
 /* nonzero is written as the Rice code of the zeros before it (counted  */
 /* from the chunk start or the previous nonzero), then zigzag(k) - 1 in */
