@@ -306,6 +306,18 @@ __global__ void __launch_bounds__(kDecThreads, MINB) k_decode(Plan P, const uint
       int64_t e = ch * kRiceChunk;
       uint64_t pos = cw[2 + ch];
       bool ok = true;
+      int64_t pg[8];
+      int32_t pk[8];
+      int npend = 0;
+      auto flush = [&]() {
+        T val[8];
+#pragma unroll
+        for (int b = 0; b < 8; ++b) val[b] = b < npend ? out[pg[b]] : T(0);
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+          if (b < npend) out[pg[b]] = tf<T>((T)pk[b], step_t, val[b]);
+        npend = 0;
+      };
       for (;;) {
         // the unary part: ones up to a zero
         uint64_t q = 0;
@@ -333,21 +345,42 @@ __global__ void __launch_bounds__(kDecThreads, MINB) k_decode(Plan P, const uint
         if (pos + (uint64_t)wv > nbits) { ok = false; break; }
         const int32_t kv = unzigzag(get_bits(rw, pos, wv) + 1u);
         pos += (uint64_t)wv;
-        const int64_t gi = elem_off(P, g, e);
-        out[gi] = tf<T>((T)kv, step_t, out[gi]);
+        // the read-backs of the outputs go eight at a time (distinct elements)
+        pg[npend] = elem_off(P, g, e);
+        pk[npend] = kv;
+        if (++npend == 8) flush();
         ++e;
       }
+      flush();
       if (!ok) atomicOr(&st->corrupt, 1u);
     }
   } else if (!dense && wk > 0) {
-#pragma unroll 4
-    for (int64_t i = tid; i < ncorr; i += kDecThreads) {
-      const uint64_t pos = (uint64_t)i * (uint64_t)(ib + wk);
-      const int64_t e = get_bits(cw, pos, ib);
-      const int32_t kv = unzigzag(get_bits(cw, pos + ib, wk));
-      if (e >= N) { atomicOr(&st->corrupt, 1u); continue; }
-      const int64_t gi = elem_off(P, g, e);
-      out[gi] = tf<T>((T)kv, step_t, out[gi]);
+    // entry-list corrections read the rows' outputs back: eight entries a
+    // thread at a time, all eight loads issued before the first store, so that
+    // the read-backs overlap (entries name distinct elements)
+    constexpr int kB = 8;
+    for (int64_t i0 = tid; i0 < ncorr; i0 += (int64_t)kB * kDecThreads) {
+      int64_t gi[kB];
+      int32_t kv[kB];
+      T val[kB];
+#pragma unroll
+      for (int b = 0; b < kB; ++b) {
+        const int64_t i = i0 + (int64_t)b * kDecThreads;
+        gi[b] = -1;
+        kv[b] = 0;
+        if (i < ncorr) {
+          const uint64_t pos = (uint64_t)i * (uint64_t)(ib + wk);
+          const int64_t e = get_bits(cw, pos, ib);
+          kv[b] = unzigzag(get_bits(cw, pos + ib, wk));
+          if (e >= N) atomicOr(&st->corrupt, 1u);
+          else gi[b] = elem_off(P, g, e);
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < kB; ++b) val[b] = gi[b] >= 0 ? out[gi[b]] : T(0);
+#pragma unroll
+      for (int b = 0; b < kB; ++b)
+        if (gi[b] >= 0) out[gi[b]] = tf<T>((T)kv[b], step_t, val[b]);
     }
   }
   __syncthreads();
