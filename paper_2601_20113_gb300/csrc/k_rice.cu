@@ -158,6 +158,7 @@ __device__ void load_chunk(const CorrSrc& s, int64_t c0, int64_t c1, int64_t lo,
   for (int64_t j = lo + lane; j < hi; j += 32) {
     const uint64_t pos = (uint64_t)j * W;
     const int d = (int)((int64_t)rd_bits(s.cw, pos, s.ib) - c0);
+    if (d < 0 || d >= kRiceChunk) continue;     // entries are the chunk's (the packers sort them)
     atomicOr(&V.mask[d >> 5], 1u << (d & 31));
     V.z[33 * (d >> 5) + (d & 31)] = rd_bits(s.cw, pos + s.ib, s.wk);
   }
@@ -187,6 +188,8 @@ __device__ __forceinline__ void chunk_entries(const CorrSrc& s, const RiceChunk*
   }
   *lo = chunks[ch].first;
   *hi = ch + 1 < nch ? (int64_t)chunks[ch + 1].first : s.ncorr;
+  if (*hi > s.ncorr) *hi = s.ncorr;              // within the record's entry list
+  if (*lo > *hi) *lo = *hi;
 }
 
 // A lane's part of chunk [c0, c1): its first and last nonzero (-1 when none)
