@@ -37,13 +37,13 @@ def field():
     return torch.cat([a, b], dim=0).contiguous()
 
 
-def _params(x, eb_type, form, gstats=None):
+def _params(x, eb_type, form, gstats=None, codec=0):
     return dls.make_params(tuple(x.shape), x.dtype, BLOCK, EB[eb_type], eb_type, 16, precision=form[0],
-                           rank_mode=form[1], global_stats=gstats)
+                           rank_mode=form[1], global_stats=gstats, corr_codec=codec)
 
 
-def _compress(x, eb_type, form, gstats=None, plan=False):
-    p = _params(x, eb_type, form, gstats)
+def _compress(x, eb_type, form, gstats=None, plan=False, codec=0):
+    p = _params(x, eb_type, form, gstats, codec)
     out = torch.empty(dls.compress_bound(p), dtype=torch.uint8, device="cuda")
     ws = torch.empty(dls.workspace_size(p), dtype=torch.uint8, device="cuda")
     if plan:
@@ -104,3 +104,20 @@ def test_zslab_parts_merge_into_the_whole_stream(field, eb_type, form, world):
             assert nrmse <= EB[eb_type][v]
         else:
             assert err[v].abs().max().item() <= info.eb[v]
+
+
+@pytest.mark.parametrize("eb_type", [dls.EB_ABS, dls.EB_REL_RANGE])
+def test_zslab_parts_with_rice_coded_corrections(field, eb_type):
+    """The lossless stage changes records, not their order: parts compressed
+    with Rice-coded corrections merge into the whole field's stream with them."""
+    form = FORMS[1]
+    ranges = [shard.zslab_range(DIMS[2], BLOCK[2], r, 2) for r in range(2)]
+    parts = [field[:, :, z0:z1].contiguous() for z0, z1 in ranges]
+    g = shard.combine_stats([_stats(x) for x in parts])
+    merged = shard.merge_zslabs([_compress(x, eb_type, form, g, codec=1) for x in parts])
+    assert merged == _compress(field, eb_type, form, g, codec=1)
+    plain = _compress(field, eb_type, form, g)
+    assert len(merged) < len(plain)
+    a = dls.decompress(torch.from_numpy(np.frombuffer(merged, np.uint8).copy()).cuda())
+    b = dls.decompress(torch.from_numpy(np.frombuffer(plain, np.uint8).copy()).cuda())
+    assert torch.equal(a.view(torch.int32), b.view(torch.int32))
