@@ -659,9 +659,8 @@ def main():
     dms = d0.elapsed_time(d1) / args.steps
 
     # end-to-end through the host-buffer entry point; the pinned buffers are
-    # allocated from the CPUs of the GPU's NUMA node, so that their pages sit
-    # next to the GPU's host link (a buffer on the far node crosses the
-    # socket link and measured 61-70 GB/s against 175)
+    # allocated from the CPUs of the GPU's NUMA node, so that on a machine with
+    # several nodes their pages sit next to the GPU's host link
     node, keep = _pin_near_gpu(dev)
     try:
         h_in = torch.empty(field.shape, dtype=field.dtype, pin_memory=True)
