@@ -37,7 +37,7 @@ struct GbPlan {
 };
 
 struct GbStatus {
-  unsigned int bad_origin, overflow, corrupt, pad;
+  unsigned int bad_origin, overflow, corrupt, nonfinite;
   double eps_l2, delta;
   unsigned long long total;
 };
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(256) k_gb_norm(GbPlan g, const float* __restri
     __syncthreads();
   }
   if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
-  if (bad) atomicOr(&st->corrupt, 2u);
+  if (bad) atomicOr(&st->nonfinite, 1u);
 }
 
 // eps = eps_t ||u|| / 100, eps_l^2 = eps^2 M / K, delta = eps / sqrt(K).
@@ -642,7 +642,7 @@ int dls_gb_compress(const dls_gb_params* p, const float* d_in, const int64_t* d_
       cudaStreamSynchronize(s) != cudaSuccess)
     return DLS_ERR_CUDA;
   if (hs.bad_origin || hs.overflow) return DLS_ERR_INVALID_ARG;
-  if (hs.corrupt & 2u) return DLS_ERR_NONFINITE;
+  if (hs.nonfinite) return DLS_ERR_NONFINITE;
   *out_bytes = (size_t)hs.total;
   return hs.total > out_cap ? DLS_ERR_CAPACITY : DLS_OK;
 }
@@ -688,7 +688,10 @@ int dls_gb_decompress(const void* d_comp, size_t comp_bytes, double* d_out, size
   if (first != 0 || (uint64_t)g.payload_pos + last != (uint64_t)comp_bytes) return DLS_ERR_CORRUPT;
   GbStatus* gs = nullptr;
   if (cudaMallocAsync((void**)&gs, sizeof(GbStatus), s) != cudaSuccess) return DLS_ERR_CUDA;
-  cudaMemsetAsync(gs, 0, sizeof(GbStatus), s);
+  if (cudaMemsetAsync(gs, 0, sizeof(GbStatus), s) != cudaSuccess) {
+    cudaFreeAsync(gs, s);
+    return DLS_ERR_CUDA;
+  }
   if (g.nrec > 0)
     k_gb_decode<<<(unsigned)cdiv(g.nrec, 8), 256, 0, s>>>(g, c, (unsigned long long)comp_bytes, delta, d_out, gs);
   GbStatus hs;
