@@ -368,6 +368,7 @@ def _plan_run(p, field, steps, stream=None):
     out = torch.empty(dls.compress_bound(p), dtype=torch.uint8, device=field.device)
     ws = torch.empty(dls.workspace_size(p), dtype=torch.uint8, device=field.device)
     plan = dls.CompressPlan(p, field, out, ws, stream)
+    tuning = plan.tuning()
     for _ in range(3):
         nb = plan.execute(stream)
     torch.cuda.synchronize()
@@ -382,6 +383,7 @@ def _plan_run(p, field, steps, stream=None):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     counters = dls.phase_cycles(p, ws)
+    counters["tuning"] = tuning
     plan.close()
     stages = {k: sum(d[k] for d in phs) / len(phs) for k in phs[0]}
     comp = out[:nb].clone()
@@ -481,7 +483,8 @@ def run_config(args):
                                 precision=dls.PREC_FP32, rank_mode=rm)
             ms, nb, stages, c, cs = _plan_run(p, field, args.steps)
             modes[name] = {"value": in_bytes / (ms * 1e-3) / 1e9, "ms_per_step": ms, "ratio": in_bytes / nb,
-                           "n_accepted": c["n_accepted"], "n_searched": c["n_searched"], "phases_ms": stages}
+                           "n_accepted": c["n_accepted"], "n_searched": c["n_searched"], "phases_ms": stages,
+                           "tuning": c["tuning"]}
             if name == "learned":
                 comp = cs
         rec = dls.decompress(comp)
@@ -609,7 +612,7 @@ def main():
     stream = torch.cuda.current_stream()
     in_bytes = field.numel() * field.element_size()
 
-    # the captured plan: autotuned variant, whole compression in one CUDA graph
+    # the captured plan: occupancy form tuned per shape class, whole compression in one CUDA graph
     plan = dls.CompressPlan(p, field, out, ws, stream)
     for _ in range(args.warmup):
         nb = plan.execute(stream)
@@ -638,6 +641,7 @@ def main():
     counters = dls.phase_cycles(p, ws) if args.form != "plain" else None
     graph_kernels = plan.timing()[1]
     variant, tune_ms = plan.info()
+    tuning = plan.tuning()
     plan.close()
     if dist is not None:
         t = torch.tensor([ms], device=dev)
@@ -696,7 +700,7 @@ def main():
         "e2e": {"value": in_bytes * world / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": in_bytes,
                 "d2h_bytes_per_step": enb, "host_numa_node": node},
         "gpu_launches": graph_kernels * args.steps,
-        "plan": {"variant": variant, "tune_ms": list(tune_ms), "kernel_ms": kernel_ms,
+        "plan": {"variant": variant, "tune_ms": list(tune_ms), "tuning": tuning, "kernel_ms": kernel_ms,
                  "graph_kernel_nodes": graph_kernels},
         "clocks": clk,
     }

@@ -176,10 +176,13 @@ int dls_field_stats(const dls_params* p, const void* d_in, double* h_stats, void
 
 /* Reusable compression plan for fixed parameters and buffers (a time series
  * of snapshots written into the same buffers, for example).  Creation
- * validates like dls_compress, picks the occupancy variant of the per-block
- * kernel by timing each on the real data (two full compressions per variant;
- * the choice is cached as JSON lines in the file named by the environment
- * variable DLS_AUTOTUNE_CACHE when set), then captures the whole compression
+ * validates like dls_compress, picks the occupancy form of the per-block
+ * kernels for each shape class of the plan's blocks by timing both forms on
+ * the real data (two full compressions per form, the classes timed apart by
+ * events between their kernels; each class's choice is cached as a JSON line
+ * in the file named by the environment variable DLS_AUTOTUNE_CACHE when set,
+ * keyed by the parameters and the class; dls_plan_tuning reports it), then
+ * captures the whole compression
  * (status reset, bound resolution, the persistent per-block kernel over every
  * block of every variable, scan + header, record placement and the deferred
  * record packer, status readback) in one CUDA graph.  Execution returns what
@@ -190,10 +193,23 @@ typedef struct dls_plan dls_plan;
 int dls_plan_create(const dls_params* p, const void* d_in, void* d_out, size_t out_cap, void* d_workspace,
                     size_t ws_bytes, dls_stream_t stream, dls_plan** out_plan);
 int dls_plan_execute(dls_plan* plan, size_t* out_bytes, dls_stream_t stream);
-/* Chosen occupancy variant (1: fewer CTAs per SM with more registers each,
- * 2: more CTAs per SM) and the two timings in ms (0 if the choice came from
- * the cache or the form has one variant). */
+/* Chosen occupancy form of the whole-block class (as dls_plan_tuning's
+ * forms[0]) and the device ms of the per-block kernels, scan and packing of
+ * one compression with every class in form 1 and in form 2 (0 if the choices
+ * came from the cache or the form has one variant). */
 int dls_plan_info(const dls_plan* plan, int32_t* variant, float* tune_ms);
+/* The plan's occupancy form per shape class -- 1: the kernels built for 2
+ * CTAs per SM (more registers per thread), 2: built for 4 -- and the device
+ * time that chose it.  Classes: [0] "whole", the blocks of the full block
+ * shape that the encode kernel finishes at the predicted rank (Sec. 2.5 rank
+ * step); [1] "rest", what the searching kernels take: edge blocks of smaller
+ * shapes (Sec. 2.7.1 partition remainders), predictions the exact test
+ * rejects, blocks whose Gram side is space, or every block when the plan
+ * searches.  forms: 2 entries (form 1 or 2 of each class); class_ms: 4
+ * entries, class_ms[2 c + f - 1] = ms of class c's kernels in form f during
+ * tuning (0 if the choices came from the cache).  The forms run the same code,
+ * so the stream does not depend on them.  Either pointer may be null. */
+int dls_plan_tuning(const dls_plan* plan, int32_t* forms, float* class_ms);
 /* Device time in ms of the per-block compression kernels during the most
  * recent dls_plan_execute (events recorded around them inside the graph; waits
  * for that execution), and the number of kernel nodes in the plan's graph.

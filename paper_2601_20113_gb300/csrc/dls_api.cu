@@ -157,12 +157,14 @@ static MixedRoute mixed_route(const Plan& P) {
   return r;
 }
 
-static int launch_mixed_all(const Plan& P, const void* d_in, const MixedWork& mw, int mode, int variant,
+static int launch_mixed_all(const Plan& P, const void* d_in, const MixedWork& mw, int mode, Occupancy occ,
                             cudaStream_t s, const cudaEvent_t* pev = nullptr) {
   const MixedRoute rt = mixed_route(P);
   int st;
-  if (rt.tile && (st = launch_tile_compress(P, d_in, mw, mode, variant, s, 0, -1, pev)) != DLS_OK) return st;
-  if (rt.legacy && (st = launch_mixed_compress(P, d_in, mw, mode, variant, rt.spatial_only ? 1 : 0, s)) != DLS_OK)
+  if (rt.tile && (st = launch_tile_compress(P, d_in, mw, mode, occ, s, 0, -1, pev)) != DLS_OK) return st;
+  if (rt.legacy &&
+      (st = launch_mixed_compress(P, d_in, mw, mode, occ.rest != 0 ? occ.rest : 2, rt.spatial_only ? 1 : 0, s)) !=
+          DLS_OK)
     return st;
   return DLS_OK;
 }
@@ -362,7 +364,7 @@ static MixedWork mixed_work(const Plan& P, const Layout& L, void* ws) {
 // events) marks the ends of k_gram, k_eig, the Rayleigh-Ritz kernels, k_enc
 // and of the record packing.
 static int enqueue_compress(const Plan& P, const Layout& L, const void* d_in, void* d_out, size_t out_cap,
-                            void* d_ws, int variant, cudaStream_t s, cudaEvent_t ev0 = nullptr,
+                            void* d_ws, Occupancy occ, cudaStream_t s, cudaEvent_t ev0 = nullptr,
                             cudaEvent_t ev1 = nullptr, const cudaEvent_t* pev = nullptr) {
   int st;
   Work w = carve(L, d_ws);
@@ -377,16 +379,16 @@ static int enqueue_compress(const Plan& P, const Layout& L, const void* d_in, vo
     const MixedWork mw = mixed_work(P, L, d_ws);
     CK(cudaMemsetAsync(mw.phase, 0, sizeof(unsigned long long) * (size_t)L.ctas * kMixedPhases, s));
     const int mode = P.rank_mode == DLS_RANK_LEARNED ? kRankMlp : (P.rank_mode == DLS_RANK_TAIL ? kRankTail : kRankSearch);
-    if (ev0) CK(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
-    if ((st = launch_mixed_all(P, d_in, mw, mode, variant, s, pev)) != DLS_OK) return st;
-    if (ev1) CK(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
+    if (ev0) CK(record_marker(ev0, s));
+    if ((st = launch_mixed_all(P, d_in, mw, mode, occ, s, pev)) != DLS_OK) return st;
+    if (ev1) CK(record_marker(ev1, s));
     if ((st = launch_scan(P, w, cap1, out1, s)) != DLS_OK) return st;
     if ((st = launch_compact(P, mw, out1, s)) != DLS_OK) return st;
     if ((st = launch_pack_tile(P, mw, d_in, out1, s)) != DLS_OK) return st;
   } else {
-    if (ev0) CK(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
+    if (ev0) CK(record_marker(ev0, s));
     if ((st = launch_plain_compress(P, d_in, w, s)) != DLS_OK) return st;
-    if (ev1) CK(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
+    if (ev1) CK(record_marker(ev1, s));
     if ((st = launch_scan(P, w, cap1, out1, s)) != DLS_OK) return st;
     if ((st = launch_pack(P, d_in, w, out1, cap1, s)) != DLS_OK) return st;
   }
@@ -394,7 +396,7 @@ static int enqueue_compress(const Plan& P, const Layout& L, const void* d_in, vo
       (st = launch_rice(P, w, (const uint8_t*)out1, (RiceInfo*)((uint8_t*)d_ws + L.rice_info),
                         (RiceChunk*)((uint8_t*)d_ws + L.rice_chunks), out_cap, d_out, s)) != DLS_OK)
     return st;
-  if (L.mixed && pev && pev[4]) CK(cudaEventRecordWithFlags(pev[4], s, cudaEventRecordExternal));
+  if (L.mixed && pev && pev[4]) CK(record_marker(pev[4], s));
   return DLS_OK;
 }
 
@@ -448,7 +450,7 @@ static int compress_host_pipelined(const Plan& P, const Layout& L, const void* h
     if (cudaStreamWaitEvent(s, ev[k], 0) != cudaSuccess ||
         cudaMemsetAsync(&w.status->pad[1], 0, sizeof(unsigned long long), s) != cudaSuccess)
       return done(DLS_ERR_CUDA);
-    if ((st = launch_tile_compress(P, d_in, mw, mode, 2, s, k * nbs, (k + 1) * nbs)) != DLS_OK) return done(st);
+    if ((st = launch_tile_compress(P, d_in, mw, mode, kOccDefault, s, k * nbs, (k + 1) * nbs)) != DLS_OK) return done(st);
   }
   uint8_t* out1 = P.corr_codec ? d_ws + L.rice_tmp : d_out;
   if ((st = launch_scan(P, w, bound, out1, s)) != DLS_OK) return done(st);
@@ -478,8 +480,9 @@ struct dls_plan {
   void* d_out;
   size_t out_cap;
   void* d_ws;
-  int variant;
-  float tune_ms[3];
+  dls::Occupancy occ;
+  float tune_ms[3];        // [1], [2]: a whole compression with every class in form 1, in form 2
+  float class_ms[2][2];    // [class][form - 1]: device ms of the class's kernels (whole, rest)
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   dls::Status* h_status;   // pinned
@@ -510,7 +513,9 @@ static const char* tune_cache_path() {
   return (e && *e) ? e : nullptr;
 }
 
-// Cached variant for the key (JSON lines {"key": "...", "variant": v, ...}), or 0.
+// Cached form for the key (JSON lines {"key": "...", "variant": v, ...}; the
+// last line for a key wins), or 0.  A plan's keys are its parameters' key
+// followed by "|whole" and "|rest", one line per shape class.
 static int tune_lookup(const std::string& key) {
   const char* path = tune_cache_path();
   if (!path) return 0;
@@ -534,7 +539,7 @@ static void tune_store(const std::string& key, int variant, const float* ms) {
   if (!path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "{\"key\": \"%s\", \"variant\": %d, \"ms\": [%.4f, %.4f]}\n", key.c_str(), variant, ms[1], ms[2]);
+  fprintf(f, "{\"key\": \"%s\", \"variant\": %d, \"ms\": [%.4f, %.4f]}\n", key.c_str(), variant, ms[0], ms[1]);
   fclose(f);
 }
 
@@ -592,7 +597,7 @@ int dls_compress(const dls_params* p, const void* d_in, void* d_out, size_t out_
   cudaStream_t s = (cudaStream_t)stream;
   Work w = carve(L, d_workspace);
   if ((st = upload_basis(p, P, L, d_workspace, s)) != DLS_OK) return st;
-  if ((st = enqueue_compress(P, L, d_in, d_out, out_cap, d_workspace, 2, s)) != DLS_OK) return st;
+  if ((st = enqueue_compress(P, L, d_in, d_out, out_cap, d_workspace, kOccDefault, s)) != DLS_OK) return st;
   Status hs;
   CK(cudaMemcpyAsync(&hs, w.status, sizeof(Status), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -701,7 +706,7 @@ int dls_block_features(const dls_params* p, const void* d_in, float* d_feat, int
   MixedWork mw = mixed_work(P, L, d_workspace);
   mw.feat = d_feat;
   mw.ranks = d_rank;
-  if ((st = launch_mixed_all(P, d_in, mw, kRankSearch, 2, s)) != DLS_OK) return st;
+  if ((st = launch_mixed_all(P, d_in, mw, kRankSearch, kOccDefault, s)) != DLS_OK) return st;
   Status hs;
   CK(cudaMemcpyAsync(&hs, w.status, sizeof(Status), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -794,8 +799,9 @@ int dls_plan_create(const dls_params* p, const void* d_in, void* d_out, size_t o
   pl->d_out = d_out;
   pl->out_cap = out_cap;
   pl->d_ws = d_workspace;
-  pl->variant = 2;
+  pl->occ = kOccDefault;
   pl->tune_ms[0] = pl->tune_ms[1] = pl->tune_ms[2] = 0.0f;
+  for (int c = 0; c < 2; ++c) pl->class_ms[c][0] = pl->class_ms[c][1] = 0.0f;
   pl->graph = nullptr;
   pl->exec = nullptr;
   pl->h_status = nullptr;
@@ -821,27 +827,45 @@ int dls_plan_create(const dls_params* p, const void* d_in, void* d_out, size_t o
   // the fixed basis goes into the workspace once, outside the captured graph
   if ((st = upload_basis(p, P, L, d_workspace, s)) != DLS_OK) return fail(st);
   if ((P.basis_n > 0 || P.has_gstats) && cudaStreamSynchronize(s) != cudaSuccess) return fail(DLS_ERR_CUDA);
-  // autotune: time each occupancy variant of the per-block kernel on the real work
+  // autotune, per shape class: run every class in form 1, then every class in
+  // form 2 (a warm-up compression, then a timed one), time each class's
+  // kernels with the events between the stages, and keep each class's faster
+  // form.  The classes run in separate kernels one after the other, and the
+  // rest class's list does not depend on the form k_enc ran in, so the two
+  // choices are independent.
   if (L.mixed) {
     const std::string key = tune_key(P);
-    int v = tune_lookup(key);
-    if (v == 0) {
-      cudaEvent_t e0, e1;
-      if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(DLS_ERR_CUDA);
-      for (int var = 1; var <= 2; ++var) {
-        if ((st = enqueue_compress(P, L, d_in, d_out, out_cap, d_workspace, var, s)) != DLS_OK) return fail(st);
-        cudaEventRecord(e0, s);
-        if ((st = enqueue_compress(P, L, d_in, d_out, out_cap, d_workspace, var, s)) != DLS_OK) return fail(st);
-        cudaEventRecord(e1, s);
-        if (cudaEventSynchronize(e1) != cudaSuccess) return fail(DLS_ERR_CUDA);
-        cudaEventElapsedTime(&pl->tune_ms[var], e0, e1);
+    const std::string kc[2] = {key + "|whole", key + "|rest"};
+    int v[2] = {tune_lookup(kc[0]), tune_lookup(kc[1])};
+    if (v[0] == 0 || v[1] == 0) {
+      const bool staged = mixed_route(P).tile;
+      for (int form = 1; form <= 2; ++form) {
+        const Occupancy o{form, form};
+        if ((st = enqueue_compress(P, L, d_in, d_out, out_cap, d_workspace, o, s)) != DLS_OK) return fail(st);
+        if ((st = enqueue_compress(P, L, d_in, d_out, out_cap, d_workspace, o, s, pl->kev[0], pl->kev[1],
+                                   pl->pev)) != DLS_OK)
+          return fail(st);
+        if (cudaEventSynchronize(pl->pev[4]) != cudaSuccess) return fail(DLS_ERR_CUDA);
+        float whole = 0.0f, rest = 0.0f;
+        if (staged) {
+          // k_enc between the Rayleigh-Ritz stage and its own end; k_tile and
+          // k_mixed from there to the end of the per-block kernels
+          if (cudaEventElapsedTime(&whole, pl->pev[2], pl->pev[3]) != cudaSuccess ||
+              cudaEventElapsedTime(&rest, pl->pev[3], pl->kev[1]) != cudaSuccess)
+            return fail(DLS_ERR_CUDA);
+        } else if (cudaEventElapsedTime(&rest, pl->kev[0], pl->kev[1]) != cudaSuccess) {
+          return fail(DLS_ERR_CUDA);
+        }
+        if (cudaEventElapsedTime(&pl->tune_ms[form], pl->kev[0], pl->pev[4]) != cudaSuccess) return fail(DLS_ERR_CUDA);
+        pl->class_ms[0][form - 1] = whole;
+        pl->class_ms[1][form - 1] = rest;
       }
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      v = pl->tune_ms[1] < pl->tune_ms[2] ? 1 : 2;
-      tune_store(key, v, pl->tune_ms);
+      for (int c = 0; c < 2; ++c) {
+        v[c] = pl->class_ms[c][0] < pl->class_ms[c][1] ? 1 : 2;
+        tune_store(kc[c], v[c], pl->class_ms[c]);
+      }
     }
-    pl->variant = v;
+    pl->occ = Occupancy{v[0], v[1]};
   }
   // capture the sequence, ending with the status copy into pinned memory, on a
   // private stream (the legacy default stream cannot be captured)
@@ -852,7 +876,7 @@ int dls_plan_create(const dls_params* p, const void* d_in, void* d_out, size_t o
     cudaStreamDestroy(cs);
     return fail(DLS_ERR_CUDA);
   }
-  st = enqueue_compress(P, L, d_in, d_out, out_cap, d_workspace, pl->variant, cs, pl->kev[0], pl->kev[1],
+  st = enqueue_compress(P, L, d_in, d_out, out_cap, d_workspace, pl->occ, cs, pl->kev[0], pl->kev[1],
                         L.mixed ? pl->pev : nullptr);
   Work w = carve(L, d_workspace);
   cudaError_t ce = cudaMemcpyAsync(pl->h_status, w.status, sizeof(Status), cudaMemcpyDeviceToHost, cs);
@@ -893,8 +917,20 @@ int dls_plan_execute(dls_plan* pl, size_t* out_bytes, dls_stream_t stream) {
 
 int dls_plan_info(const dls_plan* pl, int32_t* variant, float* tune_ms) {
   if (!pl) return DLS_ERR_INVALID_ARG;
-  if (variant) *variant = pl->variant;
+  if (variant) *variant = pl->occ.whole;
   if (tune_ms) { tune_ms[0] = pl->tune_ms[1]; tune_ms[1] = pl->tune_ms[2]; }
+  return DLS_OK;
+}
+
+int dls_plan_tuning(const dls_plan* pl, int32_t* forms, float* class_ms) {
+  if (!pl) return DLS_ERR_INVALID_ARG;
+  if (forms) {
+    forms[0] = pl->occ.whole;
+    forms[1] = pl->occ.rest;
+  }
+  if (class_ms)
+    for (int c = 0; c < 2; ++c)
+      for (int f = 0; f < 2; ++f) class_ms[2 * c + f] = pl->class_ms[c][f];
   return DLS_OK;
 }
 

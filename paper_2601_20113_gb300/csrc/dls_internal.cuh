@@ -282,9 +282,35 @@ int64_t fault_withheld_block();
 // ---------------------------------------------------------------- launchers (defined in .cu files)
 int launch_mixed_compress(const Plan& p, const void* d_in, const MixedWork& w, int learned, int variant,
                           int spatial_only, cudaStream_t s);
+// Occupancy forms of the per-block kernels, one per shape class of a
+// compression's blocks (1: the form built for 2 CTAs per SM, with more
+// registers per thread; 2: the form built for 4).  `whole`: the blocks of the
+// full block shape that k_enc encodes at the predicted rank.  `rest`: what
+// k_tile and k_mixed take -- edge blocks of smaller shapes, predictions k_enc
+// rejects, blocks whose Gram side is space, every block in the search mode;
+// 0 there means the 2-CTA form behind k_enc (a short list) and the 4-CTA form
+// when k_tile takes every block.  Both forms run the same code, so the choice
+// changes the time and never a byte of the stream.
+struct Occupancy {
+  int whole;
+  int rest;
+};
+constexpr Occupancy kOccDefault{2, 0};
+
+// Records ev on s: as an event node of the graph while s is being captured
+// (its time is then read after each replay), as a plain record otherwise (the
+// external form is refused outside a capture).
+inline cudaError_t record_marker(cudaEvent_t ev, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const cudaError_t e = cudaStreamIsCapturing(s, &cs);
+  if (e != cudaSuccess) return e;
+  return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal)
+                                             : cudaEventRecord(ev, s);
+}
+
 // pev (optional): four events recorded after k_gram, k_eig, the
 // Rayleigh-Ritz kernels and k_enc (for the phase timing of captured plans).
-int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, int learned, int variant,
+int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, int learned, Occupancy occ,
                          cudaStream_t s, int64_t blo = 0, int64_t bhi = -1, const cudaEvent_t* pev = nullptr);
 bool tile_chunk_box(const Plan& p, int* bxb, int* yc, int* zc, int* bt);
 size_t tile_fast_bytes(int64_t nb);

@@ -2820,10 +2820,10 @@ size_t tile_fast_bytes(int64_t nb) {
          (size_t)align_up(n1 * 4, 256);
 }
 
-int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, int learned, int variant,
+int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, int learned, Occupancy occ,
                          cudaStream_t s, int64_t blo, int64_t bhi, const cudaEvent_t* pev) {
   auto mark = [&](int i) -> bool {
-    return !pev || !pev[i] || cudaEventRecordWithFlags(pev[i], s, cudaEventRecordExternal) == cudaSuccess;
+    return !pev || !pev[i] || record_marker(pev[i], s) == cudaSuccess;
   };
   if (bhi < 0) bhi = p.nb;
   if (blo < 0 || blo > bhi || bhi > p.nb || !w.fast || !w.phase || w.ctas < 1) return DLS_ERR_INVALID_ARG;
@@ -2958,25 +2958,27 @@ int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, in
   // 3. encode pass and deferred record at the predicted rank
   const size_t tsm = tile_smem_bytes(false);
   if (learned != kRankSearch) {
-    const int per = variant == 1 ? ctas_per_sm_of(k_enc<2>, tsm, false) : ctas_per_sm_of(k_enc<4>, tsm, false);
+    const int per = occ.whole == 1 ? ctas_per_sm_of(k_enc<2>, tsm, false) : ctas_per_sm_of(k_enc<4>, tsm, false);
     cudaGetLastError();
     if (per < 1) return DLS_ERR_CUDA;
     const int grid = grid_of(per, w.ctas);
-    if (variant == 1) k_enc<2><<<grid, kTT, tsm, s>>>(tmap, tmapg, a);
+    if (occ.whole == 1) k_enc<2><<<grid, kTT, tsm, s>>>(tmap, tmapg, a);
     else k_enc<4><<<grid, kTT, tsm, s>>>(tmap, tmapg, a);
     a.from_list = 1;
   }
   if (!mark(3)) return DLS_ERR_CUDA;
-  // 4. the other blocks (all of them with the bisection); the few k_enc leaves
-  //    take the 2-CTA form (no spills: 0.334 -> 0.285 ms for the one block left
-  //    at 1e-3), a full search the plan's variant
+  // 4. the other blocks (all of them with the bisection).  By default the few
+  //    k_enc leaves take the 2-CTA form (no spills: 0.334 -> 0.285 ms for the
+  //    one block left at 1e-3) and a full search the 4-CTA form; a plan's
+  //    tuning picks the form for its own list.
   {
-    const int per = tile_ctas_per_sm(a.from_list ? 1 : variant);
+    const int rv = occ.rest != 0 ? occ.rest : (a.from_list ? 1 : 2);
+    const int per = tile_ctas_per_sm(rv);
     if (per < 1) return DLS_ERR_CUDA;
     int ctas = sms * per;
     if (ctas > w.ctas) ctas = w.ctas;
     if ((int64_t)ctas > nblk) ctas = (int)nblk;
-    if (variant == 1 || a.from_list) k_tile<2><<<ctas, kTT, tsm, s>>>(tmap, tmapg, a);
+    if (rv == 1) k_tile<2><<<ctas, kTT, tsm, s>>>(tmap, tmapg, a);
     else k_tile<4><<<ctas, kTT, tsm, s>>>(tmap, tmapg, a);
   }
   return cudaGetLastError() == cudaSuccess ? DLS_OK : DLS_ERR_CUDA;

@@ -112,6 +112,7 @@ _SIGS = {
                                   C.c_void_p, C.POINTER(C.c_void_p)]),
     "dls_plan_execute": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t), C.c_void_p]),
     "dls_plan_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
+    "dls_plan_tuning": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
     "dls_plan_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_int32)]),
     "dls_plan_destroy": (C.c_int, [C.c_void_p]),
     "dls_plan_phase_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int32]),
@@ -444,6 +445,17 @@ class CompressPlan:
         ms = (C.c_float * 2)()
         lib().dls_plan_info(self.handle, C.byref(v), ms)
         return v.value, (ms[0], ms[1])
+
+    def tuning(self) -> dict:
+        """The occupancy form per shape class (1: built for 2 CTAs per SM, 2:
+        for 4) and each class's device ms in either form while tuning (zeros
+        when the choice came from the cache)."""
+        forms = (C.c_int32 * 2)()
+        ms = (C.c_float * 4)()
+        st = lib().dls_plan_tuning(self.handle, forms, ms)
+        if st != OK:
+            raise DlsError(st, "dls_plan_tuning")
+        return {"whole": forms[0], "rest": forms[1], "ms": {"whole": (ms[0], ms[1]), "rest": (ms[2], ms[3])}}
 
     def timing(self):
         """(device ms of the per-block kernels in the last execute, kernel nodes in the graph)."""

@@ -1,5 +1,6 @@
 """Plans: the autotuned, graph-captured compression of fixed buffers gives the
-same stream as dls_compress, call after call, on an uneven multi-variable field."""
+same stream as dls_compress, call after call, on an uneven multi-variable field;
+the tuner picks and caches an occupancy form per shape class of the blocks."""
 import json
 import os
 
@@ -25,30 +26,74 @@ def _buffers(p, field):
     return out, ws
 
 
-def test_plan_matches_compress_on_uneven_multivariable_field(tmp_path, monkeypatch):
-    cache = tmp_path / "tune.jsonl"
-    monkeypatch.setenv("DLS_AUTOTUNE_CACHE", str(cache))
+def _uneven():
     f = synth.multivar(50, 38, 26, 18).cuda()
     ebs = [1e-3, 1e-3, 1e-3, 1e-4, 1e-4]
     p = dls.make_params(tuple(f.shape), f.dtype, (16, 16, 16, 16), ebs, dls.EB_REL_RANGE, 16,
                         precision=dls.PREC_FP32, rank_mode=dls.RANK_TAIL)
+    return f, p
+
+
+def _key_class(line):
+    return line["key"].rsplit("|", 1)[1]
+
+
+def test_plan_matches_compress_on_uneven_multivariable_field(tmp_path, monkeypatch):
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("DLS_AUTOTUNE_CACHE", str(cache))
+    f, p = _uneven()
     out, ws = _buffers(p, f)
     st, nb = dls.compress_into(p, f, out, ws)
     assert st == 0
     ref = out[:nb].cpu().clone()
     plan = dls.CompressPlan(p, f, out, ws)
     variant, ms = plan.info()
-    assert variant in (1, 2) and min(ms) > 0
+    tu = plan.tuning()
+    assert variant == tu["whole"] and min(ms) > 0
+    # both classes have work here (whole blocks, and edge blocks on every axis),
+    # and each class keeps its faster form
+    for c in ("whole", "rest"):
+        a, b = tu["ms"][c]
+        assert min(a, b) > 0 and tu[c] == (1 if a < b else 2)
     for _ in range(3):
         n = plan.execute()
         assert n == nb and torch.equal(out[:n].cpu(), ref)
     plan.close()
     lines = [json.loads(l) for l in cache.read_text().splitlines()]
-    assert len(lines) == 1 and lines[0]["variant"] == variant
+    assert sorted(_key_class(l) for l in lines) == ["rest", "whole"]
+    assert {_key_class(l): l["variant"] for l in lines} == {"whole": tu["whole"], "rest": tu["rest"]}
     plan2 = dls.CompressPlan(p, f, out, ws)      # second creation reads the cache
-    assert plan2.info()[0] == variant and plan2.info()[1] == (0.0, 0.0)
+    t2 = plan2.tuning()
+    assert (t2["whole"], t2["rest"]) == (tu["whole"], tu["rest"]) and plan2.info()[1] == (0.0, 0.0)
+    assert t2["ms"] == {"whole": (0.0, 0.0), "rest": (0.0, 0.0)}
     assert plan2.execute() == nb
     plan2.close()
+
+
+@pytest.mark.parametrize("forms", [(1, 2), (2, 1)])
+def test_plan_takes_each_shape_class_form_from_the_cache(tmp_path, monkeypatch, forms):
+    """Different cached forms for the two shape classes are each honoured, and
+    the stream does not depend on them."""
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("DLS_AUTOTUNE_CACHE", str(cache))
+    f, p = _uneven()
+    out, ws = _buffers(p, f)
+    st, nb = dls.compress_into(p, f, out, ws)
+    assert st == 0
+    ref = out[:nb].cpu().clone()
+    dls.CompressPlan(p, f, out, ws).close()      # tunes and writes one line per class
+    lines = [json.loads(l) for l in cache.read_text().splitlines()]
+    want = dict(zip(("whole", "rest"), forms))
+    with open(cache, "a") as fh:                 # later lines for a key win
+        for l in lines:
+            fh.write(json.dumps({"key": l["key"], "variant": want[_key_class(l)], "ms": [0, 0]}) + "\n")
+    plan = dls.CompressPlan(p, f, out, ws)
+    tu = plan.tuning()
+    assert (tu["whole"], tu["rest"]) == forms
+    for _ in range(2):
+        n = plan.execute()
+        assert n == nb and torch.equal(out[:n].cpu(), ref)
+    plan.close()
 
 
 def test_plan_plain_form_equals_oracle():
