@@ -907,6 +907,9 @@ __device__ __forceinline__ void mixed_body(const MxArgs& a) {
     }
     bool raw = false;
     if (!accepted) {
+      // every warp has read S.ovf (above) before thread 0 clears it, so that
+      // all take the same decision path and meet at the same barriers
+      __syncthreads();
       if (tid == 0) S.ovf = 0;
       __syncthreads();
       int ovf = 0;

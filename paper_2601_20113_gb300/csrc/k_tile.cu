@@ -2582,6 +2582,10 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
     }
     bool raw = false;
     if (!accepted) {
+      // every warp has read S.ovf (above) before thread 0 clears it: a warp
+      // that read the cleared flag would take the decision the others skip,
+      // and the CTA's barriers and chunk arrivals would no longer pair up
+      __syncthreads();
       if (tid == 0) S.ovf = 0;
       __syncthreads();
       int ovf = 0;
@@ -2612,15 +2616,21 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
     // otherwise the block is encoded again into the CTA's scratch for the
     // record writer here, with every element written when it has escapes
     // (the writer lists escapes from k8 itself)
+    // (the pass's counters are read into registers, and a barrier passed,
+    // before another pass lets thread 0 reset them)
     if (!raw && in_slot) {
       // the layout's own choice: a dense record needs no entry list
-      const int wk = bit_width((uint32_t)S.kmax), ib = bit_width((uint32_t)(g.N - 1));
-      const bool dense = wk > 0 && (g.N * wk + 31) / 32 < ((int64_t)S.ncorr * (ib + wk) + 31) / 32;
+      const int kmax = S.kmax, ncorr = S.ncorr, nesc = S.nesc;
+      const int wk = bit_width((uint32_t)kmax), ib = bit_width((uint32_t)(g.N - 1));
+      const bool dense = wk > 0 && (g.N * wk + 31) / 32 < ((int64_t)ncorr * (ib + wk) + 31) / 32;
       const SlotScratch sc = slot_scratch(r, g.n, g.L, g.N);
-      if (wk > kDeferMaxWk || (!dense && S.ncorr > sc.list_cap) || S.nesc > sc.esc_cap)
-        if (!encode(r, false, S.nesc == 0, true)) break;
-    } else if (!raw && sparse && S.nesc > 0) {
-      if (!encode(r, false, false, true)) break;
+      __syncthreads();
+      if (wk > kDeferMaxWk || (!dense && ncorr > sc.list_cap) || nesc > sc.esc_cap)
+        if (!encode(r, false, nesc == 0, true)) break;
+    } else if (!raw && sparse) {
+      const int nesc = S.nesc;
+      __syncthreads();
+      if (nesc > 0 && !encode(r, false, false, true)) break;
     }
     const bool deferred = !raw && in_slot;
     // the next block's first chunks load while this record is packed
