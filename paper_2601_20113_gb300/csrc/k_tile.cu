@@ -1932,7 +1932,9 @@ struct FastBlock {
   int32_t flags, rpred;
   int32_t pad[2];
 };
-enum : int32_t { kFbNonfinite = 1, kFbRR = 2, kFbOverflow = 4 };
+// kFbRankFail: k_enc ran the exact test at the predicted rank and it failed
+// (or a coefficient overflowed), so k_tile goes straight to the search.
+enum : int32_t { kFbNonfinite = 1, kFbRR = 2, kFbOverflow = 4, kFbRankFail = 8 };
 
 // Block counters of the phase kernels and the list of blocks k_enc leaves.
 struct FastCtl {
@@ -2429,6 +2431,9 @@ __global__ void __launch_bounds__(kTT, MINB) k_enc(const __grid_constant__ CUten
       if (rp > 0 && p_r) p_rm1 = decide_pass(a, S, g, rp - 1, E_rm1, bnd, el2, rcst);
       accepted = p_r && !p_rm1;
     }
+    // k_tile would repeat this very test (same pass, same inputs, same
+    // decision) before searching: record that it failed
+    const bool rank_fail = !accepted;
     // a deferred record has no correction beyond kDeferMaxWk bits, its
     // escapes fit the slot's list and, when sparse, so does its entry list
     if (accepted) {
@@ -2438,6 +2443,7 @@ __global__ void __launch_bounds__(kTT, MINB) k_enc(const __grid_constant__ CUten
     }
     pc.mark(S, kPhDecide);
     if (!accepted) {
+      if (rank_fail && threadIdx.x == 0) a.fb[bi].flags |= kFbRankFail;
       to_list(bi);
       __syncthreads();
       continue;
@@ -2566,7 +2572,7 @@ __global__ void __launch_bounds__(kTT, MINB) k_tile(const __grid_constant__ CUte
     const double bnd = (double)(rows_per_thread * n + 40) * 6.6e-8;
     bool accepted = false;
     int r = 0;
-    if (a.learned != kRankSearch && !may_overflow) {
+    if (a.learned != kRankSearch && !may_overflow && !(a.fb[bi].flags & kFbRankFail)) {
       const int rp = S.r_pred;
       if (!encode(rp, true, sparse, false)) break;
       pc.mark(S, kPhEncode);
