@@ -106,6 +106,8 @@ struct Layout {
   size_t gstats;        // nvars x 4 doubles when the caller gives the whole field's statistics
   size_t rice_tmp, rice_info, rice_chunks;   // Rice stage: the packers' stream (bound bytes), per-block
                                              // choices, per-chunk run counts
+  size_t pitched;       // the field with padded x lines (MixedWork::pitched)
+  int64_t pitch;
   int ctas;
   bool mixed;
 };
@@ -206,6 +208,8 @@ static Layout work_layout(const Plan& P) {
     L.phase = take(sizeof(unsigned long long) * (size_t)L.ctas * kMixedPhases);
     L.fast = take(tile_fast_bytes(P.nb));
     L.gstats = P.has_gstats ? take(sizeof(double) * 4 * (size_t)P.nvars) : 0;
+    L.pitch = pitched_row(P, mixed_route(P).tile);
+    L.pitched = L.pitch ? take(sizeof(float) * (size_t)(P.nvars * P.dims[3] * P.dims[2] * P.dims[1] * L.pitch)) : 0;
     take_rice(L);
     L.total = off;
     return L;
@@ -354,6 +358,8 @@ static MixedWork mixed_work(const Plan& P, const Layout& L, void* ws) {
   mw.ctas = L.ctas;
   mw.phase = (unsigned long long*)(b + L.phase);
   mw.fast = b + L.fast;
+  mw.pitched = L.pitch ? (float*)(b + L.pitched) : nullptr;
+  mw.pitch = L.pitch;
   return mw;
 }
 

@@ -254,7 +254,17 @@ struct MixedWork {
   int ctas;
   unsigned long long* phase;   // ctas x kMixedPhases cycle counters
   uint8_t* fast;        // per-block state of the tile route's phase kernels (tile_fast_bytes)
+  // The field with its x lines padded to `pitch` floats (a multiple of 4), for
+  // fields whose x extent is not: the staged kernels' tensor map reads this
+  // copy, so every chunk comes in by TMA (null and 0 when not used).
+  float* pitched;
+  int64_t pitch;
 };
+// Padded x-line length of the pitched copy for a plan, or 0 when the plan
+// reads its field directly: a float32 field through the staged kernels, over
+// its whole block range, whose x extent is not a multiple of 4 while the block
+// width is (a TMA box row must be a multiple of 16 bytes).
+int64_t pitched_row(const Plan& P, bool staged);
 constexpr int kMaxMixedN = 16;
 constexpr int kMixedPhases = 14;
 

@@ -2787,6 +2787,34 @@ bool tile_chunk_box(const Plan& p, int* bxb, int* yc, int* zc, int* bt) {
   return true;
 }
 
+int64_t pitched_row(const Plan& p, bool staged) {
+  if (!staged || p.dtype != DLS_F32 || p.b0 != 0 || p.nb != p.nb_total || p.nb == 0) return 0;
+  if (p.dims[0] % 4 == 0 || p.block[0] % 4 != 0) return 0;
+  return align_up(p.dims[0], 4);
+}
+
+// The pitched copy: one warp per x line (rows = nvars * nt * nz * ny), the
+// line's nx values then zeros up to the pitch.  Pairs of floats where nx is
+// even and the input 8-byte aligned (the copy's lines start on 16 bytes).
+__global__ void __launch_bounds__(256) k_pitch_rows(const float* __restrict__ in, float* __restrict__ out,
+                                                    int64_t rows, int64_t nx, int64_t pitch, int pairs) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = w0; r < rows; r += nw) {
+    const float* src = in + r * nx;
+    float* dst = out + r * pitch;
+    if (pairs) {
+      const float2* s2 = reinterpret_cast<const float2*>(src);
+      float2* d2 = reinterpret_cast<float2*>(dst);
+      for (int64_t i = lane; i < nx / 2; i += 32) d2[i] = __ldg(s2 + i);
+    } else {
+      for (int64_t i = lane; i < nx; i += 32) dst[i] = __ldg(src + i);
+    }
+    for (int64_t i = nx + lane; i < pitch; i += 32) dst[i] = 0.0f;
+  }
+}
+
 // Dynamic shared memory: alignment slack, the shared struct, and with the
 // tensor-core Gram the 16 KiB lo buffer.
 size_t tile_smem_bytes(bool tc) {
@@ -2883,20 +2911,41 @@ int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, in
   a.mrc = magic(a.rc);
   a.cp_pairs = (p.dims[0] % 2 == 0) && (a.bxb % 2 == 0) && (((uintptr_t)d_in & 7) == 0);
   a.jfloor = 5e-2;
+  // The tensor map reads the field itself when its x lines are whole
+  // multiples of 16 bytes, else the pitched copy the launch writes first (a
+  // plan over the whole field); the per-element reads (exact evaluations, raw
+  // records, escapes) stay on the field itself.
+  const void* tsrc = d_in;
+  int64_t pitch = p.dims[0];
+  const bool pitched = w.pitched && w.pitch > 0 && blo == 0 && bhi == p.nb && pitched_row(p, true) == w.pitch;
+  if (pitched) {
+    const int64_t rows = p.nvars * p.dims[3] * p.dims[2] * p.dims[1];
+    const int pairs = (p.dims[0] % 2 == 0) && (((uintptr_t)d_in & 7) == 0);
+    int dev0 = 0, sms0 = 152;
+    if (cudaGetDevice(&dev0) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms0, cudaDevAttrMultiProcessorCount, dev0) != cudaSuccess)
+      return DLS_ERR_CUDA;
+    const int64_t cap = (int64_t)sms0 * 8, need = cdiv(rows, 8);
+    k_pitch_rows<<<(unsigned)(need < cap ? (need > 0 ? need : 1) : cap), 256, 0, s>>>(
+        static_cast<const float*>(d_in), w.pitched, rows, p.dims[0], w.pitch, pairs);
+    tsrc = w.pitched;
+    pitch = w.pitch;
+  }
   CUtensorMap tmap;
   memset(&tmap, 0, sizeof(tmap));
-  const bool aligned = (p.dims[0] % 4 == 0) && (p.block[0] % 4 == 0) && (((uintptr_t)d_in & 15) == 0);
+  const bool aligned = (pitch % 4 == 0) && (p.block[0] % 4 == 0) && (((uintptr_t)tsrc & 15) == 0);
   a.use_tma = 0;
   if (aligned) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (enc) {
       const cuuint64_t dims[5] = {(cuuint64_t)p.dims[0], (cuuint64_t)p.dims[1], (cuuint64_t)p.dims[2],
                                   (cuuint64_t)p.dims[3], (cuuint64_t)p.nvars};
-      const cuuint64_t strides[4] = {(cuuint64_t)p.dims[0] * 4, (cuuint64_t)(p.dims[0] * p.dims[1]) * 4,
-                                     (cuuint64_t)p.P * 4, (cuuint64_t)p.K * 4};
+      const cuuint64_t plane = (cuuint64_t)(pitch * p.dims[1] * p.dims[2]);     // one time step
+      const cuuint64_t strides[4] = {(cuuint64_t)pitch * 4, (cuuint64_t)(pitch * p.dims[1]) * 4, plane * 4,
+                                     plane * (cuuint64_t)p.dims[3] * 4};
       const cuuint32_t box[5] = {(cuuint32_t)a.bxb, (cuuint32_t)a.yc, (cuuint32_t)a.zc, (cuuint32_t)a.bt, 1u};
       const cuuint32_t es[5] = {1, 1, 1, 1, 1};
-      const CUresult rc = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void*>(d_in), dims, strides, box,
+      const CUresult rc = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void*>(tsrc), dims, strides, box,
                               es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       a.use_tma = rc == CUDA_SUCCESS ? 1 : 0;
@@ -2912,7 +2961,7 @@ int launch_tile_compress(const Plan& p, const void* d_in, const MixedWork& w, in
                       : p.precision == DLS_PREC_BF16X3 ? kTcBf16x3
                       : p.precision == DLS_PREC_BF16  ? kTcBf16
                                                       : kTcNone;
-  if (tc_mode != kTcNone && a.use_tma && a.bxb == 16 && a.yc == 16 && a.zc == 1 && a.bt == 16) {
+  if (tc_mode != kTcNone && a.use_tma && !pitched && a.bxb == 16 && a.yc == 16 && a.zc == 1 && a.bt == 16) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     const cuuint64_t dims[5] = {4, (cuuint64_t)(p.dims[3] * p.nvars), (cuuint64_t)(p.dims[0] / 4), (cuuint64_t)p.dims[1],
                                 (cuuint64_t)p.dims[2]};
