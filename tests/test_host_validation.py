@@ -88,3 +88,22 @@ def test_global_basis_rejects_null_buffers_before_device_work():
     st = dls.lib().dls_gb_compress(C.byref(p), None, None, None, 0, C.byref(nb), None, 0, None)
     assert st == -1
     assert dls.lib().dls_gb_decompress(None, 0, None, 0, None) == -1
+
+
+def test_pitched_copy_in_the_workspace():
+    """A float32 field whose x extent is not a multiple of 4 floats, compressed
+    whole by the staged kernels, has a copy with x lines padded to a multiple of
+    4 floats in its workspace; a block range of it, and a field whose lines are
+    already whole multiples of 16 bytes, have none."""
+    from paper_2601_20113_gb300 import dls
+
+    def ws(shape, **kw):
+        p = dls.make_params(shape, torch.float32, BLOCK, 1e-3, dls.EB_ABS, 16, precision=dls.PREC_FP32, **kw)
+        return dls.workspace_size(p)
+
+    nb = 2 * 2 * 2 * 3 * 4                       # 2 variables, 2 x 2 x 3 x 4 blocks of 16^4 each
+    slack = 16384                                # the last block's per-block entries and alignments
+    for nx, pitched in ((50, 2 * 18 * 26 * 38 * 52 * 4), (52, 0)):
+        shape = (2, 18, 26, 38, nx)
+        diff = ws(shape) - ws(shape, block_end=nb - 1)
+        assert pitched <= diff <= pitched + slack, (nx, diff)
