@@ -147,7 +147,12 @@ typedef struct {
 size_t dls_compress_bound(const dls_params* p);
 
 /* Device workspace dls_compress needs, in bytes (caller allocates, 256-byte
- * aligned).  0 if the parameters are invalid. */
+ * aligned).  0 if the parameters are invalid.  For a float32 field compressed
+ * in a non-FP64 precision mode over its whole block range, whose x extent is
+ * not a multiple of 4 (x lines not a multiple of 16 bytes) while block[0] is,
+ * it includes a copy of the field with x lines padded to a multiple of 4
+ * values: the staged kernels read their tiles by TMA from that copy, written
+ * at the start of every compression. */
 size_t dls_workspace_size(const dls_params* p);
 
 /* Compress a device field (Algorithm 1, step 2-3; Sec. 2.7.2 stream).
