@@ -531,7 +531,8 @@ def run_config(args):
                                 precision=dls.PREC_FP32, rank_mode=rm)
             ms, nb, stages, c, cs = _plan_run(p, field, args.steps)
             modes[name] = {"value": in_bytes / (ms * 1e-3) / 1e9, "ms_per_step": ms, "ratio": in_bytes / nb,
-                           "n_accepted": c["n_accepted"], "n_searched": c["n_searched"], "phases_ms": stages}
+                           "n_accepted": c["n_accepted"], "n_searched": c["n_searched"], "phases_ms": stages,
+                           "tuning": c["tuning"]}
             if name == "learned":
                 comp = cs
             else:
