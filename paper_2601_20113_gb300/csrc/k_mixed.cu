@@ -943,7 +943,9 @@ __device__ __forceinline__ void mixed_body(const MxArgs& a) {
 }
 
 // Two occupancy variants of the same kernel: 2 CTAs per SM (128 registers per
-// thread) or 1 CTA per SM (no register cap); the plan's autotuner picks one.
+// thread) or 1 CTA per SM (no register cap); a plan's tuning picks one as the
+// form of the shape class this kernel serves with k_tile (the blocks that are
+// not whole blocks of the encode pass).
 template <int MINB>
 __global__ void __launch_bounds__(kMT, MINB) k_mixed(MxArgs a) {
   mixed_body(a);
