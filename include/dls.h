@@ -203,9 +203,10 @@ int dls_plan_execute(dls_plan* plan, size_t* out_bytes, dls_stream_t stream);
  * one compression with every class in form 1 and in form 2 (0 if the choices
  * came from the cache or the form has one variant). */
 int dls_plan_info(const dls_plan* plan, int32_t* variant, float* tune_ms);
-/* The plan's occupancy form per shape class -- 1: the kernels built for 2
- * CTAs per SM (more registers per thread), 2: built for 4 -- and the device
- * time that chose it.  Classes: [0] "whole", the blocks of the full block
+/* The plan's occupancy form per shape class -- 1: the kernels built for fewer
+ * CTAs per SM with more registers per thread (2 per SM for the staged kernels,
+ * 1 for the space-side kernel), 2: built for more (4, 2) -- and the device time
+ * that chose it.  Classes: [0] "whole", the blocks of the full block
  * shape that the encode kernel finishes at the predicted rank (Sec. 2.5 rank
  * step); [1] "rest", what the searching kernels take: edge blocks of smaller
  * shapes (Sec. 2.7.1 partition remainders), predictions the exact test
