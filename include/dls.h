@@ -262,7 +262,9 @@ int dls_compress_host(const dls_params* p, const void* h_in, void* h_out, size_t
  * workspace: the workspace is a 64 MiB device array inside this library.
  *   - Fields whose dls_workspace_size(p) exceeds 64 MiB are rejected with
  *     DLS_ERR_WORKSPACE (float32 blocks of 16^3 x 16 need about 8.2 bytes of
- *     workspace per point: up to roughly 8 million points).
+ *     workspace per point: up to roughly 8 million points; about 4 bytes more
+ *     per point where the workspace holds the pitched copy of a field whose x
+ *     extent is not a multiple of 4, see dls_workspace_size).
  *   - The first call on each device looks up the array's device address with
  *     that device current; make that first call before any stream capture.
  *     Under CUDA's lazy module loading (the default) that lookup is also when
